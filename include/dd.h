@@ -1,0 +1,251 @@
+/*
+ * dd.h - C ABI of the GB300 (sm_103a) library for the domain-decomposed
+ * Wilson-Dirac hot path of the hierarchical acceptance algorithm of
+ * Leder, Finkenrath, Knechtli, "Fermions as global correction in lattice QCD"
+ * (Lattice 2011).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * Lattice: extents L0 x L1 x L2 x L3, axis 3 is time, canonical site index
+ *   s = x0 + L0*(x1 + L1*(x2 + L2*x3)).  Every extent must be even.  Blocks
+ *   (domains) of extent b_a tile the lattice from the origin; the number of
+ *   blocks per direction must be even and >= 2 (checkerboard colouring of the
+ *   blocks, Sec. 3 and Fig. 1); block colour = (sum_a B_a) mod 2, 0 = black.
+ * Fields at the boundary are FP64 complex numbers stored as interleaved
+ *   (re, im) doubles, canonical site order:
+ *     gauge field  U[s][a][i][j]   72 doubles per site: SU(3) link from s to
+ *                                  s + a-hat (a = lattice axis 0..3);
+ *     spinor       psi[s][spin][c] 24 doubles per site (4 spins x 3 colours),
+ *                                  chiral gamma basis (gamma_0 = time =
+ *                                  axis 3, gamma_5 = diag(1, 1, -1, -1));
+ *     nrhs spinors are stored one after another (stride 24*V doubles), or
+ *     24*V/2 doubles for even-site vectors (DD_OP_DTILDE*, DD_OP_HEO).
+ *   Pointers named U, in, out, x, b, eta are DEVICE pointers owned by the
+ *   caller; the library never frees them.  Scalars written through pointers
+ *   documented as "device" are valid after the handle's stream has been
+ *   synchronised (dd_sync); "host" pointers are written before return.
+ * Operator: D = 1 - kappa*H with the Wilson hopping term
+ *   (H psi)(x) = sum_a [(1 - gamma_a) U_a(x) psi(x + a) + (1 + gamma_a) U_a(x - a)^dag psi(x - a)],
+ *   hops across the time edge multiplied by bc_time.
+ * Random streams: Philox4x32-10 (Salmon et al., SC'11), key = seed, counter =
+ *   (element, purpose << 24 | sub, ctr mod 2^32, ctr >> 32); Gaussian noise with
+ *   density ~ exp(-|eta|^2) by Box-Muller in FP64 (the normalisation for which
+ *   the estimator of Sec. 4 is unbiased).
+ * Errors: every call returns DD_OK (0) or a negative DD_ERR_* code; nothing is
+ *   thrown across the boundary; dd_last_error() gives a message.  Device-side
+ *   failures (a solver that hits its iteration cap, a non-finite reduction, a
+ *   bounded wait that ran out) set a status word read by dd_status(); no kernel
+ *   traps.  All work is enqueued on the stream given to dd_init.
+ */
+#ifndef DD_H
+#define DD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define DD_OK 0
+#define DD_ERR_INVALID_ARG (-1)
+#define DD_ERR_UNSUPPORTED (-2)
+#define DD_ERR_CUDA (-3)
+#define DD_ERR_NOT_CONVERGED (-4)
+#define DD_ERR_NUMERIC (-5)
+#define DD_ERR_TIMEOUT (-6)
+#define DD_ERR_NO_WORKSPACE (-7)
+
+/* arithmetic / storage precision of a kernel */
+#define DD_PREC_F64 0 /* FP64 storage and arithmetic */
+#define DD_PREC_F32 1 /* FP32 storage (links: rows 1-2, third row rebuilt), FP32 arithmetic */
+#define DD_PREC_F16 2 /* FP16 storage (spinors with a per-site FP32 scale), FP32 arithmetic */
+
+/* active-link sets (Sec. 3: links with at most one end on a block boundary) */
+#define DD_ACTIVE_AUTO 0   /* INTRA if a block extent <= 2, INNER6 if all >= 8, else PAPER */
+#define DD_ACTIVE_PAPER 1  /* the rule applied to the block itself */
+#define DD_ACTIVE_INNER6 2 /* the rule applied to the block shrunk by one site per side */
+#define DD_ACTIVE_INTRA 3  /* every link with both ends in one block (updated colour by colour) */
+
+/* operators of dd_apply_D */
+#define DD_OP_D 0          /* D psi on the whole lattice */
+#define DD_OP_DDAG 1       /* D^dag psi = gamma5 D gamma5 psi */
+#define DD_OP_DTILDE 2     /* even sites: (1 - kappa^2 H_eo H_oe) psi_e */
+#define DD_OP_DTILDE_DAG 3 /* even sites: gamma5 Dtilde gamma5 psi_e */
+#define DD_OP_HEO 4        /* even sites <- odd sites: H_eo psi_o (in: odd-site vector) */
+#define DD_OP_INTER 5      /* (D_bw + D_wb) psi: only the hops that cross block faces */
+
+/* purposes of the random stream (counter word 1, bits 24-31) */
+#define DD_PURPOSE_GLOBAL_NOISE 1
+#define DD_PURPOSE_BLOCK_NOISE 2
+#define DD_PURPOSE_HEATBATH 3
+#define DD_PURPOSE_BLOCK_ACCEPT 5
+#define DD_PURPOSE_GLOBAL_ACCEPT 6
+#define DD_PURPOSE_USER_NOISE 7
+
+/* estimator modes (Eq. param) */
+#define DD_EST_FACTORS 0  /* factor i uses U_i, U_{i+1} of the geodesic path, its own eta_i */
+#define DD_EST_REPLICAS 1 /* every factor uses (U, U'), its own eta_i (variance measurement) */
+
+/* block filter modes (Eq. 4step, step 1) */
+#define DD_FILTER_STOCHASTIC 0
+#define DD_FILTER_EXACT 1
+
+typedef struct dd_handle* dd_t;
+
+typedef struct {
+    int dims[4];       /* lattice extents, axis 3 = time */
+    int block[4];      /* block (domain) extents */
+    double kappa;      /* hopping parameter of D = 1 - kappa*H */
+    int bc_time;       /* fermion boundary phase in time: -1 antiperiodic, +1 periodic */
+    int active_mode;   /* DD_ACTIVE_* */
+    int max_rhs;       /* largest nrhs or number of factors of any later call */
+    int inner_prec;    /* precision of the inner global solver: DD_PREC_F64/F32/F16 */
+    int block_prec;    /* precision of the inner block solver: DD_PREC_F64/F32 */
+    double tol_global; /* true relative residual of global solves, ||b - D x|| / ||b|| */
+    double tol_block;  /* true relative residual of Dirichlet block solves */
+    double tol_inner;  /* residual reduction asked of one inner solve (defect correction) */
+    int maxit;         /* iteration cap of any single Krylov solve */
+} dd_params;
+
+/* Fill p with defaults: kappa 0.125, bc_time -1, DD_ACTIVE_AUTO, max_rhs 1,
+ * inner F16, block F32, tol_global 1e-10, tol_block 1e-12, tol_inner 1e-3,
+ * maxit 20000.  dims/block are zeroed and must be set by the caller. */
+int dd_default_params(dd_params* p);
+
+/* Create a handle for one lattice and block decomposition (Sec. 3, Eq. domdec).
+ * stream: a cudaStream_t (NULL = legacy default stream); all later work of
+ * the handle is enqueued on it.  Builds the geometry tables on the host and
+ * uploads them (the only allocation the library makes itself).
+ * Errors: DD_ERR_INVALID_ARG for odd or non-dividing extents, blocks per
+ * direction odd or < 2, kappa <= 0, max_rhs < 1; DD_ERR_CUDA on a CUDA error. */
+int dd_init(dd_t* h, const dd_params* p, void* stream);
+
+/* Bytes of device workspace the handle needs for its max_rhs. */
+int dd_workspace_size(dd_t h, size_t* bytes);
+
+/* Hand the library device memory of at least dd_workspace_size bytes,
+ * 256-byte aligned.  The caller owns it and must keep it alive until
+ * dd_finalize or the next dd_set_workspace.  Every entry point below except
+ * dd_get_maps and dd_status fails with DD_ERR_NO_WORKSPACE before this call. */
+int dd_set_workspace(dd_t h, void* dev_ptr, size_t bytes);
+
+/* Copy the geometry tables to HOST arrays (any pointer may be NULL):
+ *   nbr[s*8 + 2a]     = canonical index of s + a-hat, nbr[s*8 + 2a + 1] = of s - a-hat;
+ *   sign[s*8 + k]     = fermion phase of that hop (+1 or bc_time);
+ *   dd_order[q]       = canonical site at block-ordered position q (black
+ *                       blocks first in increasing block id, then white;
+ *                       sites of a block in local lexicographic order, Sec. 3);
+ *   block_of[s]       = block id of s (lexicographic in block coordinates);
+ *   active[s*4 + a]   = 1 if link (s, a) belongs to the active set.
+ * Sizes: V = L0*L1*L2*L3. */
+int dd_get_maps(dd_t h, int32_t* nbr, int32_t* sign, int32_t* dd_order, int32_t* block_of, uint8_t* active);
+
+/* out = op(U) in for nrhs spinors (op = DD_OP_*), in precision prec
+ * (the FP32/FP16 forms round links and spinors to that storage first).
+ * Definition: the Wilson-Dirac operator (Sec. 5: "plain Wilson-Dirac"), its
+ * even-odd Schur complement and the block-interaction terms of Eq. domdec.
+ * in/out: device, canonical spinors (even-site vectors for DTILDE/DTILDE_DAG,
+ * odd-site in / even-site out for HEO; the sites of one parity in canonical
+ * order).  in and out must not overlap. */
+int dd_apply_D(dd_t h, void* out, const void* in, const void* U, int op, int prec, int nrhs);
+
+/* out = D_b psi on the blocks of the colours in colour_mask (bit 0 black,
+ * bit 1 white), 0 on the other sites: every hop that leaves a block is
+ * dropped (Dirichlet block operators, D_bb and D_ww of Eq. domdec). */
+int dd_apply_D_block(dd_t h, void* out, const void* in, const void* U, int colour_mask, int prec, int nrhs);
+
+/* Solve D x = b for nrhs right-hand sides (shared U) by CG on the even-odd
+ * normal equations; with prec = DD_PREC_F32/F16 the inner solver runs in that
+ * precision inside an FP64 defect-correction loop whose residual is the FP64
+ * true residual ||b - D x|| / ||b|| <= tol_global.  iters (host, may be NULL)
+ * receives the total inner iterations, relres (host, nrhs doubles, may be
+ * NULL) the final true relative residuals.  DD_ERR_NOT_CONVERGED if maxit was
+ * reached first (x then holds the last iterate). */
+int dd_solve(dd_t h, void* x, const void* b, const void* U, int nrhs, int prec, int* iters, double* relres);
+
+/* Complex Gaussian noise (density ~ exp(-|eta|^2), Sec. 4) on every site for
+ * nrhs vectors: component (s, spin, c) of vector r uses element
+ * s*12 + spin*3 + c, purpose `purpose`, sub = r, counter ctr, key seed. */
+int dd_noise(dd_t h, void* eta, int nrhs, int purpose, uint64_t seed, uint64_t ctr);
+
+/* U_t = U (U^dag U')^t, t = i/n, on the active links (other links copied from
+ * U); the geodesic path of Eq. param with the branch for which det = 1
+ * (phases in (-pi, pi], the largest lowered / smallest raised by 2 pi when
+ * they sum to +-2 pi).  i = 0 gives U and i = n gives U' exactly. */
+int dd_interpolate(dd_t h, void* U_t, const void* U, const void* U_new, int i, int n);
+
+/* Stochastic estimate of the global Schur-complement step (Eq. 4step step 3,
+ * Sec. 4): n factors, factor i with M_i = Dhat[U_{i+1}]^{-1} Dhat[U_i]
+ * (DD_EST_FACTORS; U_0 = U_old, U_n = U_new) or M = Dhat[U_new]^{-1} Dhat[U_old]
+ * (DD_EST_REPLICAS), noise eta_i on the black sites (purpose
+ * DD_PURPOSE_GLOBAL_NOISE, sub = i).  ln_out[i] (device, n doubles) receives
+ * -eta_i^dag (M_i^dag M_i - 1) eta_i, computed as -(2 Re<eta, d> + |d|^2) with
+ * d = (M_i - 1) eta_i, d = [D'^{-1} (s, 0)]_black,
+ * s = B'E'^{-1}C' eta - A'A^{-1}BE^{-1}C eta.  Block solves to tol_block,
+ * the global solve to tol_global in inner_prec. */
+int dd_det_ratio_estimate(dd_t h, const void* U_old, const void* U_new, int n, uint64_t seed, uint64_t ctr,
+                          int mode, double* ln_out);
+
+/* Block filter (Eq. 4step step 1; Sec. 5 "block-wise accepted"): for every
+ * block of a colour in colour_mask, ln_b[block] (device, nblocks doubles) =
+ * sum over n factors of -(2 Re<eta, d> + |d|^2), d = D_b[U_{i+1}]^{-1}
+ * (D_b[U_i] - D_b[U_{i+1}]) eta_{b,i} (DD_FILTER_STOCHASTIC, purpose
+ * DD_PURPOSE_BLOCK_NOISE, sub = i), or 2 (ln|det D_b[U_new]| - ln|det D_b[U_old]|)
+ * (DD_FILTER_EXACT, dense LU, blocks of at most 256 sites).  Then accept[block]
+ * (device, nblocks bytes) = ln u_b < ln_b (u_b: purpose DD_PURPOSE_BLOCK_ACCEPT,
+ * element = block id), 1 for blocks outside colour_mask, and the active links
+ * of rejected blocks are copied back from U_old into U_new (in place).
+ * All (block, factor) solves run in one persistent launch. */
+int dd_block_filter(dd_t h, const void* U_old, void* U_new, int colour_mask, int mode, int n, uint64_t seed,
+                    uint64_t ctr, double* ln_b, uint8_t* accept);
+
+/* Proposal (Eq. 4step step 0): n_hb Cabibbo-Marinari heat-bath sweeps of the
+ * Wilson plaquette action at beta, each followed by n_or over-relaxation
+ * sweeps, on the active links of the blocks of the colours in colour_mask,
+ * in place.  Sweep order: direction 0..3, site parity even then odd;
+ * subgroups (0,1), (1,2), (0,2); Kennedy-Pendleton sampler with at most 64
+ * tries (after which the subgroup element is kept; counted in dd_status).
+ * Random numbers: purpose DD_PURPOSE_HEATBATH, element 4*s + a,
+ * sub = sweep << 16 | subgroup << 12 | draw. */
+int dd_gauge_update(dd_t h, void* U, int colour_mask, double beta, int n_hb, int n_or, uint64_t seed, uint64_t ctr);
+
+/* Global acceptance (Eq. 4step step 3 decision): accept iff
+ * ln u < sum_i ln_r[i] (ln_r device, n doubles; u: purpose
+ * DD_PURPOSE_GLOBAL_ACCEPT, element 0).  On rejection U_old is copied into U.
+ * accept (device, 1 byte) receives the decision, ln_margin (device, 1 double,
+ * may be NULL) the value sum_i ln_r[i] - ln u. */
+int dd_global_accept(dd_t h, void* U, const void* U_old, const double* ln_r, int n, uint64_t seed, uint64_t ctr,
+                     uint8_t* accept, double* ln_margin);
+
+/* Exact check path (Sec. 3: block determinants "computed exactly by ...
+ * LU-decomposition"): dense FP64 LU with partial pivoting of D (which = 0,
+ * out[0] = ln|det D|, lattices of at most 512 sites) or of every block
+ * operator D_b (which = 1, out[b] = ln|det D_b|, blocks of at most 256 sites),
+ * or of the domain Schur complement Dhat (which = 2, out[0] = ln|det Dhat|,
+ * at most 512 sites).  out: device doubles. */
+int dd_logdet_exact(dd_t h, const void* U, int which, double* out);
+
+/* Mean plaquette <Re tr U_P / 3> (device, 1 double). */
+int dd_plaquette(dd_t h, const void* U, double* out);
+
+/* Wait for the handle's stream. */
+int dd_sync(dd_t h);
+
+/* Read and clear the device status word: 0, or a DD_ERR_* code raised by a
+ * kernel since the last call.  heatbath_fails (may be NULL) receives the
+ * number of subgroup updates left unchanged by the Kennedy-Pendleton cap. */
+int dd_status(dd_t h, int* device_status, long long* heatbath_fails);
+
+/* Message of the last error of this handle (static storage, never NULL). */
+const char* dd_last_error(dd_t h);
+
+/* Release the handle's own tables; the workspace stays with the caller. */
+int dd_finalize(dd_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DD_H */

@@ -1,0 +1,112 @@
+"""ctypes binding of the C ABI declared in include/dd.h.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libdd.so.  The library is loaded from this package directory; if
+it is missing the import fails loudly (there is no CPU fallback).
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdd.so")
+
+DD_OK = 0
+DD_ERR_INVALID_ARG = -1
+DD_ERR_UNSUPPORTED = -2
+DD_ERR_CUDA = -3
+DD_ERR_NOT_CONVERGED = -4
+DD_ERR_NUMERIC = -5
+DD_ERR_TIMEOUT = -6
+DD_ERR_NO_WORKSPACE = -7
+
+DD_PREC_F64, DD_PREC_F32, DD_PREC_F16 = 0, 1, 2
+DD_ACTIVE_AUTO, DD_ACTIVE_PAPER, DD_ACTIVE_INNER6, DD_ACTIVE_INTRA = 0, 1, 2, 3
+DD_OP_D, DD_OP_DDAG, DD_OP_DTILDE, DD_OP_DTILDE_DAG, DD_OP_HEO, DD_OP_INTER = 0, 1, 2, 3, 4, 5
+DD_PURPOSE_GLOBAL_NOISE = 1
+DD_PURPOSE_BLOCK_NOISE = 2
+DD_PURPOSE_HEATBATH = 3
+DD_PURPOSE_BLOCK_ACCEPT = 5
+DD_PURPOSE_GLOBAL_ACCEPT = 6
+DD_PURPOSE_USER_NOISE = 7
+DD_EST_FACTORS, DD_EST_REPLICAS = 0, 1
+DD_FILTER_STOCHASTIC, DD_FILTER_EXACT = 0, 1
+
+ERROR_NAMES = {
+    DD_ERR_INVALID_ARG: "DD_ERR_INVALID_ARG",
+    DD_ERR_UNSUPPORTED: "DD_ERR_UNSUPPORTED",
+    DD_ERR_CUDA: "DD_ERR_CUDA",
+    DD_ERR_NOT_CONVERGED: "DD_ERR_NOT_CONVERGED",
+    DD_ERR_NUMERIC: "DD_ERR_NUMERIC",
+    DD_ERR_TIMEOUT: "DD_ERR_TIMEOUT",
+    DD_ERR_NO_WORKSPACE: "DD_ERR_NO_WORKSPACE",
+}
+
+
+class dd_params(ctypes.Structure):
+    _fields_ = [
+        ("dims", ctypes.c_int * 4),
+        ("block", ctypes.c_int * 4),
+        ("kappa", ctypes.c_double),
+        ("bc_time", ctypes.c_int),
+        ("active_mode", ctypes.c_int),
+        ("max_rhs", ctypes.c_int),
+        ("inner_prec", ctypes.c_int),
+        ("block_prec", ctypes.c_int),
+        ("tol_global", ctypes.c_double),
+        ("tol_block", ctypes.c_double),
+        ("tol_inner", ctypes.c_double),
+        ("maxit", ctypes.c_int),
+    ]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_U64 = ctypes.c_uint64
+
+# name -> (argtypes); every function returns int except dd_last_error
+SIGNATURES = {
+    "dd_default_params": [ctypes.POINTER(dd_params)],
+    "dd_init": [ctypes.POINTER(_P), ctypes.POINTER(dd_params), _P],
+    "dd_workspace_size": [_P, ctypes.POINTER(ctypes.c_size_t)],
+    "dd_set_workspace": [_P, _P, ctypes.c_size_t],
+    "dd_get_maps": [_P, _P, _P, _P, _P, _P],
+    "dd_apply_D": [_P, _P, _P, _P, _I, _I, _I],
+    "dd_apply_D_block": [_P, _P, _P, _P, _I, _I, _I],
+    "dd_solve": [_P, _P, _P, _P, _I, _I, ctypes.POINTER(_I), _P],
+    "dd_noise": [_P, _P, _I, _I, _U64, _U64],
+    "dd_interpolate": [_P, _P, _P, _P, _I, _I],
+    "dd_det_ratio_estimate": [_P, _P, _P, _I, _U64, _U64, _I, _P],
+    "dd_block_filter": [_P, _P, _P, _I, _I, _I, _U64, _U64, _P, _P],
+    "dd_gauge_update": [_P, _P, _I, _D, _I, _I, _U64, _U64],
+    "dd_global_accept": [_P, _P, _P, _P, _I, _U64, _U64, _P, _P],
+    "dd_logdet_exact": [_P, _P, _I, _P],
+    "dd_plaquette": [_P, _P, _P],
+    "dd_sync": [_P],
+    "dd_status": [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_longlong)],
+    "dd_last_error": [_P],
+    "dd_finalize": [_P],
+}
+
+_lib = None
+
+
+def load():
+    """Load libdd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library {LIB_PATH} is missing: run paper_1112_1243_gb300.build.build() "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, args in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_char_p if name == "dd_last_error" else ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(SIGNATURES)

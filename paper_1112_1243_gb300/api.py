@@ -1,0 +1,220 @@
+"""Python binding of the C ABI (include/dd.h) with the same entry-point names.
+
+Device buffers are torch tensors (PyTorch provides device memory and the
+stream); every function here only marshals arguments and calls libdd.so.
+Fields use the canonical FP64 layouts of the C ABI:
+  gauge field  complex128 tensor of shape (V, 4, 3, 3)
+  spinors      complex128 tensor of shape (nrhs, V, 4, 3) or (V, 4, 3)
+"""
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import *  # noqa: F401,F403  (constants)
+
+
+class DDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_lib.ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Handle:
+    """A dd_t handle plus the torch-owned workspace it uses."""
+
+    def __init__(self, ptr, params, workspace, stream):
+        self.ptr = ptr
+        self.params = params
+        self.workspace = workspace
+        self.stream = stream
+        self.dims = tuple(params.dims)
+        self.block = tuple(params.block)
+        self.V = self.dims[0] * self.dims[1] * self.dims[2] * self.dims[3]
+        self.nblocks = 1
+        for L, b in zip(self.dims, self.block):
+            self.nblocks *= L // b
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            try:
+                _lib.load().dd_finalize(self.ptr)
+            except Exception:
+                pass
+            self.ptr = None
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_contiguous():
+        raise ValueError("tensors passed to the library must be contiguous")
+    return t.data_ptr()
+
+
+def _check(h, rc):
+    if rc != _lib.DD_OK:
+        lib = _lib.load()
+        msg = lib.dd_last_error(h.ptr if isinstance(h, Handle) else h)
+        raise DDError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def dd_default_params():
+    p = _lib.dd_params()
+    _lib.load().dd_default_params(ctypes.byref(p))
+    return p
+
+
+def dd_init(dims, block, kappa, bc_time=-1, active_mode=_lib.DD_ACTIVE_AUTO, max_rhs=1,
+            inner_prec=_lib.DD_PREC_F16, block_prec=_lib.DD_PREC_F32, tol_global=1e-10,
+            tol_block=1e-12, tol_inner=1e-3, maxit=20000, stream=None, device=None):
+    """Create a handle and give it a torch-allocated workspace on `device`."""
+    lib = _lib.load()
+    p = dd_default_params()
+    for a in range(4):
+        p.dims[a] = int(dims[a])
+        p.block[a] = int(block[a])
+    p.kappa = float(kappa)
+    p.bc_time = int(bc_time)
+    p.active_mode = int(active_mode)
+    p.max_rhs = int(max_rhs)
+    p.inner_prec = int(inner_prec)
+    p.block_prec = int(block_prec)
+    p.tol_global = float(tol_global)
+    p.tol_block = float(tol_block)
+    p.tol_inner = float(tol_inner)
+    p.maxit = int(maxit)
+    device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    h = ctypes.c_void_p()
+    rc = lib.dd_init(ctypes.byref(h), ctypes.byref(p), ctypes.c_void_p(stream.cuda_stream))
+    if rc != _lib.DD_OK:
+        raise DDError(rc, "dd_init failed (check extents, blocks and parameters)")
+    size = ctypes.c_size_t()
+    _check(h, lib.dd_workspace_size(h, ctypes.byref(size)))
+    ws = torch.empty(size.value + 256, dtype=torch.uint8, device=device)
+    base = (ws.data_ptr() + 255) & ~255
+    _check(h, lib.dd_set_workspace(h, ctypes.c_void_p(base), ctypes.c_size_t(size.value)))
+    return Handle(h, p, ws, stream)
+
+
+def dd_get_maps(h):
+    """Host copies of the geometry tables as numpy arrays."""
+    import numpy as np
+    V = h.V
+    nbr = np.zeros(V * 8, dtype=np.int32)
+    sign = np.zeros(V * 8, dtype=np.int32)
+    order = np.zeros(V, dtype=np.int32)
+    blk = np.zeros(V, dtype=np.int32)
+    act = np.zeros(V * 4, dtype=np.uint8)
+    _check(h, _lib.load().dd_get_maps(h.ptr, nbr.ctypes.data, sign.ctypes.data, order.ctypes.data,
+                                      blk.ctypes.data, act.ctypes.data))
+    return {"nbr": nbr.reshape(V, 4, 2), "sign": sign.reshape(V, 4, 2), "dd_order": order,
+            "block_of": blk, "active": act.reshape(V, 4).astype(bool)}
+
+
+def dd_apply_D(h, out, inp, U, op=_lib.DD_OP_D, prec=_lib.DD_PREC_F64, nrhs=1):
+    return _check(h, _lib.load().dd_apply_D(h.ptr, _ptr(out), _ptr(inp), _ptr(U), int(op), int(prec), int(nrhs)))
+
+
+def dd_apply_D_block(h, out, inp, U, colour_mask=3, prec=_lib.DD_PREC_F64, nrhs=1):
+    return _check(h, _lib.load().dd_apply_D_block(h.ptr, _ptr(out), _ptr(inp), _ptr(U), int(colour_mask),
+                                                  int(prec), int(nrhs)))
+
+
+def dd_solve(h, x, b, U, nrhs=1, prec=_lib.DD_PREC_F64, check=True):
+    """Returns (total inner iterations, list of true relative residuals, rc)."""
+    import numpy as np
+    it = ctypes.c_int(0)
+    res = np.zeros(max(1, nrhs), dtype=np.float64)
+    rc = _lib.load().dd_solve(h.ptr, _ptr(x), _ptr(b), _ptr(U), int(nrhs), int(prec), ctypes.byref(it),
+                              res.ctypes.data)
+    if check:
+        _check(h, rc)
+    return it.value, res.tolist(), rc
+
+
+def dd_noise(h, eta, nrhs, purpose, seed, ctr):
+    return _check(h, _lib.load().dd_noise(h.ptr, _ptr(eta), int(nrhs), int(purpose), int(seed), int(ctr)))
+
+
+def dd_interpolate(h, Ut, U, Unew, i, n):
+    return _check(h, _lib.load().dd_interpolate(h.ptr, _ptr(Ut), _ptr(U), _ptr(Unew), int(i), int(n)))
+
+
+def dd_det_ratio_estimate(h, U_old, U_new, n, seed, ctr, mode=_lib.DD_EST_FACTORS, ln_out=None):
+    if ln_out is None:
+        ln_out = torch.zeros(n, dtype=torch.float64, device=h.workspace.device)
+    _check(h, _lib.load().dd_det_ratio_estimate(h.ptr, _ptr(U_old), _ptr(U_new), int(n), int(seed), int(ctr),
+                                                int(mode), _ptr(ln_out)))
+    return ln_out
+
+
+def dd_block_filter(h, U_old, U_new, colour_mask, mode, n, seed, ctr, ln_b=None, accept=None):
+    dev = h.workspace.device
+    if ln_b is None:
+        ln_b = torch.zeros(h.nblocks, dtype=torch.float64, device=dev)
+    if accept is None:
+        accept = torch.zeros(h.nblocks, dtype=torch.uint8, device=dev)
+    _check(h, _lib.load().dd_block_filter(h.ptr, _ptr(U_old), _ptr(U_new), int(colour_mask), int(mode), int(n),
+                                          int(seed), int(ctr), _ptr(ln_b), _ptr(accept)))
+    return ln_b, accept
+
+
+def dd_gauge_update(h, U, colour_mask, beta, n_hb, n_or, seed, ctr):
+    return _check(h, _lib.load().dd_gauge_update(h.ptr, _ptr(U), int(colour_mask), float(beta), int(n_hb),
+                                                 int(n_or), int(seed), int(ctr)))
+
+
+def dd_global_accept(h, U, U_old, ln_r, seed, ctr, accept=None, margin=None):
+    dev = h.workspace.device
+    if accept is None:
+        accept = torch.zeros(1, dtype=torch.uint8, device=dev)
+    if margin is None:
+        margin = torch.zeros(1, dtype=torch.float64, device=dev)
+    _check(h, _lib.load().dd_global_accept(h.ptr, _ptr(U), _ptr(U_old), _ptr(ln_r), int(ln_r.numel()), int(seed),
+                                           int(ctr), _ptr(accept), _ptr(margin)))
+    return accept, margin
+
+
+def dd_logdet_exact(h, U, which, out=None):
+    if out is None:
+        n = h.nblocks if which == 1 else 1
+        out = torch.zeros(n, dtype=torch.float64, device=h.workspace.device)
+    _check(h, _lib.load().dd_logdet_exact(h.ptr, _ptr(U), int(which), _ptr(out)))
+    return out
+
+
+def dd_plaquette(h, U, out=None):
+    if out is None:
+        out = torch.zeros(1, dtype=torch.float64, device=h.workspace.device)
+    _check(h, _lib.load().dd_plaquette(h.ptr, _ptr(U), _ptr(out)))
+    return out
+
+
+def dd_sync(h):
+    return _check(h, _lib.load().dd_sync(h.ptr))
+
+
+def dd_status(h):
+    st = ctypes.c_int(0)
+    hb = ctypes.c_longlong(0)
+    _check(h, _lib.load().dd_status(h.ptr, ctypes.byref(st), ctypes.byref(hb)))
+    return st.value, hb.value
+
+
+def dd_last_error(h):
+    m = _lib.load().dd_last_error(h.ptr)
+    return m.decode() if m else ""
+
+
+def dd_finalize(h):
+    if h.ptr:
+        rc = _lib.load().dd_finalize(h.ptr)
+        h.ptr = None
+        return rc
+    return 0

@@ -1,0 +1,363 @@
+// Batched Dirichlet block solves in one persistent launch (Eq. 4step step 1
+// and the block inverses A^{-1}, E^{-1} of the Schur complement, Eq. ddfactor).
+//
+// Every thread block of the grid takes work items (block, factor) from an
+// atomic queue and runs a complete solve of D_b x = src for that item with
+// the whole thread block: FP64 defect correction around an inner CG on the
+// block's normal equations (FP32 arithmetic on FP32 storage, or FP64), all
+// vectors in a per-thread-block scratch slot laid out block-local and
+// chunk-major (coalesced, L2-resident for blocks up to 8^4 sites).
+//
+// D_b = 1 - kappa * H restricted to hops with both ends in block b (Dirichlet
+// boundary: hops leaving the block are dropped).  Blocks never straddle the
+// time edge (at least two blocks per direction), so no boundary phase occurs
+// inside a block.  Block data (links, vectors) are stored in block order:
+// position q = block_pos * bsites + local index, local index lexicographic.
+#pragma once
+
+#include "dd_internal.h"
+#include "reduce.cuh"
+
+struct BlockCtx {
+    int bd[4];    // block extents
+    int st[4];    // local strides
+    int nb;       // sites per block
+    double kappa;
+};
+
+DD_DEV void local_coords(const BlockCtx& c, int j, int l[4]) {
+    l[0] = j % c.bd[0];
+    int r = j / c.bd[0];
+    l[1] = r % c.bd[1];
+    r /= c.bd[1];
+    l[2] = r % c.bd[2];
+    l[3] = r / c.bd[2];
+}
+
+// acc = H_b in at local site j (hops inside the block only)
+template <class R, class SIn, class LK>
+DD_DEV void dirichlet_hop(const BlockCtx& c, int j, const SIn& in, const LK& lk, int g5in, Spinor<R>& acc) {
+    int l[4];
+    local_coords(c, j, l);
+    zero(acc);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        if (l[a] < c.bd[a] - 1) {
+            int jn = j + c.st[a];
+            Spinor<R> s;
+            in.load(jn, s);
+            if (g5in) gamma5(s);
+            Half<R> hf, uh;
+            project<R>(a, +1, s, hf);
+            Link<R> u;
+            lk.load(j, a, u);
+            mul_link(u, hf, uh);
+            accumulate<R>(a, +1, uh, (R)1, acc);
+        }
+        if (l[a] > 0) {
+            int jn = j - c.st[a];
+            Spinor<R> s;
+            in.load(jn, s);
+            if (g5in) gamma5(s);
+            Half<R> hf, uh;
+            project<R>(a, -1, s, hf);
+            Link<R> u;
+            lk.load(jn, a, u);
+            mul_link_dag(u, hf, uh);
+            accumulate<R>(a, -1, uh, (R)1, acc);
+        }
+    }
+}
+
+// out = D_b in (dag: gamma5 D_b gamma5); returns this thread's |out|^2 (block-reduce it)
+template <class R, class SIn, class SOut, class LK>
+DD_DEV double dirichlet_apply(const BlockCtx& c, const SIn& in, const SOut& out, const LK& lk, int dag) {
+    double n2 = 0.0;
+    for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+        Spinor<R> acc, v;
+        dirichlet_hop<R>(c, j, in, lk, dag, acc);
+        in.load(j, v);
+        if (dag) gamma5(v);
+        const R mk_ = (R)(-c.kappa);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v.c[k] = v.c[k] + mk_ * acc.c[k];
+        if (dag) gamma5(v);
+        out.store(j, v);
+        n2 += (double)snorm2(v);
+    }
+    return n2;
+}
+
+// Inner CG on the normal equations D_b^dag D_b x = D_b^dag r0 (x starts at 0,
+// r holds r0 on entry).  Stops when |r|^2 <= tol2rel |r0|^2 or after maxit.
+template <class R, class S, class LK>
+DD_DEV int block_cgnr(const BlockCtx& c, const S& x, const S& r, const S& p, const S& q, const S& z, const LK& lk,
+                      double tol2rel, int maxit, double* sh) {
+    double rr0 = 0.0;
+    for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+        Spinor<R> zz;
+        zero(zz);
+        x.store(j, zz);
+        Spinor<R> v;
+        r.load(j, v);
+        rr0 += (double)snorm2(v);
+    }
+    rr0 = block_sum(rr0, sh);  // includes a barrier: r and x complete
+    if (!(rr0 > 0.0)) return 0;
+    double zz = block_sum(dirichlet_apply<R>(c, r, z, lk, 1), sh);
+    for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+        Spinor<R> v;
+        z.load(j, v);
+        p.store(j, v);
+    }
+    __syncthreads();
+    const double target = tol2rel * rr0;
+    int it = 0;
+    while (it < maxit) {
+        double qq = block_sum(dirichlet_apply<R>(c, p, q, lk, 0), sh);
+        if (!(qq > 0.0)) break;
+        const R alpha = (R)(zz / qq);
+        double rr = 0.0;
+        for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+            Spinor<R> a, b;
+            x.load(j, a);
+            p.load(j, b);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) a.c[k] = a.c[k] + alpha * b.c[k];
+            x.store(j, a);
+            r.load(j, a);
+            q.load(j, b);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) a.c[k] = a.c[k] - alpha * b.c[k];
+            r.store(j, a);
+            rr += (double)snorm2(a);
+        }
+        rr = block_sum(rr, sh);
+        ++it;
+        if (rr <= target) break;
+        double zn = block_sum(dirichlet_apply<R>(c, r, z, lk, 1), sh);
+        const R beta = (R)(zn / zz);
+        zz = zn;
+        for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+            Spinor<R> a, b;
+            z.load(j, a);
+            p.load(j, b);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) a.c[k] = a.c[k] + beta * b.c[k];
+            p.store(j, a);
+        }
+        __syncthreads();
+    }
+    return it;
+}
+
+// ----------------------------------------------------------- the launch
+enum BlockMode { BLOCK_FILTER = 0, BLOCK_SOLVE = 1 };
+
+struct BlockItem {
+    int block_pos;  // position of the block in block order
+    int f_src;      // field slot of the source operator (filter) / unused
+    int f_sol;      // field slot of the solve
+    int vec;        // factor index (noise sub) / vector index in the banks
+};
+
+struct BlockArgs {
+    Geo g;
+    BlockCtx c;
+    int mode;
+    const BlockItem* items;
+    int nitems;
+    int* queue;
+    const double2* dd64;  // field slot 0, FP64 links in block order
+    long long dd64_fs;    // elements between consecutive field slots
+    const float4* dd32;
+    long long dd32_fs;
+    const double2* in_bank;  // BLOCK_SOLVE right-hand sides (block order, FP64)
+    double2* out_bank;       // BLOCK_SOLVE solutions
+    long long bank_vs;       // elements between consecutive vectors of a bank
+    double* item_out;        // BLOCK_FILTER: -(2 Re<eta, d> + |d|^2) per item
+    char* scratch;
+    long long slot_bytes;
+    uint64_t seed, ctr;
+    int purpose;
+    double tol2;       // relative target of the FP64 residual (squared)
+    double tol2_inner; // relative target of one inner solve (squared)
+    int maxit_inner;
+    int max_outer;
+    int inner_f64;
+    int* status;
+};
+
+// block id of the block at position pos of the block order
+DD_DEV int block_id_at(const Geo& g, int pos, int* colour) {
+    int half = g.nblocks / 2;
+    int col = pos >= half ? 1 : 0;
+    int rank = pos - col * half;
+    int id = 2 * rank;
+    int B1 = (id / g.nbk[0]) % g.nbk[1], B2 = (id / (g.nbk[0] * g.nbk[1])) % g.nbk[2],
+        B3 = id / (g.nbk[0] * g.nbk[1] * g.nbk[2]);
+    if (((B1 + B2 + B3) & 1) != col) id += 1;
+    *colour = col;
+    return id;
+}
+DD_DEV void block_origin(const Geo& g, int id, int o[4]) {
+    o[0] = (id % g.nbk[0]) * g.b[0];
+    int r = id / g.nbk[0];
+    o[1] = (r % g.nbk[1]) * g.b[1];
+    r /= g.nbk[1];
+    o[2] = (r % g.nbk[2]) * g.b[2];
+    o[3] = (r / g.nbk[2]) * g.b[3];
+}
+
+template <class LK>
+DD_DEV LK make_inner_links(const BlockArgs& A, int f, int pos);
+template <>
+DD_DEV LinkF32 make_inner_links<LinkF32>(const BlockArgs& A, int f, int pos) {
+    return LinkF32{A.dd32 + (long long)f * A.dd32_fs + (long long)pos * 4 * 3 * A.c.nb, A.c.nb};
+}
+template <>
+DD_DEV LinkF64 make_inner_links<LinkF64>(const BlockArgs& A, int f, int pos) {
+    return LinkF64{A.dd64 + (long long)f * A.dd64_fs + (long long)pos * 4 * 9 * A.c.nb, A.c.nb};
+}
+template <class S>
+DD_DEV S scratch_spinor(char* base, int index, long long nb);
+template <>
+DD_DEV SpinorF32 scratch_spinor<SpinorF32>(char* base, int index, long long nb) {
+    return SpinorF32{(float4*)base + (long long)index * 6 * nb, nb};
+}
+template <>
+DD_DEV SpinorF64 scratch_spinor<SpinorF64>(char* base, int index, long long nb) {
+    return SpinorF64{(double2*)base + (long long)index * 12 * nb, nb};
+}
+
+template <class RI, class SI, class LKI>
+__global__ void __launch_bounds__(256) block_solve_kernel(BlockArgs A) {
+    __shared__ double sh[34];
+    __shared__ int s_item;
+    const BlockCtx& c = A.c;
+    const long long nb = c.nb;
+    // scratch slot of this thread block: FP64 vectors eta, b, x, r; inner vectors x, r, p, q, z
+    char* base = A.scratch + (long long)blockIdx.x * A.slot_bytes;
+    SpinorF64 eta{(double2*)base, nb};
+    SpinorF64 bv{(double2*)base + 12 * nb, nb};
+    SpinorF64 xv{(double2*)base + 24 * nb, nb};
+    SpinorF64 rv{(double2*)base + 36 * nb, nb};
+    char* ib = base + 48 * nb * sizeof(double2);
+    SI xi = scratch_spinor<SI>(ib, 0, nb), ri = scratch_spinor<SI>(ib, 1, nb), pi = scratch_spinor<SI>(ib, 2, nb),
+       qi = scratch_spinor<SI>(ib, 3, nb), zi = scratch_spinor<SI>(ib, 4, nb);
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(A.queue, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= A.nitems) break;
+        const BlockItem it = A.items[item];
+        LinkF64 lsol{A.dd64 + (long long)it.f_sol * A.dd64_fs + (long long)it.block_pos * 4 * 9 * nb, nb};
+        LKI lsoli = make_inner_links<LKI>(A, it.f_sol, it.block_pos);
+        int colour;
+        int id = block_id_at(A.g, it.block_pos, &colour);
+        int org[4];
+        block_origin(A.g, id, org);
+        // ---- right-hand side
+        if (A.mode == BLOCK_FILTER) {
+            LinkF64 lsrc{A.dd64 + (long long)it.f_src * A.dd64_fs + (long long)it.block_pos * 4 * 9 * nb, nb};
+            for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+                int l[4];
+                local_coords(c, j, l);
+                int x[4] = {org[0] + l[0], org[1] + l[1], org[2] + l[2], org[3] + l[3]};
+                uint32_t s = (uint32_t)canon_index(A.g, x);
+                Spinor<double> e;
+#pragma unroll
+                for (int k = 0; k < 12; ++k) e.c[k] = gaussian(s * 12u + k, (uint32_t)A.purpose, (uint32_t)it.vec, A.seed, A.ctr);
+                eta.store(j, e);
+            }
+            __syncthreads();
+            // b = (D_b[src] - D_b[sol]) eta = -kappa (H[src] - H[sol]) eta
+            for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+                Spinor<double> h1, h2;
+                dirichlet_hop<double>(c, j, eta, lsrc, 0, h1);
+                dirichlet_hop<double>(c, j, eta, lsol, 0, h2);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) h1.c[k] = (-c.kappa) * (h1.c[k] - h2.c[k]);
+                bv.store(j, h1);
+            }
+        } else {
+            SpinorF64 src{(double2*)A.in_bank + (long long)it.vec * A.bank_vs + (long long)it.block_pos * 12 * nb, nb};
+            for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+                Spinor<double> v;
+                src.load(j, v);
+                bv.store(j, v);
+            }
+        }
+        // ---- x = 0, r = b
+        double bb = 0.0;
+        for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+            Spinor<double> v, z;
+            bv.load(j, v);
+            rv.store(j, v);
+            zero(z);
+            xv.store(j, z);
+            bb += snorm2(v);
+        }
+        bb = block_sum(bb, sh);
+        double rr = bb;
+        int outer = 0;
+        while (rr > A.tol2 * bb && outer < A.max_outer) {
+            // inner right-hand side: the FP64 residual
+            for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+                Spinor<RI> v;
+                rv.load(j, v);
+                ri.store(j, v);
+            }
+            __syncthreads();
+            block_cgnr<RI>(c, xi, ri, pi, qi, zi, lsoli, A.tol2_inner, A.maxit_inner, sh);
+            // x += e; r = b - D_b x (FP64)
+            for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+                Spinor<double> a;
+                Spinor<RI> e;
+                xv.load(j, a);
+                xi.load(j, e);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) a.c[k] = a.c[k] + mk<double>((double)e.c[k].x, (double)e.c[k].y);
+                xv.store(j, a);
+            }
+            __syncthreads();
+            rr = 0.0;
+            for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+                Spinor<double> acc, v, b;
+                dirichlet_hop<double>(c, j, xv, lsol, 0, acc);
+                xv.load(j, v);
+                bv.load(j, b);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) b.c[k] = b.c[k] - (v.c[k] + (-c.kappa) * acc.c[k]);
+                rv.store(j, b);
+                rr += snorm2(b);
+            }
+            rr = block_sum(rr, sh);
+            ++outer;
+        }
+        if (rr > A.tol2 * bb && threadIdx.x == 0) raise_status(A.status, DD_ERR_NOT_CONVERGED);
+        if (!isfinite(rr) && threadIdx.x == 0) raise_status(A.status, DD_ERR_NUMERIC);
+        // ---- results
+        if (A.mode == BLOCK_FILTER) {
+            double s = 0.0;
+            for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+                Spinor<double> e, d;
+                eta.load(j, e);
+                xv.load(j, d);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) s += 2.0 * (e.c[k].x * d.c[k].x + e.c[k].y * d.c[k].y) + norm2(d.c[k]);
+            }
+            s = block_sum(s, sh);
+            if (threadIdx.x == 0) A.item_out[item] = -s;
+        } else {
+            SpinorF64 dst{A.out_bank + (long long)it.vec * A.bank_vs + (long long)it.block_pos * 12 * nb, nb};
+            for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+                Spinor<double> v;
+                xv.load(j, v);
+                dst.store(j, v);
+            }
+        }
+        __syncthreads();
+    }
+}

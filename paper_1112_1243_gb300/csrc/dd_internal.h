@@ -1,0 +1,146 @@
+// Host-side handle and workspace plan of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dd.h"
+#include "dd_common.cuh"
+
+// Per-system state of a batched Krylov solve, kept in device memory so that
+// iterations run without host round trips.
+struct CGState {
+    double zz;     // |z|^2 = |A^dag r|^2
+    double qq;     // |A p|^2
+    double rr;     // |r|^2
+    double alpha;  // step length
+    double beta;   // direction update
+    double tol2;   // stop when rr <= tol2
+    int active;    // 1 while iterating
+    int iters;     // iterations done
+    int maxit;     // cap
+    int flags;     // bit 0: hit maxit, bit 1: non-finite
+};
+
+// reduction finishers run by the last thread block of a reduction
+enum FinOp { FIN_NONE = 0, FIN_STORE = 1, FIN_ALPHA = 2, FIN_RR = 3, FIN_BETA = 4, FIN_ZZ_INIT = 5 };
+
+struct Reduce {
+    double* partials;     // [rhs][gridDim.x]
+    unsigned* counters;   // [rhs]
+    CGState* st;          // [rhs] (FIN_ALPHA / RR / BETA / ZZ_INIT)
+    double* out;          // [rhs] (FIN_STORE)
+    int op;
+    int* status;
+};
+
+// One formatted copy of a gauge field.
+struct FieldSlot {
+    double2* eo64;   // eo layout, FP64, 9 chunks, [parity][dir][chunk][Vh]
+    float4* eo32;    // eo layout, FP32 rows 0-1, 3 chunks
+    uint2* eo16;     // eo layout, FP16 rows 0-1, 3 chunks
+    double2* dd64;   // block order, FP64 [blockpos][dir][chunk][bsites]
+    float4* dd32;    // block order, FP32 rows 0-1
+    double2* canon;  // canonical FP64 copy (interpolated fields)
+};
+
+// Vectors of one right-hand side of the global solver (eo layout, Vh sites).
+struct SolverVecs {
+    double2* be;   // FP64 even part of b (and b-tilde)
+    double2* bo;   // FP64 odd part of b
+    double2* xe;   // FP64 even solution
+    double2* xo;   // FP64 odd solution
+    double2* re;   // FP64 residual
+    double2* t64;  // FP64 temporary (odd)
+    double2* t64b; // FP64 temporary (even)
+    double2* x64;  // FP64 inner vectors of the plain FP64 solver
+    double2* p64;
+    double2* q64;
+    double2* z64;
+    float4* x32;   // inner solution (correction)
+    float4* r32;
+    float4* p32;
+    float4* q32;
+    float4* z32;
+    float4* t32;   // odd temporary (hop output)
+    uint4* p16;    // FP16 hop copies + scales
+    float* p16n;
+    uint4* r16;
+    float* r16n;
+    uint4* t16;
+    float* t16n;
+    uint4* q16;
+    float* q16n;
+};
+
+struct dd_handle {
+    dd_params prm;
+    Geo g;
+    cudaStream_t stream;
+    int n_active;                    // number of active links
+    // device tables owned by the handle
+    int* d_active_links = nullptr;   // canonical link indices 4*s + a of the active set, grouped
+    std::vector<int> h_group_off;    // offsets of (colour, dir, parity) groups in d_active_links (17 entries)
+    uint8_t* d_active_mask = nullptr;  // [V*4]
+    int* d_status = nullptr;           // device status word
+    unsigned long long* d_hb_fails = nullptr;
+    // workspace
+    char* ws = nullptr;
+    size_t ws_size = 0;
+    size_t ws_needed = 0;
+    std::vector<FieldSlot> fields;   // max_rhs + 1 slots
+    std::vector<SolverVecs> vecs;    // max_rhs systems
+    double2* dd_vec = nullptr;       // block-ordered FP64 vectors: [6][max_rhs][12][V]
+    CGState* d_cg = nullptr;         // [2 * max_rhs]
+    double* d_partials = nullptr;    // reduction partials
+    unsigned* d_counters = nullptr;  // reduction tickets
+    size_t partials_cap = 0;
+    double* d_scalars = nullptr;     // scratch doubles [64 * max_rhs]
+    char* block_scratch = nullptr;   // persistent block-solver slots
+    size_t block_slot_bytes = 0;
+    int block_slots = 0;
+    double* d_item_out = nullptr;    // per-item results of the block kernel
+    int* d_items = nullptr;          // item descriptors
+    int* d_queue = nullptr;          // work-queue head
+    int* d_imap = nullptr;           // small index maps: [nblocks] item bases, [2*max_rhs] field slots
+    int items_cap = 0;
+    double* d_lu = nullptr;          // dense matrices for the exact path
+    size_t lu_bytes = 0;
+    std::string last_error;
+    int num_sms = 0;
+};
+
+// error plumbing
+int dd_fail(dd_handle* h, int code, const std::string& msg);
+int dd_cuda_check(dd_handle* h, cudaError_t e, const char* where);
+#define DD_CUDA(h, call)                                        \
+    do {                                                        \
+        cudaError_t _e = (call);                                \
+        if (_e != cudaSuccess) return dd_cuda_check(h, _e, #call); \
+    } while (0)
+#define DD_LAUNCH_CHECK(h, what)                                    \
+    do {                                                            \
+        cudaError_t _e = cudaGetLastError();                        \
+        if (_e != cudaSuccess) return dd_cuda_check(h, _e, what);   \
+    } while (0)
+
+int dd_require_ws(dd_handle* h);
+
+// exact block log-determinant ratios of the block filter (lu.cu)
+int block_filter_exact(dd_handle* h, const double* U_old, const double* U_new, int colour_mask, double* ln_b);
+
+// shared launch helpers (defined in lattice.cu / solver.cu)
+inline int grid_for(long long n, int threads) { return (int)((n + threads - 1) / threads); }
+
+// field formatting (lattice.cu)
+int format_field(dd_handle* h, const double* U, FieldSlot& f, bool eo64, bool eo32, bool eo16, bool dd64, bool dd32);
+// spinor packing between canonical FP64 and eo FP64 (lattice.cu)
+void launch_pack_spinor_eo(dd_handle* h, const double* in, double2* out, int parity, int nrhs, long long in_rhs_stride);
+void launch_unpack_spinor_eo(dd_handle* h, const double2* in, double* out, int parity, int nrhs, long long out_rhs_stride);
+void launch_pack_spinor_dd(dd_handle* h, const double* in, double2* out, int nrhs);
+void launch_pack_spinor_sub(dd_handle* h, const double* in, double2* out, int nrhs);
+void launch_unpack_spinor_sub(dd_handle* h, const double2* in, double* out, int nrhs);
+void launch_unpack_spinor_dd(dd_handle* h, const double2* in, double* out, int nrhs);

@@ -1,0 +1,141 @@
+// Even-odd Wilson hopping kernel (Sec. 5 "plain Wilson-Dirac"; Eq. domdec
+// for the intra-/inter-block restrictions).
+//
+// One thread per output site of parity p:
+//   out(x) = a * xin(x) + b * G5out( sum_hops (1 -+ gamma_a) U psi(x +- a) ),
+// psi read from the opposite parity, optionally gamma5-multiplied on load.
+// MASK = 0: all hops; 1: hops inside a block only (Dirichlet D_b); 2: only
+// hops that cross a block face (D_bw, D_wb).  Links are stored per parity:
+// the forward hop of x uses U_a(x) (parity p), the backward hop the link
+// U_a(x - a) stored at the neighbour (parity 1 - p).
+#pragma once
+
+#include "dd_internal.h"
+#include "reduce.cuh"
+
+// per-rhs shifted copies of storage descriptors (contiguous per-rhs blocks)
+DD_DEV SpinorF64 at_rhs(SpinorF64 s, int r) {
+    s.p += (long long)r * 12 * s.stride;
+    return s;
+}
+DD_DEV SpinorF32 at_rhs(SpinorF32 s, int r) {
+    s.p += (long long)r * 6 * s.stride;
+    return s;
+}
+DD_DEV SpinorF16 at_rhs(SpinorF16 s, int r) {
+    s.p += (long long)r * 3 * s.stride;
+    s.nrm += (long long)r * s.stride;
+    return s;
+}
+
+template <class SIn, class SX, class SOut, class LK>
+struct HopArgs {
+    Geo g;
+    int p;                    // output parity
+    SIn in;                   // input field (parity 1 - p)
+    SX xin;                   // a * xin term (parity p), used when has_x
+    SOut out;                 // output (parity p)
+    LK lk;                    // gauge field, both parities: [parity][dir][chunk][Vh]
+    long long lk_rhs_stride;  // elements between the fields of consecutive rhs (0: shared)
+    double a, b;
+    int has_x;
+    int g5in, g5out;
+    int colour_mask;          // 3 = every site; else zero the output outside these block colours
+    const CGState* st;        // per-rhs activity (may be null)
+    Reduce red;               // |out|^2 reduction (red.op == FIN_NONE: off)
+};
+
+template <class LK>
+DD_DEV LK link_parity(LK lk, int par, long long Vh) {
+    lk.p += (long long)par * 4 * LK::chunks * Vh;
+    return lk;
+}
+
+template <class R, class SIn, class LK, int MASK>
+DD_DEV void hop_site(const Geo& g, int p, int h, const int x[4], const SIn& in, const LK& lk_p, const LK& lk_q,
+                     int g5in, Spinor<R>& acc) {
+    zero(acc);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        int loc = x[a] % g.b[a];
+        // forward: (1 - gamma_a) U_a(x) psi(x + a)
+        bool okf = true, okb = true;
+        if (MASK == 1) {
+            okf = loc != g.b[a] - 1;
+            okb = loc != 0;
+        } else if (MASK == 2) {
+            okf = loc == g.b[a] - 1;
+            okb = loc == 0;
+        }
+        if (okf) {
+            int yh = shift_index(g, x, a, +1) >> 1;
+            Spinor<R> s;
+            in.load(yh, s);
+            if (g5in) gamma5(s);
+            Half<R> hf, uh;
+            project<R>(a, +1, s, hf);
+            Link<R> u;
+            lk_p.load(h, a, u);
+            mul_link(u, hf, uh);
+            R sc = (a == 3 && x[3] == g.L[3] - 1) ? (R)g.bc : (R)1;
+            accumulate<R>(a, +1, uh, sc, acc);
+        }
+        if (okb) {
+            int yh = shift_index(g, x, a, -1) >> 1;
+            Spinor<R> s;
+            in.load(yh, s);
+            if (g5in) gamma5(s);
+            Half<R> hf, uh;
+            project<R>(a, -1, s, hf);
+            Link<R> u;
+            lk_q.load(yh, a, u);
+            mul_link_dag(u, hf, uh);
+            R sc = (a == 3 && x[3] == 0) ? (R)g.bc : (R)1;
+            accumulate<R>(a, -1, uh, sc, acc);
+        }
+    }
+}
+
+template <class R, class SIn, class SX, class SOut, class LK, int MASK>
+__global__ void __launch_bounds__(128) hop_eo_kernel(HopArgs<SIn, SX, SOut, LK> A) {
+    __shared__ double sh[34];
+    const int rhs = blockIdx.y;
+    if (A.st && !A.st[rhs].active) return;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long Vh = A.g.Vh;
+    double nrm = 0.0;
+    if (h < A.g.Vh) {
+        SIn in = at_rhs(A.in, rhs);
+        LK lk = A.lk;
+        lk.p += (long long)rhs * A.lk_rhs_stride;
+        LK lk_p = link_parity(lk, A.p, Vh);
+        LK lk_q = link_parity(lk, 1 - A.p, Vh);
+        int x[4];
+        eo_coords(A.g, A.p, h, x);
+        Spinor<R> acc;
+        hop_site<R, SIn, LK, MASK>(A.g, A.p, h, x, in, lk_p, lk_q, A.g5in, acc);
+        if (A.g5out) gamma5(acc);
+        Spinor<R> res;
+        const R bb = (R)A.b;
+        if (A.has_x) {
+            Spinor<R> xv;
+            at_rhs(A.xin, rhs).load(h, xv);
+            const R aa = (R)A.a;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) res.c[k] = aa * xv.c[k] + bb * acc.c[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) res.c[k] = bb * acc.c[k];
+        }
+        if (A.colour_mask != 3 && !((A.colour_mask >> block_colour_of(A.g, x)) & 1)) zero(res);
+        at_rhs(A.out, rhs).store(h, res);
+        nrm = (double)snorm2(res);
+    }
+    if (A.red.op != FIN_NONE) grid_reduce(A.red, rhs, nrm, sh);
+}
+
+template <class R, class SIn, class SX, class SOut, class LK, int MASK>
+inline void launch_hop(const HopArgs<SIn, SX, SOut, LK>& A, int nrhs, cudaStream_t s) {
+    dim3 grid(grid_for(A.g.Vh, 128), nrhs);
+    hop_eo_kernel<R, SIn, SX, SOut, LK, MASK><<<grid, 128, 0, s>>>(A);
+}

@@ -1,0 +1,448 @@
+// Stochastic determinant-ratio estimates and acceptance steps.
+//
+// Global step (Eq. 4step step 3, Sec. 4): with M_i = Dhat[U_{i+1}]^{-1}
+// Dhat[U_i] and a fresh complex Gaussian eta_i on the black sites per factor
+// (Eq. param), ln r_i = -eta^dag (M^dag M - 1) eta = -(2 Re<eta, d> + |d|^2),
+// d = (M - 1) eta.  Using Dhat'^{-1} = (D'^{-1})_bb A' (block inverse of
+// Eq. domdec) and A'(Dhat - Dhat') = B'E'^{-1}C' - A'A^{-1}BE^{-1}C:
+//   w = C eta, w' = C' eta            (inter-block hops, black -> white)
+//   z = E^{-1} w, z' = E'^{-1} w'     (white Dirichlet block solves)
+//   v = B z, v' = B' z'               (inter-block hops, white -> black)
+//   a = A^{-1} v                      (black Dirichlet block solves)
+//   s = v' - A' a                     (black Dirichlet apply)
+//   y = D'^{-1} (s, 0),  d = y_black  (global solve)
+// All factors are processed as one batch: one launch per stage.
+//
+// Block filter (Eq. 4step step 1; Sec. 5): per block and factor
+//   d = D_b[U_{i+1}]^{-1} (D_b[U_i] - D_b[U_{i+1}]) eta_{b,i},
+//   ln r_b = sum_i -(2 Re<eta, d> + |d|^2), accept iff ln u_b < ln r_b.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "blocksolve.cuh"
+#include "dslash.cuh"
+#include "solver.h"
+
+int launch_interpolate(dd_handle* h, const double* U, const double* Up, double* out, int num, int den);
+
+namespace {
+
+// canonical coordinates of block-order position q
+DD_DEV void dd_coords(const Geo& g, const BlockCtx& c, long long q, int x[4], int* colour) {
+    int pos = (int)(q / c.nb), j = (int)(q % c.nb);
+    int id = block_id_at(g, pos, colour);
+    int o[4], l[4];
+    block_origin(g, id, o);
+    local_coords(c, j, l);
+    for (int a = 0; a < 4; ++a) x[a] = o[a] + l[a];
+}
+
+// eta on the black sites (purpose / sub), 0 on white; block order
+__global__ void noise_black_kernel(Geo g, BlockCtx c, double2* bank, long long vs, int purpose, uint64_t seed,
+                                   uint64_t ctr) {
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y;
+    if (q >= g.V) return;
+    int x[4], col;
+    dd_coords(g, c, q, x, &col);
+    long long pos = q / c.nb, j = q % c.nb;
+    SpinorF64 out{bank + (long long)i * vs + pos * 12 * c.nb, c.nb};
+    Spinor<double> e;
+    uint32_t s = (uint32_t)canon_index(g, x);
+    if (col == 0) {
+        for (int k = 0; k < 12; ++k) e.c[k] = gaussian(s * 12u + k, (uint32_t)purpose, (uint32_t)i, seed, ctr);
+    } else {
+        zero(e);
+    }
+    out.store(j, e);
+}
+
+// out = -kappa * (hops that cross block faces) in, on the sites of colour
+// `target` (0 elsewhere).  Links from the canonical FP64 copy of the field.
+__global__ void inter_hop_kernel(Geo g, BlockCtx c, const double2* in_bank, double2* out_bank, long long vs,
+                                 const double* canon0, long long canon_fs, const int* field_of, int target) {
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y;
+    if (q >= g.V) return;
+    const double* U = canon0 + (long long)field_of[i] * canon_fs;
+    int x[4], col;
+    dd_coords(g, c, q, x, &col);
+    long long pos = q / c.nb, j = q % c.nb;
+    Spinor<double> acc;
+    zero(acc);
+    if (col == target) {
+        const int s = canon_index(g, x);
+        const int bid = block_id_of(g, x);
+        for (int a = 0; a < 4; ++a) {
+            for (int dir = +1; dir >= -1; dir -= 2) {
+                int y[4] = {x[0], x[1], x[2], x[3]};
+                y[a] += dir;
+                if (y[a] == g.L[a]) y[a] = 0;
+                if (y[a] < 0) y[a] = g.L[a] - 1;
+                if (block_id_of(g, y) == bid) continue;
+                long long qy = dd_position(g, y);
+                SpinorF64 src{(double2*)in_bank + (long long)i * vs + (qy / c.nb) * 12 * c.nb, c.nb};
+                Spinor<double> sp;
+                src.load(qy % c.nb, sp);
+                Half<double> hf, uh;
+                project<double>(a, dir, sp, hf);
+                Link<double> u;
+                const int ys = canon_index(g, y);
+                const double* lp = U + ((long long)(dir > 0 ? s : ys) * 4 + a) * 18;
+                for (int k = 0; k < 9; ++k) u.m[k / 3][k % 3] = mk<double>(lp[2 * k], lp[2 * k + 1]);
+                if (dir > 0)
+                    mul_link(u, hf, uh);
+                else
+                    mul_link_dag(u, hf, uh);
+                double sc = 1.0;
+                if (a == 3 && ((dir > 0 && x[3] == g.L[3] - 1) || (dir < 0 && x[3] == 0))) sc = g.bc;
+                accumulate<double>(a, dir, uh, sc, acc);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc.c[k] = (-c.kappa) * acc.c[k];
+    }
+    SpinorF64 dst{out_bank + (long long)i * vs + pos * 12 * c.nb, c.nb};
+    dst.store(j, acc);
+}
+
+// out = v - D_b[field] a on black sites, 0 on white (block order)
+__global__ void schur_source_kernel(Geo g, BlockCtx c, const double2* v_bank, const double2* a_bank,
+                                    double2* out_bank, long long vs, const double2* dd64, long long fs,
+                                    const int* field_of) {
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y;
+    if (q >= g.V) return;
+    long long pos = q / c.nb;
+    int j = (int)(q % c.nb);
+    SpinorF64 dst{out_bank + (long long)i * vs + pos * 12 * c.nb, c.nb};
+    Spinor<double> r;
+    if (pos < g.nblocks / 2) {
+        SpinorF64 av{(double2*)a_bank + (long long)i * vs + pos * 12 * c.nb, c.nb};
+        SpinorF64 vv{(double2*)v_bank + (long long)i * vs + pos * 12 * c.nb, c.nb};
+        LinkF64 lk{dd64 + (long long)field_of[i] * fs + pos * 4 * 9 * c.nb, c.nb};
+        Spinor<double> acc, a;
+        dirichlet_hop<double>(c, j, av, lk, 0, acc);
+        av.load(j, a);
+        vv.load(j, r);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) r.c[k] = r.c[k] - (a.c[k] + (-c.kappa) * acc.c[k]);
+    } else {
+        zero(r);
+    }
+    dst.store(j, r);
+}
+
+// block order (FP64) -> eo FP64 chunks of the global solver
+__global__ void dd_to_eo_kernel(Geo g, BlockCtx c, const double2* bank, long long vs, double2* be, double2* bo) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y;
+    if (s >= g.V) return;
+    int x[4];
+    canon_coords(g, s, x);
+    long long q = dd_position(g, x);
+    SpinorF64 src{(double2*)bank + (long long)i * vs + (q / c.nb) * 12 * c.nb, c.nb};
+    Spinor<double> v;
+    src.load(q % c.nb, v);
+    const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+    SpinorF64 dst{(par ? bo : be) + (long long)i * 12 * g.Vh, g.Vh};
+    dst.store(s >> 1, v);
+}
+
+// ln_i = -sum_black (2 Re<eta, d> + |d|^2), d from the eo solution
+__global__ void __launch_bounds__(128) estimate_kernel(Geo g, BlockCtx c, const double2* eta_bank, long long vs,
+                                                       const double2* xe, const double2* xo, Reduce red) {
+    __shared__ double sh[34];
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y;
+    double acc = 0.0;
+    if (q < g.V / 2) {  // black sites come first in block order
+        int x[4], col;
+        dd_coords(g, c, q, x, &col);
+        SpinorF64 es{(double2*)eta_bank + (long long)i * vs + (q / c.nb) * 12 * c.nb, c.nb};
+        Spinor<double> e, d;
+        es.load(q % c.nb, e);
+        const int s = canon_index(g, x);
+        const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+        SpinorF64 ds{(double2*)(par ? xo : xe) + (long long)i * 12 * g.Vh, g.Vh};
+        ds.load(s >> 1, d);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc += 2.0 * (e.c[k].x * d.c[k].x + e.c[k].y * d.c[k].y) + norm2(d.c[k]);
+        acc = -acc;
+    }
+    grid_reduce(red, i, acc, sh);
+}
+
+__global__ void sum_items_kernel(int nblocks, const int* item_base, int n, const double* item_out, double* ln_b) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nblocks) return;
+    int base = item_base[b];
+    double s = 0.0;
+    if (base >= 0)
+        for (int i = 0; i < n; ++i) s += item_out[base + i];
+    ln_b[b] = s;
+}
+
+__global__ void block_accept_kernel(Geo g, int colour_mask, const double* ln_b, uint8_t* accept, uint64_t seed,
+                                    uint64_t ctr) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= g.nblocks) return;
+    int B[4] = {b % g.nbk[0], (b / g.nbk[0]) % g.nbk[1], (b / (g.nbk[0] * g.nbk[1])) % g.nbk[2],
+                b / (g.nbk[0] * g.nbk[1] * g.nbk[2])};
+    int col = (B[0] + B[1] + B[2] + B[3]) & 1;
+    if (!((colour_mask >> col) & 1)) {
+        accept[b] = 1;
+        return;
+    }
+    double u1, u2;
+    uniform_pair((uint32_t)b, DD_PURPOSE_BLOCK_ACCEPT, 0u, seed, ctr, u1, u2);
+    accept[b] = log(u1) < ln_b[b] ? 1 : 0;
+}
+
+__global__ void restore_kernel(Geo g, int n, const int* links, const uint8_t* accept, const double* U_old,
+                               double* U_new) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int l = links[k];
+    int s = l >> 2;
+    int x[4];
+    canon_coords(g, s, x);
+    if (accept[block_id_of(g, x)]) return;
+    for (int e = 0; e < 18; ++e) U_new[(long long)l * 18 + e] = U_old[(long long)l * 18 + e];
+}
+
+__global__ void global_accept_kernel(const double* ln_r, int n, uint64_t seed, uint64_t ctr, uint8_t* accept,
+                                     double* margin) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += ln_r[i];
+    double u1, u2;
+    uniform_pair(0u, DD_PURPOSE_GLOBAL_ACCEPT, 0u, seed, ctr, u1, u2);
+    double lu = log(u1);
+    accept[0] = lu < s ? 1 : 0;
+    if (margin) margin[0] = s - lu;
+}
+
+__global__ void conditional_copy_kernel(long long n, const uint8_t* accept, const double* src, double* dst) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || accept[0]) return;
+    dst[i] = src[i];
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- helpers
+static BlockCtx block_ctx(dd_handle* h) {
+    BlockCtx c;
+    for (int a = 0; a < 4; ++a) c.bd[a] = h->g.b[a];
+    c.st[0] = 1;
+    c.st[1] = c.bd[0];
+    c.st[2] = c.bd[0] * c.bd[1];
+    c.st[3] = c.bd[0] * c.bd[1] * c.bd[2];
+    c.nb = h->g.bsites;
+    c.kappa = h->prm.kappa;
+    return c;
+}
+
+// format slots 0..nslots-1 from interpolated (or copied) fields
+static int prepare_fields(dd_handle* h, const double* U_old, const double* U_new, int n, bool factors, bool eo) {
+    const int nslots = factors ? n + 1 : 2;
+    const int ip = h->prm.inner_prec;
+    for (int k = 0; k < nslots; ++k) {
+        FieldSlot& f = h->fields[k];
+        int num = factors ? k : (k == 0 ? 0 : 1);
+        int den = factors ? n : 1;
+        int rc = launch_interpolate(h, U_old, U_new, (double*)f.canon, num, den);
+        if (rc) return rc;
+        bool need_eo = eo && (k > 0);
+        rc = format_field(h, (const double*)f.canon, f, need_eo, need_eo && ip == DD_PREC_F32,
+                          need_eo && ip == DD_PREC_F16, true, true);
+        if (rc) return rc;
+    }
+    return DD_OK;
+}
+
+static int launch_blocks(dd_handle* h, int mode, const std::vector<BlockItem>& items, const double2* in_bank,
+                         double2* out_bank, uint64_t seed, uint64_t ctr) {
+    if (items.empty()) return DD_OK;
+    if ((int)items.size() > h->items_cap) return dd_fail(h, DD_ERR_INVALID_ARG, "too many block items");
+    DD_CUDA(h, cudaMemcpyAsync(h->d_items, items.data(), sizeof(BlockItem) * items.size(), cudaMemcpyHostToDevice,
+                               h->stream));
+    DD_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream));
+    BlockArgs A;
+    A.g = h->g;
+    A.c = block_ctx(h);
+    A.mode = mode;
+    A.items = (const BlockItem*)h->d_items;
+    A.nitems = (int)items.size();
+    A.queue = h->d_queue;
+    A.dd64 = h->fields[0].dd64;
+    A.dd64_fs = (long long)(h->fields[1].dd64 - h->fields[0].dd64);
+    A.dd32 = h->fields[0].dd32;
+    A.dd32_fs = (long long)(h->fields[1].dd32 - h->fields[0].dd32);
+    A.in_bank = in_bank;
+    A.out_bank = out_bank;
+    A.bank_vs = 12LL * h->g.V;
+    A.item_out = h->d_item_out;
+    A.scratch = h->block_scratch;
+    A.slot_bytes = (long long)h->block_slot_bytes;
+    A.seed = seed;
+    A.ctr = ctr;
+    A.purpose = DD_PURPOSE_BLOCK_NOISE;
+    A.tol2 = h->prm.tol_block * h->prm.tol_block;
+    A.inner_f64 = h->prm.block_prec == DD_PREC_F64;
+    A.tol2_inner = A.inner_f64 ? 0.25 * A.tol2 : 1e-10;
+    A.maxit_inner = std::min(h->prm.maxit, 2000);
+    A.max_outer = A.inner_f64 ? 3 : 12;
+    A.status = h->d_status;
+    int grid = std::min((int)items.size(), h->block_slots);
+    if (A.inner_f64)
+        block_solve_kernel<double, SpinorF64, LinkF64><<<grid, 256, 0, h->stream>>>(A);
+    else
+        block_solve_kernel<float, SpinorF32, LinkF32><<<grid, 256, 0, h->stream>>>(A);
+    DD_LAUNCH_CHECK(h, "block_solve_kernel");
+    return DD_OK;
+}
+
+// ------------------------------------------------------------- entry points
+extern "C" int dd_block_filter(dd_t h, const void* U_old, void* U_new, int colour_mask, int mode, int n,
+                               uint64_t seed, uint64_t ctr, double* ln_b, uint8_t* accept) {
+    int rc = dd_require_ws(h);
+    if (rc) return rc;
+    if (!U_old || !U_new || !ln_b || !accept || n < 1 || n > h->prm.max_rhs || colour_mask < 1 || colour_mask > 3)
+        return dd_fail(h, DD_ERR_INVALID_ARG, "dd_block_filter: bad arguments");
+    if (mode == DD_FILTER_EXACT) {
+        rc = block_filter_exact(h, (const double*)U_old, (const double*)U_new, colour_mask, ln_b);
+        if (rc) return rc;
+    } else if (mode == DD_FILTER_STOCHASTIC) {
+        rc = prepare_fields(h, (const double*)U_old, (const double*)U_new, n, true, false);
+        if (rc) return rc;
+        const Geo& g = h->g;
+        std::vector<BlockItem> items;
+        std::vector<int> base(g.nblocks, -1);
+        const int half = g.nblocks / 2;
+        // items of a block are consecutive; block ids from positions
+        std::vector<int> id_at(g.nblocks);
+        {
+            // host mirror of block_id_at
+            for (int pos = 0; pos < g.nblocks; ++pos) {
+                int col = pos >= half ? 1 : 0, rank = pos - col * half, id = 2 * rank;
+                int B1 = (id / g.nbk[0]) % g.nbk[1], B2 = (id / (g.nbk[0] * g.nbk[1])) % g.nbk[2],
+                    B3 = id / (g.nbk[0] * g.nbk[1] * g.nbk[2]);
+                if (((B1 + B2 + B3) & 1) != col) id += 1;
+                id_at[pos] = id;
+            }
+        }
+        for (int pos = 0; pos < g.nblocks; ++pos) {
+            int col = pos >= half ? 1 : 0;
+            if (!((colour_mask >> col) & 1)) continue;
+            base[id_at[pos]] = (int)items.size();
+            for (int i = 0; i < n; ++i) items.push_back(BlockItem{pos, i, i + 1, i});
+        }
+        rc = launch_blocks(h, BLOCK_FILTER, items, nullptr, nullptr, seed, ctr);
+        if (rc) return rc;
+        int* d_base = h->d_imap;
+        DD_CUDA(h, cudaMemcpyAsync(d_base, base.data(), sizeof(int) * g.nblocks, cudaMemcpyHostToDevice, h->stream));
+        sum_items_kernel<<<grid_for(g.nblocks, 128), 128, 0, h->stream>>>(g.nblocks, d_base, n, h->d_item_out, ln_b);
+        DD_LAUNCH_CHECK(h, "sum_items_kernel");
+    } else {
+        return dd_fail(h, DD_ERR_INVALID_ARG, "dd_block_filter: unknown mode");
+    }
+    block_accept_kernel<<<grid_for(h->g.nblocks, 128), 128, 0, h->stream>>>(h->g, colour_mask, ln_b, accept, seed, ctr);
+    if (h->n_active > 0)
+        restore_kernel<<<grid_for(h->n_active, 128), 128, 0, h->stream>>>(h->g, h->n_active, h->d_active_links, accept,
+                                                                        (const double*)U_old, (double*)U_new);
+    DD_LAUNCH_CHECK(h, "block accept");
+    return DD_OK;
+}
+
+extern "C" int dd_det_ratio_estimate(dd_t h, const void* U_old, const void* U_new, int n, uint64_t seed,
+                                     uint64_t ctr, int mode, double* ln_out) {
+    int rc = dd_require_ws(h);
+    if (rc) return rc;
+    if (!U_old || !U_new || !ln_out || n < 1 || n > h->prm.max_rhs || (mode != DD_EST_FACTORS && mode != DD_EST_REPLICAS))
+        return dd_fail(h, DD_ERR_INVALID_ARG, "dd_det_ratio_estimate: bad arguments");
+    const bool factors = mode == DD_EST_FACTORS;
+    rc = prepare_fields(h, (const double*)U_old, (const double*)U_new, n, factors, true);
+    if (rc) return rc;
+    const Geo& g = h->g;
+    const BlockCtx c = block_ctx(h);
+    const int R = h->prm.max_rhs;
+    const long long vs = 12LL * g.V;
+    double2* bank[6];
+    for (int k = 0; k < 6; ++k) bank[k] = h->dd_vec + (long long)k * R * vs;
+    // field slot of the old / new operator of every factor
+    std::vector<int> f_old(n), f_new(n);
+    for (int i = 0; i < n; ++i) {
+        f_old[i] = factors ? i : 0;
+        f_new[i] = factors ? i + 1 : 1;
+    }
+    int* d_fold = h->d_imap + g.nblocks;
+    int* d_fnew = d_fold + 2 * R;
+    DD_CUDA(h, cudaMemcpyAsync(d_fold, f_old.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+    DD_CUDA(h, cudaMemcpyAsync(d_fnew, f_new.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+    const long long canon_fs = (long long)(h->fields[1].canon - h->fields[0].canon) * 2;  // doubles
+    const long long dd64_fs = (long long)(h->fields[1].dd64 - h->fields[0].dd64);
+    dim3 gv(grid_for(g.V, 128), n);
+    // 1. eta on black sites
+    noise_black_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], vs, DD_PURPOSE_GLOBAL_NOISE, seed, ctr);
+    // 2. w = C eta, w' = C' eta (onto white sites)
+    inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], bank[1], vs, (const double*)h->fields[0].canon, canon_fs, d_fold, 1);
+    inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], bank[2], vs, (const double*)h->fields[0].canon, canon_fs, d_fnew, 1);
+    DD_LAUNCH_CHECK(h, "schur stage 1-2");
+    // 3. z = E^{-1} w, z' = E'^{-1} w'  (banks 1,2 are contiguous, so are 3,4)
+    const int half = g.nblocks / 2;
+    std::vector<BlockItem> items;
+    for (int i = 0; i < n; ++i)
+        for (int pos = half; pos < g.nblocks; ++pos) {
+            items.push_back(BlockItem{pos, 0, f_old[i], i});
+            items.push_back(BlockItem{pos, 0, f_new[i], R + i});
+        }
+    rc = launch_blocks(h, BLOCK_SOLVE, items, bank[1], bank[3], seed, ctr);
+    if (rc) return rc;
+    // 4. v = B z, v' = B' z' (onto black sites)
+    inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[3], bank[1], vs, (const double*)h->fields[0].canon, canon_fs, d_fold, 0);
+    inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[4], bank[2], vs, (const double*)h->fields[0].canon, canon_fs, d_fnew, 0);
+    DD_LAUNCH_CHECK(h, "schur stage 4");
+    // 5. a = A^{-1} v
+    items.clear();
+    for (int i = 0; i < n; ++i)
+        for (int pos = 0; pos < half; ++pos) items.push_back(BlockItem{pos, 0, f_old[i], i});
+    rc = launch_blocks(h, BLOCK_SOLVE, items, bank[1], bank[5], seed, ctr);
+    if (rc) return rc;
+    // 6. s = v' - A' a  -> bank 3
+    schur_source_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[2], bank[5], bank[3], vs, h->fields[0].dd64, dd64_fs, d_fnew);
+    // 7. global solve D' y = (s, 0)
+    SolverVecs& v = h->vecs[0];
+    dd_to_eo_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[3], vs, v.be, v.bo);
+    DD_LAUNCH_CHECK(h, "schur stage 6-7");
+    int iters = 0;
+    rc = solve_packed(h, n, f_new[0], factors ? 1 : 0, h->prm.inner_prec, h->prm.tol_global, h->prm.maxit, &iters,
+                      nullptr);
+    if (rc && rc != DD_ERR_NOT_CONVERGED) return dd_fail(h, rc, "dd_det_ratio_estimate: global solve failed");
+    // 8. ln r_i
+    Reduce red;
+    red.partials = h->d_partials;
+    red.counters = h->d_counters;
+    red.st = nullptr;
+    red.out = ln_out;
+    red.op = FIN_STORE;
+    red.status = h->d_status;
+    dim3 gb(grid_for(g.V / 2, 128), n);
+    estimate_kernel<<<gb, 128, 0, h->stream>>>(g, c, bank[0], vs, v.xe, v.xo, red);
+    DD_LAUNCH_CHECK(h, "estimate_kernel");
+    if (rc == DD_ERR_NOT_CONVERGED) return dd_fail(h, rc, "dd_det_ratio_estimate: global solve hit maxit");
+    return DD_OK;
+}
+
+extern "C" int dd_global_accept(dd_t h, void* U, const void* U_old, const double* ln_r, int n, uint64_t seed,
+                                uint64_t ctr, uint8_t* accept, double* ln_margin) {
+    int rc = dd_require_ws(h);
+    if (rc) return rc;
+    if (!U || !U_old || !ln_r || !accept || n < 1) return dd_fail(h, DD_ERR_INVALID_ARG, "dd_global_accept: bad arguments");
+    global_accept_kernel<<<1, 1, 0, h->stream>>>(ln_r, n, seed, ctr, accept, ln_margin);
+    const long long m = (long long)h->g.V * 72;
+    conditional_copy_kernel<<<grid_for(m, 256), 256, 0, h->stream>>>(m, accept, (const double*)U_old, (double*)U);
+    DD_LAUNCH_CHECK(h, "global accept");
+    return DD_OK;
+}

@@ -1,0 +1,154 @@
+// Proposal step (Eq. 4step step 0): heat-bath / over-relaxation of the
+// Wilson plaquette action S_G = beta sum_P (1 - Re tr U_P / 3) on the active
+// links of the selected block colours.
+//
+// Cabibbo-Marinari: for each link the SU(2) subgroups (0,1), (1,2), (0,2) in
+// turn; with the staple sum A and W = U A, the subgroup block w of W has the
+// SU(2)-proportional part k V; the new element is R = X V^dag, X drawn from
+// exp(alpha x0) dX (alpha = 2 beta k / 3) by the Kennedy-Pendleton sampler
+// (at most 64 tries), direction of (x1, x2, x3) uniform; U <- R U.
+// Over-relaxation: R = (V^dag)^2.  One launch per (colour, direction, site
+// parity) group: links of one direction and one site parity share no
+// plaquette, so a group is updated in parallel.
+#include <algorithm>
+#include <cmath>
+
+#include "dd_internal.h"
+#include "su3.cuh"
+
+namespace {
+
+struct Q4 {
+    double a0, a1, a2, a3;
+};
+// 2x2 SU(2) matrix in the parametrisation [[a0 + i a3, a2 + i a1], [-a2 + i a1, a0 - i a3]]
+struct M2 {
+    cpx<double> m[2][2];
+};
+DD_DEV M2 su2(double a0, double a1, double a2, double a3) {
+    M2 r;
+    r.m[0][0] = mk<double>(a0, a3);
+    r.m[0][1] = mk<double>(a2, a1);
+    r.m[1][0] = mk<double>(-a2, a1);
+    r.m[1][1] = mk<double>(a0, -a3);
+    return r;
+}
+DD_DEV M2 mul2(const M2& a, const M2& b) {
+    M2 c;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) c.m[i][j] = cmul(a.m[i][0], b.m[0][j]) + cmul(a.m[i][1], b.m[1][j]);
+    return c;
+}
+DD_DEV M2 dag2(const M2& a) {
+    M2 c;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) c.m[i][j] = conj(a.m[j][i]);
+    return c;
+}
+
+DD_DEV M3 link_at(const double* U, long long s, int a) { return load_m3(U + (s * 4 + a) * 18); }
+
+__global__ void heatbath_kernel(Geo g, double* U, const int* links, int n, double beta, int overrelax, int sweep,
+                                uint64_t seed, uint64_t ctr, unsigned long long* fails) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int l = links[k];
+    const int s = l >> 2, a = l & 3;
+    int x[4];
+    canon_coords(g, s, x);
+    const int sa = shift_index(g, x, a, +1);
+    int xa[4];
+    canon_coords(g, sa, xa);
+    // staple sum
+    M3 A;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) A.m[i][j] = mk<double>(0, 0);
+    for (int b = 0; b < 4; ++b) {
+        if (b == a) continue;
+        const int sb = shift_index(g, x, b, +1);
+        const int smb = shift_index(g, x, b, -1);
+        const int samb = shift_index(g, xa, b, -1);
+        // U_b(s+a) U_a(s+b)^dag U_b(s)^dag
+        A = add(A, mul_dag_right(mul_dag_right(link_at(U, sa, b), link_at(U, sb, a)), link_at(U, s, b)));
+        // U_b(s+a-b)^dag U_a(s-b)^dag U_b(s-b)
+        A = add(A, mul(dagger(mul(link_at(U, smb, a), link_at(U, samb, b))), link_at(U, smb, b)));
+    }
+    M3 u = link_at(U, s, a);
+    const int SG[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+    unsigned long long nf = 0;
+    for (int sg = 0; sg < 3; ++sg) {
+        const int i = SG[sg][0], j = SG[sg][1];
+        M3 W = mul(u, A);
+        double a0 = 0.5 * (W.m[i][i].x + W.m[j][j].x);
+        double a3 = 0.5 * (W.m[i][i].y - W.m[j][j].y);
+        double a2 = 0.5 * (W.m[i][j].x - W.m[j][i].x);
+        double a1 = 0.5 * (W.m[i][j].y + W.m[j][i].y);
+        double kk = sqrt(a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3);
+        if (!(kk > 1e-300)) continue;
+        M2 Vm = su2(a0 / kk, a1 / kk, a2 / kk, a3 / kk);
+        M2 R;
+        if (overrelax) {
+            R = mul2(dag2(Vm), dag2(Vm));
+        } else {
+            const uint32_t sub_base = ((uint32_t)sweep << 16) | ((uint32_t)sg << 12);
+            const double alpha = 2.0 * beta * kk / 3.0;
+            double x0 = 1.0;
+            bool ok = false;
+            for (int t = 0; t < 64 && !ok; ++t) {
+                double u1, u2, u3, u4;
+                uniform_pair((uint32_t)l, DD_PURPOSE_HEATBATH, sub_base + 2 * t, seed, ctr, u1, u2);
+                uniform_pair((uint32_t)l, DD_PURPOSE_HEATBATH, sub_base + 2 * t + 1, seed, ctr, u3, u4);
+                double c = cos(6.283185307179586477 * u2);
+                double lam2 = -(log(u1) + c * c * log(u3)) / (2.0 * alpha);
+                if (u4 * u4 <= 1.0 - lam2) {
+                    x0 = 1.0 - 2.0 * lam2;
+                    ok = true;
+                }
+            }
+            if (!ok) {
+                ++nf;
+                continue;
+            }
+            double u5, u6;
+            uniform_pair((uint32_t)l, DD_PURPOSE_HEATBATH, sub_base + 200, seed, ctr, u5, u6);
+            double r = sqrt(fmax(0.0, 1.0 - x0 * x0));
+            double cth = 2.0 * u5 - 1.0;
+            double sth = sqrt(fmax(0.0, 1.0 - cth * cth));
+            double phi = 6.283185307179586477 * u6;
+            M2 X = su2(x0, r * sth * cos(phi), r * sth * sin(phi), r * cth);
+            R = mul2(X, dag2(Vm));
+        }
+        for (int c = 0; c < 3; ++c) {
+            cpx<double> ui = u.m[i][c], uj = u.m[j][c];
+            u.m[i][c] = cmul(R.m[0][0], ui) + cmul(R.m[0][1], uj);
+            u.m[j][c] = cmul(R.m[1][0], ui) + cmul(R.m[1][1], uj);
+        }
+    }
+    store_m3(U + ((long long)s * 4 + a) * 18, u);
+    if (nf) atomicAdd(fails, nf);
+}
+
+}  // namespace
+
+extern "C" int dd_gauge_update(dd_t h, void* U, int colour_mask, double beta, int n_hb, int n_or, uint64_t seed,
+                               uint64_t ctr) {
+    int rc = dd_require_ws(h);
+    if (rc) return rc;
+    if (!U || colour_mask < 1 || colour_mask > 3 || !(beta > 0) || n_hb < 0 || n_or < 0 || n_hb > 255)
+        return dd_fail(h, DD_ERR_INVALID_ARG, "dd_gauge_update: bad arguments");
+    for (int sweep = 0; sweep < n_hb; ++sweep)
+        for (int kind = 0; kind <= n_or; ++kind)
+            for (int a = 0; a < 4; ++a)
+                for (int par = 0; par < 2; ++par)
+                    for (int col = 0; col < 2; ++col) {
+                        if (!((colour_mask >> col) & 1)) continue;
+                        int gi = (col * 4 + a) * 2 + par;
+                        int off = h->h_group_off[gi], cnt = h->h_group_off[gi + 1] - off;
+                        if (cnt <= 0) continue;
+                        heatbath_kernel<<<grid_for(cnt, 64), 64, 0, h->stream>>>(
+                            h->g, (double*)U, h->d_active_links + off, cnt, beta, kind > 0, sweep, seed, ctr,
+                            h->d_hb_fails);
+                    }
+    DD_LAUNCH_CHECK(h, "heatbath_kernel");
+    return DD_OK;
+}

@@ -1,0 +1,513 @@
+// Global Krylov solves (Sec. 4: "one inversion for each factor"; the
+// inversions behind the stochastic acceptance steps).
+//
+// D x = b is solved through the even-site Schur complement
+//   Dtilde = 1 - kappa^2 H_eo H_oe,  b~ = b_e + kappa H_eo b_o,
+//   x_e = Dtilde^{-1} b~,  x_o = b_o + kappa H_oe x_e,
+// with CG on the normal equations Dtilde^dag Dtilde (CGNR), Dtilde^dag =
+// gamma5 Dtilde gamma5.  The plain FP64 path runs CGNR in FP64.  The mixed
+// path runs CGNR with FP32 arithmetic on FP32 or FP16 storage as the inner
+// solver of an FP64 defect-correction loop:
+//   r = b~ - Dtilde x (FP64), solve Dtilde e = r roughly, x += e,
+// until ||r|| <= tol ||b|| (that is the true residual of D x = b, because
+// x_o is formed exactly from x_e).  All Krylov scalars are FP64 grid
+// reductions finished on the device; the host only checks convergence
+// flags every few iterations.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "dslash.cuh"
+#include "solver.h"
+
+namespace {
+
+// ------------------------------------------------------------- BLAS kernels
+template <class R, class SM, class SH>
+__global__ void __launch_bounds__(128) cg_xr_kernel(long long n, SM x, SM r, SM p, SM q, SH rh, int copy,
+                                                    const CGState* st, Reduce red) {
+    __shared__ double sh[34];
+    const int rhs = blockIdx.y;
+    if (!st[rhs].active) return;
+    const R alpha = (R)st[rhs].alpha;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double nrm = 0.0;
+    if (i < n) {
+        SM xr = at_rhs(x, rhs), rr = at_rhs(r, rhs), pr = at_rhs(p, rhs), qr = at_rhs(q, rhs);
+        Spinor<R> a, b;
+        xr.load(i, a);
+        pr.load(i, b);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) a.c[k] = a.c[k] + alpha * b.c[k];
+        xr.store(i, a);
+        rr.load(i, a);
+        qr.load(i, b);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) a.c[k] = a.c[k] - alpha * b.c[k];
+        rr.store(i, a);
+        if (copy) at_rhs(rh, rhs).store(i, a);
+        nrm = (double)snorm2(a);
+    }
+    grid_reduce(red, rhs, nrm, sh);
+}
+
+template <class R, class SM, class SH>
+__global__ void __launch_bounds__(128) cg_p_kernel(long long n, SM p, SM z, SH ph, int copy, const CGState* st) {
+    const int rhs = blockIdx.y;
+    if (!st[rhs].active) return;
+    const double beta = st[rhs].beta;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    SM pr = at_rhs(p, rhs), zr = at_rhs(z, rhs);
+    Spinor<R> a, b;
+    zr.load(i, a);
+    if (beta != 0.0) {
+        pr.load(i, b);
+        const R bt = (R)beta;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) a.c[k] = a.c[k] + bt * b.c[k];
+    }
+    pr.store(i, a);
+    if (copy) at_rhs(ph, rhs).store(i, a);
+}
+
+// start an inner solve: x = 0, r = r0 (copied into the hop copy), states armed
+template <class R, class SM, class SH>
+__global__ void cg_start_kernel(long long n, SM x, SM r, SH rh, int copy, CGState* st, const CGState* outer) {
+    const int rhs = blockIdx.y;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (outer && !outer[rhs].active) return;
+    if (i < n) {
+        Spinor<R> z;
+        zero(z);
+        at_rhs(x, rhs).store(i, z);
+        if (copy) {
+            Spinor<R> a;
+            at_rhs(r, rhs).load(i, a);
+            at_rhs(rh, rhs).store(i, a);
+        }
+    }
+}
+
+__global__ void cg_arm_kernel(int nrhs, CGState* st, const CGState* outer, const double* rr0, double tol,
+                              double abs_fac, int maxit) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrhs) return;
+    CGState c;
+    c.zz = c.qq = c.alpha = c.beta = 0.0;
+    c.rr = rr0[r];
+    // relative target tol^2 |r0|^2, or a fraction of the outer absolute target
+    c.tol2 = (abs_fac > 0.0 && outer) ? abs_fac * outer[r].tol2 : tol * tol * rr0[r];
+    c.active = (outer ? outer[r].active : 1) && rr0[r] > 0.0;
+    c.iters = 0;
+    c.maxit = maxit;
+    c.flags = 0;
+    st[r] = c;
+}
+
+// outer (defect-correction) bookkeeping: active while rr > tol2
+__global__ void outer_update_kernel(int nrhs, CGState* outer, const double* rr) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrhs) return;
+    outer[r].rr = rr[r];
+    outer[r].active = outer[r].active && (rr[r] > outer[r].tol2);
+}
+__global__ void outer_arm_kernel(int nrhs, CGState* outer, const double* bb, double tol) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrhs) return;
+    CGState c;
+    c.zz = c.qq = c.alpha = c.beta = 0.0;
+    c.rr = bb[r];
+    c.tol2 = tol * tol * bb[r];
+    c.active = bb[r] > 0.0;
+    c.iters = 0;
+    c.maxit = 0;
+    c.flags = 0;
+    outer[r] = c;
+}
+
+// x64 += e (any storage), r64 = b - t (with |r|^2), v = 0, copies
+template <class SE>
+__global__ void add_correction_kernel(long long n, SpinorF64 x, SE e, const CGState* outer) {
+    const int rhs = blockIdx.y;
+    if (outer && !outer[rhs].active) return;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Spinor<double> a, b;
+    at_rhs(x, rhs).load(i, a);
+    at_rhs(e, rhs).load(i, b);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) a.c[k] = a.c[k] + b.c[k];
+    at_rhs(x, rhs).store(i, a);
+}
+__global__ void __launch_bounds__(128) residual_kernel(long long n, SpinorF64 b, SpinorF64 t, SpinorF64 r,
+                                                       const CGState* outer, Reduce red) {
+    __shared__ double sh[34];
+    const int rhs = blockIdx.y;
+    if (outer && !outer[rhs].active) return;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double nrm = 0.0;
+    if (i < n) {
+        Spinor<double> a, c;
+        at_rhs(b, rhs).load(i, a);
+        at_rhs(t, rhs).load(i, c);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) a.c[k] = a.c[k] - c.c[k];
+        at_rhs(r, rhs).store(i, a);
+        nrm = snorm2(a);
+    }
+    grid_reduce(red, rhs, nrm, sh);
+}
+template <class S>
+__global__ void __launch_bounds__(128) norm2_kernel(long long n, S v, Reduce red) {
+    __shared__ double sh[34];
+    const int rhs = blockIdx.y;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double nrm = 0.0;
+    if (i < n) {
+        Spinor<double> a;
+        at_rhs(v, rhs).load(i, a);
+        nrm = snorm2(a);
+    }
+    grid_reduce(red, rhs, nrm, sh);
+}
+template <class SIn, class SOut>
+__global__ void copy_kernel(long long n, SIn in, SOut out, const CGState* outer) {
+    const int rhs = blockIdx.y;
+    if (outer && !outer[rhs].active) return;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Spinor<double> a;
+    at_rhs(in, rhs).load(i, a);
+    at_rhs(out, rhs).store(i, a);
+}
+__global__ void zero64_kernel(long long n, SpinorF64 v) {
+    const int rhs = blockIdx.y;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Spinor<double> z;
+    zero(z);
+    at_rhs(v, rhs).store(i, z);
+}
+
+// ------------------------------------------------------------ CGNR runner
+template <class R, class SM, class SH, class LK>
+struct NormalCG {
+    dd_handle* h;
+    int nrhs;
+    SM x, r, p, q, z;
+    SH ph, rh, th;
+    int copies;
+    LK lk;
+    long long lk_rs;
+    CGState* st;
+    const CGState* outer;
+
+    Reduce red(int op) const {
+        Reduce R_;
+        R_.partials = h->d_partials;
+        R_.counters = h->d_counters;
+        R_.st = st;
+        R_.out = nullptr;
+        R_.op = op;
+        R_.status = h->d_status;
+        return R_;
+    }
+    template <class SIn, class SX, class SOut>
+    HopArgs<SIn, SX, SOut, LK> args(int par, SIn in, SX xin, SOut out, double a, double b, int hasx, int g5in,
+                                    int g5out, int op) const {
+        HopArgs<SIn, SX, SOut, LK> A;
+        A.g = h->g;
+        A.p = par;
+        A.in = in;
+        A.xin = xin;
+        A.out = out;
+        A.lk = lk;
+        A.lk_rhs_stride = lk_rs;
+        A.a = a;
+        A.b = b;
+        A.has_x = hasx;
+        A.g5in = g5in;
+        A.g5out = g5out;
+        A.colour_mask = 3;
+        A.st = st;
+        A.red = red(op);
+        return A;
+    }
+    // z = Dtilde^dag r  (two hops), |z|^2 -> op
+    void apply_dag_r(int op) {
+        const double k2 = h->prm.kappa * h->prm.kappa;
+        launch_hop<R, SH, SM, SH, LK, 0>(args(1, rh, r, th, 0.0, 1.0, 0, 1, 0, FIN_NONE), nrhs, h->stream);
+        launch_hop<R, SH, SM, SM, LK, 0>(args(0, th, r, z, 1.0, -k2, 1, 0, 1, op), nrhs, h->stream);
+    }
+    // q = Dtilde p, |q|^2 -> alpha
+    void apply_p() {
+        const double k2 = h->prm.kappa * h->prm.kappa;
+        launch_hop<R, SH, SM, SH, LK, 0>(args(1, ph, p, th, 0.0, 1.0, 0, 0, 0, FIN_NONE), nrhs, h->stream);
+        launch_hop<R, SH, SM, SM, LK, 0>(args(0, th, p, q, 1.0, -k2, 1, 0, 0, FIN_ALPHA), nrhs, h->stream);
+    }
+    // solve Dtilde x = r (r holds the right-hand side; x starts at 0)
+    int run(const double* rr0, double tol, double abs_fac, int maxit, int chunk, int* iters_out) {
+        const long long n = h->g.Vh;
+        dim3 grid(grid_for(n, 128), nrhs);
+        if (maxit < 1) maxit = 1;
+        cg_arm_kernel<<<1, 64, 0, h->stream>>>(nrhs, st, outer, rr0, tol, abs_fac, maxit);
+        cg_start_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(n, x, r, rh, copies, st, outer);
+        apply_dag_r(FIN_ZZ_INIT);
+        cg_p_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(n, p, z, ph, copies, st);
+        std::vector<CGState> hs(nrhs);
+        int done_iters = 0;
+        for (;;) {
+            for (int it = 0; it < chunk; ++it) {
+                apply_p();
+                cg_xr_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(n, x, r, p, q, rh, copies, st, red(FIN_RR));
+                apply_dag_r(FIN_BETA);
+                cg_p_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(n, p, z, ph, copies, st);
+            }
+            done_iters += chunk;
+            if (cudaGetLastError() != cudaSuccess) return DD_ERR_CUDA;
+            if (cudaMemcpyAsync(hs.data(), st, sizeof(CGState) * nrhs, cudaMemcpyDeviceToHost, h->stream) !=
+                cudaSuccess)
+                return DD_ERR_CUDA;
+            if (cudaStreamSynchronize(h->stream) != cudaSuccess) return DD_ERR_CUDA;
+            bool any = false;
+            for (int k = 0; k < nrhs; ++k) any = any || hs[k].active;
+            if (!any || done_iters >= maxit + chunk) break;
+        }
+        int tot = 0, flags = 0;
+        for (int k = 0; k < nrhs; ++k) {
+            tot += hs[k].iters;
+            flags |= hs[k].flags;
+        }
+        if (iters_out) *iters_out += tot;
+        if (flags & 2) return DD_ERR_NUMERIC;
+        return DD_OK;
+    }
+};
+
+template <class LK>
+LK field_links(dd_handle* h, int slot);
+template <>
+LinkF64 field_links<LinkF64>(dd_handle* h, int slot) {
+    return LinkF64{h->fields[slot].eo64, h->g.Vh};
+}
+template <>
+LinkF32 field_links<LinkF32>(dd_handle* h, int slot) {
+    return LinkF32{h->fields[slot].eo32, h->g.Vh};
+}
+template <>
+LinkF16 field_links<LinkF16>(dd_handle* h, int slot) {
+    return LinkF16{h->fields[slot].eo16, h->g.Vh};
+}
+template <class LK>
+long long field_stride(dd_handle* h, int step) {
+    if (!step || h->fields.size() < 2) return 0;
+    LK a = field_links<LK>(h, 0), b = field_links<LK>(h, 1);
+    return (long long)(b.p - a.p);
+}
+
+Reduce store_reduce(dd_handle* h, double* out) {
+    Reduce R_;
+    R_.partials = h->d_partials;
+    R_.counters = h->d_counters;
+    R_.st = nullptr;
+    R_.out = out;
+    R_.op = FIN_STORE;
+    R_.status = h->d_status;
+    return R_;
+}
+
+// FP64 hop helper on eo FP64 vectors
+void hop64(dd_handle* h, int nrhs, int par, SpinorF64 in, SpinorF64 xin, SpinorF64 out, double a, double b,
+           int hasx, LinkF64 lk, long long lk_rs, const CGState* st, Reduce red) {
+    HopArgs<SpinorF64, SpinorF64, SpinorF64, LinkF64> A;
+    A.g = h->g;
+    A.p = par;
+    A.in = in;
+    A.xin = xin;
+    A.out = out;
+    A.lk = lk;
+    A.lk_rhs_stride = lk_rs;
+    A.a = a;
+    A.b = b;
+    A.has_x = hasx;
+    A.g5in = 0;
+    A.g5out = 0;
+    A.colour_mask = 3;
+    A.st = st;
+    A.red = red;
+    launch_hop<double, SpinorF64, SpinorF64, SpinorF64, LinkF64, 0>(A, nrhs, h->stream);
+}
+
+__global__ void add_scalars_kernel(int n, double* a, const double* b) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) a[r] += b[r];
+}
+
+// One defect-correction solve.  Inner vectors: x (correction), r (inner
+// residual, starts as the FP64 outer residual), p, q, z (storage SM) and the
+// hop copies ph, rh, th (storage SH; th lives on odd sites).
+template <class R, class SM, class SH, class LK>
+int defect_correction(dd_handle* h, int nrhs, int field0, int step, NormalCG<R, SM, SH, LK>& cg, bool fp64_inner,
+                      double tol, int maxit, int* iters, double* relres) {
+    SolverVecs& v = h->vecs[0];
+    const long long Vh = h->g.Vh;
+    const double kappa = h->prm.kappa;
+    dim3 grid(grid_for(Vh, 128), nrhs);
+    SpinorF64 be{v.be, Vh}, bo{v.bo, Vh}, xe{v.xe, Vh}, xo{v.xo, Vh}, re{v.re, Vh}, t64{v.t64, Vh},
+        t64b{v.t64b, Vh};
+    LinkF64 lk64 = field_links<LinkF64>(h, field0);
+    const long long rs64 = field_stride<LinkF64>(h, step);
+    CGState* outer = h->d_cg + h->prm.max_rhs;
+    double* bb = h->d_scalars;
+    double* tmp = h->d_scalars + nrhs;
+    double* rr = h->d_scalars + 2 * nrhs;
+    Reduce none;
+    none.op = FIN_NONE;
+    // |b|^2 over both parities, then b~ = b_e + kappa H_eo b_o (in place)
+    norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(Vh, be, store_reduce(h, bb));
+    norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(Vh, bo, store_reduce(h, tmp));
+    add_scalars_kernel<<<1, 64, 0, h->stream>>>(nrhs, bb, tmp);
+    hop64(h, nrhs, 0, bo, be, be, 1.0, kappa, 1, lk64, rs64, nullptr, none);
+    outer_arm_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, bb, tol);
+    zero64_kernel<<<grid, 128, 0, h->stream>>>(Vh, xe);
+    copy_kernel<SpinorF64, SpinorF64><<<grid, 128, 0, h->stream>>>(Vh, be, re, nullptr);
+    norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(Vh, re, store_reduce(h, rr));
+    outer_update_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, rr);
+    if (cudaGetLastError() != cudaSuccess) return DD_ERR_CUDA;
+    const double tol_inner = fp64_inner ? 0.0 : h->prm.tol_inner;
+    int total = 0;
+    std::vector<CGState> hs(nrhs);
+    for (int cycle = 0; cycle < 200; ++cycle) {
+        // inner right-hand side: the current FP64 residual
+        if (!fp64_inner) copy_kernel<SpinorF64, SM><<<grid, 128, 0, h->stream>>>(Vh, re, cg.r, outer);
+        // inner stopping rule: FP64 inner aims at the outer target directly
+        // (with margin), the mixed inner at a relative reduction tol_inner
+        int it = 0;
+        int rc = cg.run(rr, tol_inner, fp64_inner ? 0.25 : -1.0, maxit - total, 16, &it);
+        total += it;
+        if (rc) return rc;
+        add_correction_kernel<SM><<<grid, 128, 0, h->stream>>>(Vh, xe, cg.x, outer);
+        // true residual r = b~ - Dtilde x (FP64)
+        hop64(h, nrhs, 1, xe, xe, t64, 0.0, 1.0, 0, lk64, rs64, outer, none);
+        hop64(h, nrhs, 0, t64, xe, t64b, 1.0, -kappa * kappa, 1, lk64, rs64, outer, none);
+        residual_kernel<<<grid, 128, 0, h->stream>>>(Vh, be, t64b, re, outer, store_reduce(h, rr));
+        outer_update_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, rr);
+        if (cudaGetLastError() != cudaSuccess) return DD_ERR_CUDA;
+        if (cudaMemcpyAsync(hs.data(), outer, sizeof(CGState) * nrhs, cudaMemcpyDeviceToHost, h->stream) !=
+            cudaSuccess)
+            return DD_ERR_CUDA;
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) return DD_ERR_CUDA;
+        bool any = false;
+        for (int k = 0; k < nrhs; ++k) any = any || hs[k].active;
+        if (!any || total >= maxit) break;
+    }
+    // x_o = b_o + kappa H_oe x_e
+    hop64(h, nrhs, 1, xe, bo, xo, 1.0, kappa, 1, lk64, rs64, nullptr, none);
+    if (cudaGetLastError() != cudaSuccess) return DD_ERR_CUDA;
+    std::vector<double> hb(nrhs);
+    if (cudaMemcpyAsync(hb.data(), bb, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        return DD_ERR_CUDA;
+    if (cudaMemcpyAsync(hs.data(), outer, sizeof(CGState) * nrhs, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        return DD_ERR_CUDA;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return DD_ERR_CUDA;
+    bool conv = true;
+    for (int k = 0; k < nrhs; ++k) {
+        double rel = hb[k] > 0 ? std::sqrt(hs[k].rr / hb[k]) : 0.0;
+        if (relres) relres[k] = rel;
+        if (hs[k].active) conv = false;
+    }
+    if (iters) *iters = total;
+    return conv ? DD_OK : DD_ERR_NOT_CONVERGED;
+}
+
+}  // namespace
+
+int solve_packed(dd_handle* h, int nrhs, int field0, int step, int prec, double tol, int maxit, int* iters,
+                 double* relres) {
+    SolverVecs& v = h->vecs[0];
+    const long long Vh = h->g.Vh;
+    CGState* inner = h->d_cg;
+    CGState* outer = h->d_cg + h->prm.max_rhs;
+    if (prec == DD_PREC_F64) {
+        NormalCG<double, SpinorF64, SpinorF64, LinkF64> cg;
+        cg.h = h;
+        cg.nrhs = nrhs;
+        cg.x = SpinorF64{v.t64b, Vh};
+        cg.r = SpinorF64{v.re, Vh};
+        cg.p = SpinorF64{v.p64, Vh};
+        cg.q = SpinorF64{v.q64, Vh};
+        cg.z = SpinorF64{v.z64, Vh};
+        cg.ph = cg.p;
+        cg.rh = cg.r;
+        cg.th = SpinorF64{v.t64, Vh};
+        cg.copies = 0;
+        cg.lk = field_links<LinkF64>(h, field0);
+        cg.lk_rs = field_stride<LinkF64>(h, step);
+        cg.st = inner;
+        cg.outer = outer;
+        // the inner x must not alias the residual temporaries: use x64
+        cg.x = SpinorF64{v.x64, Vh};
+        return defect_correction(h, nrhs, field0, step, cg, true, tol, maxit, iters, relres);
+    } else if (prec == DD_PREC_F32) {
+        NormalCG<float, SpinorF32, SpinorF32, LinkF32> cg;
+        cg.h = h;
+        cg.nrhs = nrhs;
+        cg.x = SpinorF32{v.x32, Vh};
+        cg.r = SpinorF32{v.r32, Vh};
+        cg.p = SpinorF32{v.p32, Vh};
+        cg.q = SpinorF32{v.q32, Vh};
+        cg.z = SpinorF32{v.z32, Vh};
+        cg.ph = cg.p;
+        cg.rh = cg.r;
+        cg.th = SpinorF32{v.t32, Vh};
+        cg.copies = 0;
+        cg.lk = field_links<LinkF32>(h, field0);
+        cg.lk_rs = field_stride<LinkF32>(h, step);
+        cg.st = inner;
+        cg.outer = outer;
+        return defect_correction(h, nrhs, field0, step, cg, false, tol, maxit, iters, relres);
+    } else {
+        NormalCG<float, SpinorF32, SpinorF16, LinkF16> cg;
+        cg.h = h;
+        cg.nrhs = nrhs;
+        cg.x = SpinorF32{v.x32, Vh};
+        cg.r = SpinorF32{v.r32, Vh};
+        cg.p = SpinorF32{v.p32, Vh};
+        cg.q = SpinorF32{v.q32, Vh};
+        cg.z = SpinorF32{v.z32, Vh};
+        cg.ph = SpinorF16{v.p16, v.p16n, Vh};
+        cg.rh = SpinorF16{v.r16, v.r16n, Vh};
+        cg.th = SpinorF16{v.t16, v.t16n, Vh};
+        cg.copies = 1;
+        cg.lk = field_links<LinkF16>(h, field0);
+        cg.lk_rs = field_stride<LinkF16>(h, step);
+        cg.st = inner;
+        cg.outer = outer;
+        return defect_correction(h, nrhs, field0, step, cg, false, tol, maxit, iters, relres);
+    }
+}
+
+extern "C" int dd_solve(dd_t h, void* x, const void* b, const void* U, int nrhs, int prec, int* iters,
+                        double* relres) {
+    int rc = dd_require_ws(h);
+    if (rc) return rc;
+    if (!x || !b || !U || nrhs < 1 || nrhs > h->prm.max_rhs) return dd_fail(h, DD_ERR_INVALID_ARG, "dd_solve: bad arguments");
+    if (prec < DD_PREC_F64 || prec > DD_PREC_F16) return dd_fail(h, DD_ERR_INVALID_ARG, "dd_solve: unknown precision");
+    const long long V = h->g.V;
+    rc = format_field(h, (const double*)U, h->fields[0], true, prec == DD_PREC_F32, prec == DD_PREC_F16, false, false);
+    if (rc) return rc;
+    SolverVecs& v = h->vecs[0];
+    launch_pack_spinor_eo(h, (const double*)b, v.be, 0, nrhs, 24 * V);
+    launch_pack_spinor_eo(h, (const double*)b, v.bo, 1, nrhs, 24 * V);
+    DD_LAUNCH_CHECK(h, "dd_solve pack");
+    int it = 0;
+    rc = solve_packed(h, nrhs, 0, 0, prec, h->prm.tol_global, h->prm.maxit, &it, relres);
+    if (iters) *iters = it;
+    if (rc && rc != DD_ERR_NOT_CONVERGED) return dd_fail(h, rc, "dd_solve: solver failed");
+    launch_unpack_spinor_eo(h, v.xe, (double*)x, 0, nrhs, 24 * V);
+    launch_unpack_spinor_eo(h, v.xo, (double*)x, 1, nrhs, 24 * V);
+    DD_LAUNCH_CHECK(h, "dd_solve unpack");
+    if (rc == DD_ERR_NOT_CONVERGED) return dd_fail(h, rc, "dd_solve: iteration cap reached");
+    return DD_OK;
+}
