@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark of the hierarchical domain-decomposed step on GB300.
+
+Metric: global det-ratio estimates per second (one estimate = one
+interpolation factor with its own noise vector, solved to true relative
+residual 1e-10), mixed FP16/FP32 inner solver under FP64 defect correction.
+A step is one full pass of the hot path: heat-bath proposal on the active
+links, stochastic block filter (all Dirichlet block solves in one persistent
+launch), the global Schur-complement estimate with n_global factors and the
+global acceptance.  Default workload: 32^3 x 64 lattice, 8^4 blocks (6^4
+active sub-blocks), eps = 0.2, kappa = 0.1355, 12 global factors, 4 block
+factors, beta = 5.3.
+
+Output: one JSON line (rank 0).  `--impl reference` times the FP64 numpy
+oracle on a bounded sample of the same workload on the host cores.
+Multi-GPU (torchrun): every rank runs its own independent chain (no data-path
+collective); value = all ranks' estimates / max rank time (weak scaling).
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "det-ratio estimates/s (global Schur step, residual 1e-10, mixed FP16/FP32 + FP64 defect correction)"
+
+CONFIGS = {
+    # name: lattice, blocks, eps, kappa, gauge seed, global factors, block factors
+    "c2": dict(dims=(8, 8, 8, 8), block=(4, 4, 4, 4), eps=0.3, kappa=0.13, seed=2, n_global=16, n_block=4),
+    "c3": dict(dims=(16, 16, 16, 16), block=(8, 8, 8, 8), eps=0.25, kappa=0.135, seed=3, n_global=8, n_block=4),
+    "c5": dict(dims=(32, 32, 32, 64), block=(8, 8, 8, 8), eps=0.2, kappa=0.1355, seed=5, n_global=12, n_block=4),
+}
+BETA = 5.3
+# algorithmic bytes per output site of the eo hop kernels (input spinor + 8
+# links with two stored rows + output; FP16 spinor = 48 B + 4 B scale,
+# FP16 link rows = 24 B, FP32 spinor = 96 B, FP64 spinor 192 B, FP64 link 144 B)
+HOP_BYTES = {0: 52 + 8 * 24 + 52, 1: 52 + 8 * 24 + 96 + 96, 2: 192 + 8 * 144 + 192}
+HOP_FLOPS = 1320
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--config", default="c5", choices=sorted(CONFIGS))
+    p.add_argument("--prec", default="f16", choices=["f16", "f32", "f64"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--fp64-steps", type=int, default=0,
+                   help="also time this many steps with the plain FP64 solver (same workload)")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit())
+        smax = max(float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 3 + i and s[3 + i].strip().lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------ oracle arm
+def oracle_sample(cfg, seconds=20.0):
+    """Time the FP64 numpy oracle's Wilson operator at the full volume for a
+    bounded number of applications; returns seconds per application and the count."""
+    import numpy as np
+    from oracle import dirac, geometry
+    from paper_1112_1243_gb300 import synthetic
+    lat = geometry.Lattice(cfg["dims"], cfg["block"])
+    U = synthetic.random_gauge(cfg["dims"], cfg["eps"], cfg["seed"])
+    psi = synthetic.random_spinor(cfg["dims"], 1)
+    n, t = 0, 0.0
+    while t < seconds and n < 50:
+        t0 = time.perf_counter()
+        psi = dirac.apply_D(U, psi, lat, cfg["kappa"])
+        psi /= np.linalg.norm(psi)
+        t += time.perf_counter() - t0
+        n += 1
+    return t / n, n, t
+
+
+def site_hops_per_estimate_default(cfg_name):
+    """Full-lattice Wilson applications per global estimate, measured on the
+    GPU path (global solve only) and recorded in profiles/; used by the
+    reference arm, which runs without a GPU measurement of its own."""
+    path = os.path.join(ROOT, "profiles", "work_per_estimate.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)[cfg_name]["D_applications_per_estimate"])
+    except Exception:
+        return None
+
+
+def run_reference(args, cfg):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    napp = site_hops_per_estimate_default(args.config)
+    per_app, n, t = oracle_sample(cfg, seconds=15.0)
+    steps = []
+    for _ in range(args.warmup + args.steps):
+        pa, _, _ = oracle_sample(cfg, seconds=5.0)
+        steps.append(pa)
+    per_app = sum(steps[args.warmup:]) / max(1, args.steps)
+    if napp is None:
+        print(json.dumps({"impl": "reference", "unavailable": "no recorded GPU work-per-estimate for this config"}))
+        return 0
+    est_per_s = 1.0 / (napp * per_app)
+    V = math.prod(cfg["dims"])
+    line = {
+        "metric": METRIC, "value": est_per_s, "unit": "estimates/s", "impl": "reference",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per_app * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.config}: {'x'.join(map(str, cfg['dims']))} lattice, "
+                               f"{'x'.join(map(str, cfg['block']))} blocks, kappa {cfg['kappa']}, eps {cfg['eps']}"},
+        "cpu_baseline": {"value": est_per_s, "unit": "estimates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"numpy FP64 oracle apply_D at V={V}: {per_app:.3f} s per application "
+                                   f"(steps of >=5 s), scaled by {napp:.0f} Wilson applications per estimate "
+                                   f"(GPU-measured global-solve work; block solves not counted)"},
+        "e2e": {"value": est_per_s, "unit": "estimates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------- GPU arm
+def run_gpu(args, cfg):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1112_1243_gb300 import api, build, synthetic
+    from paper_1112_1243_gb300.chain import HierarchicalStep
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    prec = {"f16": api.DD_PREC_F16, "f32": api.DD_PREC_F32, "f64": api.DD_PREC_F64}[args.prec]
+    V = math.prod(cfg["dims"])
+    Vh = V // 2
+    nmax = max(cfg["n_global"], cfg["n_block"])
+    stream = torch.cuda.current_stream(dev)
+    h = api.dd_init(cfg["dims"], cfg["block"], cfg["kappa"], max_rhs=nmax, inner_prec=prec,
+                    block_prec=api.DD_PREC_F32, tol_global=1e-10, tol_block=1e-12, tol_inner=1e-3,
+                    maxit=40000, stream=stream, device=dev)
+    U_np = synthetic.random_gauge(cfg["dims"], cfg["eps"], cfg["seed"] + 1000 * rank)
+    U = torch.from_numpy(U_np).to(dev)
+    chain = HierarchicalStep(h, BETA, n_inner=1, n_block=cfg["n_block"], n_global=cfg["n_global"],
+                             seed=cfg["seed"] * 7919 + rank)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for k in range(args.warmup):
+        chain.step(U, k)
+    barrier()
+    api.dd_kernel_timer(h, 1, 0, 1)
+    l0 = api.dd_launch_count(h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    acc = []
+    with ClockSampler(local) as clocks:
+        e0.record(stream)
+        for k in range(args.steps):
+            ln, a = chain.step(U, args.warmup + k)
+        e1.record(stream)
+        barrier()
+    t_ms = e0.elapsed_time(e1)
+    launches = api.dd_launch_count(h) - l0
+    timing = {kind: api.dd_kernel_timer(h, 2, kind) for kind in (0, 1, 2)}
+    api.dd_kernel_timer(h, 0, 0)
+    t_max = t_ms
+    if world > 1:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    est = cfg["n_global"] * args.steps * world
+    value = est / (t_max / 1e3)
+    # dominant hop kernel: the kind with most time
+    kind = max(timing, key=lambda k: timing[k][0])
+    ms_k, cnt_k, sites_k = timing[kind]
+    peak, peak_src = peaks()
+    achieved = (sites_k * HOP_BYTES[kind] / 1e9) / (ms_k / 1e3) if ms_k > 0 else None
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "hop_traffic.json")) as f:
+            tr = json.load(f)
+        src = open(os.path.join(ROOT, "paper_1112_1243_gb300", "csrc", "dslash.cuh"), "rb").read()
+        import hashlib
+        if tr.get("dslash_sha256") == hashlib.sha256(src).hexdigest() and str(kind) in tr.get("bytes_per_site", {}):
+            traffic = tr["bytes_per_site"][str(kind)] * (sites_k / max(1, cnt_k))
+    except Exception:
+        traffic = None
+    # hop work per estimate (global solve only), for the CPU-baseline scaling
+    hop_sites = sum(timing[k][2] for k in (0, 1, 2))
+    D_apps_per_est = hop_sites / (2.0 * Vh) / max(1, cfg["n_global"] * args.steps) * 1.0
+    line = {
+        "metric": METRIC, "value": value, "unit": "estimates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"f16": "f16-storage/f32", "f32": "f32", "f64": "f64"}[args.prec] + "+f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.config}: {'x'.join(map(str, cfg['dims']))} lattice, "
+                               f"{'x'.join(map(str, cfg['block']))} blocks (6^4 active sub-blocks), eps {cfg['eps']}, "
+                               f"kappa {cfg['kappa']}, beta {BETA}, {cfg['n_global']} global + {cfg['n_block']} block "
+                               f"factors, residual 1e-10",
+                   "l2": "inputs larger than L2 (gauge field alone 1.2 GB)", "chains": world},
+        "roofline": {"bound": "hbm", "kernel": f"hop_eo_kernel kind {kind}",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "bytes_per_site": HOP_BYTES[kind], "launches_timed": cnt_k,
+                     "avg_launch_us": 1e3 * ms_k / max(1, cnt_k), "peak_source": peak_src},
+        "gpu_launches": launches,
+        "clocks": clocks.summary(),
+        "D_applications_per_estimate": D_apps_per_est,
+    }
+    # end to end through the public API with host buffers
+    if not args.no_e2e:
+        U_host = torch.empty(U.shape, dtype=U.dtype).pin_memory()
+        U_host.copy_(U.cpu())
+        ln_host = torch.empty(cfg["n_global"], dtype=torch.float64).pin_memory()
+        acc_host = torch.empty(1, dtype=torch.uint8).pin_memory()
+        U_dev = torch.empty_like(U)
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for k in range(args.steps):
+            chain.step_host(U_host, U_dev, 1000 + k, ln_host, acc_host)
+        f1.record(stream)
+        barrier()
+        te = f0.elapsed_time(f1)
+        if world > 1:
+            tt = torch.tensor([te], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        line["e2e"] = {"value": est / (te / 1e3), "unit": "estimates/s",
+                       "h2d_bytes_per_step": U.numel() * 16,
+                       "d2h_bytes_per_step": U.numel() * 16 + cfg["n_global"] * 8 + 1}
+    if args.fp64_steps > 0:
+        h64 = api.dd_init(cfg["dims"], cfg["block"], cfg["kappa"], max_rhs=nmax, inner_prec=api.DD_PREC_F64,
+                          block_prec=api.DD_PREC_F32, tol_global=1e-10, tol_block=1e-12, maxit=40000,
+                          stream=stream, device=dev)
+        c64 = HierarchicalStep(h64, BETA, n_inner=1, n_block=cfg["n_block"], n_global=cfg["n_global"],
+                               seed=cfg["seed"] * 7919 + rank)
+        U64 = torch.from_numpy(U_np).to(dev)
+        c64.step(U64, 0)
+        barrier()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for k in range(args.fp64_steps):
+            c64.step(U64, 1 + k)
+        g1.record(stream)
+        barrier()
+        line["fp64_value"] = cfg["n_global"] * args.fp64_steps / (g0.elapsed_time(g1) / 1e3)
+        del h64
+    if rank == 0 and not args.no_cpu_baseline:
+        per_app, n, t = oracle_sample(cfg, seconds=15.0)
+        line["cpu_baseline"] = {
+            "value": 1.0 / (max(D_apps_per_est, 1e-9) * per_app), "unit": "estimates/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"numpy FP64 oracle apply_D at V={V}: {n} applications in {t:.1f} s, scaled by "
+                      f"{D_apps_per_est:.0f} Wilson applications per estimate measured on this run "
+                      f"(global solve only; block solves not counted)"}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    cfg = CONFIGS[args.config]
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+    return run_gpu(args, cfg)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -241,6 +241,19 @@ int dd_status(dd_t h, int* device_status, long long* heatbath_fails);
 /* Message of the last error of this handle (static storage, never NULL). */
 const char* dd_last_error(dd_t h);
 
+/* Instrumentation (no counterpart in the paper).  dd_launch_count: kernels
+ * the handle has launched since dd_init (host, written before return).
+ * dd_kernel_timer: CUDA-event timing, on the handle's stream, of the
+ * even-odd hop kernel of one kind (0: FP16 in / FP16 out, 1: FP16 in / FP32
+ * out with the xpay term, 2: FP64).  op 1 = reset and start timing every
+ * `every`-th launch of each kind, op 0 = stop, op 2 = synchronise the stream
+ * and return the summed duration (ms), the number of timed launches and the
+ * output sites those launches processed (systems already converged in a
+ * batch are skipped and not counted) for `kind`; host pointers, may be NULL.
+ * Event recording adds well under a microsecond per timed launch. */
+int dd_launch_count(dd_t h, long long* launches);
+int dd_kernel_timer(dd_t h, int op, int kind, int every, double* total_ms, long long* timed, long long* sites);
+
 /* Release the handle's own tables; the workspace stays with the caller. */
 int dd_finalize(dd_t h);
 

@@ -85,6 +85,9 @@ SIGNATURES = {
     "dd_sync": [_P],
     "dd_status": [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_longlong)],
     "dd_last_error": [_P],
+    "dd_launch_count": [_P, ctypes.POINTER(ctypes.c_longlong)],
+    "dd_kernel_timer": [_P, _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong),
+                        ctypes.POINTER(ctypes.c_longlong)],
     "dd_finalize": [_P],
 }
 

@@ -212,6 +212,22 @@ def dd_last_error(h):
     return m.decode() if m else ""
 
 
+def dd_launch_count(h):
+    n = ctypes.c_longlong(0)
+    _check(h, _lib.load().dd_launch_count(h.ptr, ctypes.byref(n)))
+    return n.value
+
+
+def dd_kernel_timer(h, op, kind=0, every=1):
+    """op 1: start, 0: stop, 2: read -> (total ms, timed launches, sites processed)."""
+    ms = ctypes.c_double(0.0)
+    cnt = ctypes.c_longlong(0)
+    sites = ctypes.c_longlong(0)
+    _check(h, _lib.load().dd_kernel_timer(h.ptr, int(op), int(kind), int(every), ctypes.byref(ms),
+                                          ctypes.byref(cnt), ctypes.byref(sites)))
+    return ms.value, cnt.value, sites.value
+
+
 def dd_finalize(h):
     if h.ptr:
         rc = _lib.load().dd_finalize(h.ptr)

@@ -111,7 +111,32 @@ struct dd_handle {
     size_t lu_bytes = 0;
     std::string last_error;
     int num_sms = 0;
+    // instrumentation: kernels launched by this handle, and CUDA-event timing
+    // of the even-odd hop kernels (kinds: 0 FP16 -> FP16, 1 FP16 -> FP32 with
+    // xpay, 2 FP64), recorded on the handle's stream around every
+    // timer_every-th launch of a kind
+    unsigned long long launches = 0;
+    int timer_on = 0;
+    int timer_every = 1;
+    unsigned long long timer_seen[3] = {0, 0, 0};
+    std::vector<cudaEvent_t> timer_ev[3];
+    size_t timer_used[3] = {0, 0, 0};
+    unsigned long long* d_sites = nullptr;  // [3] output sites of the timed launches
 };
+
+// Launch a kernel and count it: DD_KLAUNCH(h, kern<<<grid, block, 0, h->stream>>>(args));
+#define DD_KLAUNCH(h, ...) ((__VA_ARGS__), ++(h)->launches)
+
+// next timing event of a kind (pool grows on demand)
+inline cudaEvent_t dd_timer_event(dd_handle* h, int kind) {
+    auto& v = h->timer_ev[kind];
+    if (h->timer_used[kind] == v.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        v.push_back(e);
+    }
+    return v[h->timer_used[kind]++];
+}
 
 // error plumbing
 int dd_fail(dd_handle* h, int code, const std::string& msg);

@@ -10,6 +10,8 @@
 // U_a(x - a) stored at the neighbour (parity 1 - p).
 #pragma once
 
+#include <type_traits>
+
 #include "dd_internal.h"
 #include "reduce.cuh"
 
@@ -43,6 +45,7 @@ struct HopArgs {
     int colour_mask;          // 3 = every site; else zero the output outside these block colours
     const CGState* st;        // per-rhs activity (may be null)
     Reduce red;               // |out|^2 reduction (red.op == FIN_NONE: off)
+    unsigned long long* sites;  // timed launches: output sites processed (may be null)
 };
 
 template <class LK>
@@ -103,6 +106,8 @@ __global__ void __launch_bounds__(128) hop_eo_kernel(HopArgs<SIn, SX, SOut, LK> 
     if (A.st && !A.st[rhs].active) return;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     const long long Vh = A.g.Vh;
+    if (A.sites && threadIdx.x == 0)
+        atomicAdd(A.sites, (unsigned long long)min((long long)blockDim.x, Vh - (long long)blockIdx.x * blockDim.x));
     double nrm = 0.0;
     if (h < A.g.Vh) {
         SIn in = at_rhs(A.in, rhs);
@@ -134,8 +139,31 @@ __global__ void __launch_bounds__(128) hop_eo_kernel(HopArgs<SIn, SX, SOut, LK> 
     if (A.red.op != FIN_NONE) grid_reduce(A.red, rhs, nrm, sh);
 }
 
+// timing class of a hop kernel instance (see dd_handle::timer_*), -1: not timed
+template <class SIn, class SOut>
+constexpr int hop_kind() {
+    return std::is_same<SIn, SpinorF16>::value && std::is_same<SOut, SpinorF16>::value   ? 0
+           : std::is_same<SIn, SpinorF16>::value && std::is_same<SOut, SpinorF32>::value ? 1
+           : std::is_same<SIn, SpinorF64>::value                                          ? 2
+                                                                                          : -1;
+}
+
 template <class R, class SIn, class SX, class SOut, class LK, int MASK>
-inline void launch_hop(const HopArgs<SIn, SX, SOut, LK>& A, int nrhs, cudaStream_t s) {
+inline void launch_hop(const HopArgs<SIn, SX, SOut, LK>& A, int nrhs, dd_handle* h) {
     dim3 grid(grid_for(A.g.Vh, 128), nrhs);
-    hop_eo_kernel<R, SIn, SX, SOut, LK, MASK><<<grid, 128, 0, s>>>(A);
+    constexpr int kind = hop_kind<SIn, SOut>();
+    bool timed = false;
+    if (kind >= 0 && MASK == 0 && h->timer_on) timed = (h->timer_seen[kind]++ % h->timer_every) == 0;
+    HopArgs<SIn, SX, SOut, LK> B = A;
+    B.sites = nullptr;
+    if (timed) {
+        cudaEvent_t e = dd_timer_event(h, kind);
+        if (e) cudaEventRecord(e, h->stream);
+        B.sites = h->d_sites + kind;
+    }
+    DD_KLAUNCH(h, hop_eo_kernel<R, SIn, SX, SOut, LK, MASK><<<grid, 128, 0, h->stream>>>(B));
+    if (timed) {
+        cudaEvent_t e = dd_timer_event(h, kind);
+        if (e) cudaEventRecord(e, h->stream);
+    }
 }

@@ -297,9 +297,9 @@ static int launch_blocks(dd_handle* h, int mode, const std::vector<BlockItem>& i
     A.status = h->d_status;
     int grid = std::min((int)items.size(), h->block_slots);
     if (A.inner_f64)
-        block_solve_kernel<double, SpinorF64, LinkF64><<<grid, 256, 0, h->stream>>>(A);
+        DD_KLAUNCH(h, block_solve_kernel<double, SpinorF64, LinkF64><<<grid, 256, 0, h->stream>>>(A));
     else
-        block_solve_kernel<float, SpinorF32, LinkF32><<<grid, 256, 0, h->stream>>>(A);
+        DD_KLAUNCH(h, block_solve_kernel<float, SpinorF32, LinkF32><<<grid, 256, 0, h->stream>>>(A));
     DD_LAUNCH_CHECK(h, "block_solve_kernel");
     return DD_OK;
 }
@@ -343,15 +343,15 @@ extern "C" int dd_block_filter(dd_t h, const void* U_old, void* U_new, int colou
         if (rc) return rc;
         int* d_base = h->d_imap;
         DD_CUDA(h, cudaMemcpyAsync(d_base, base.data(), sizeof(int) * g.nblocks, cudaMemcpyHostToDevice, h->stream));
-        sum_items_kernel<<<grid_for(g.nblocks, 128), 128, 0, h->stream>>>(g.nblocks, d_base, n, h->d_item_out, ln_b);
+        DD_KLAUNCH(h, sum_items_kernel<<<grid_for(g.nblocks, 128), 128, 0, h->stream>>>(g.nblocks, d_base, n, h->d_item_out, ln_b));
         DD_LAUNCH_CHECK(h, "sum_items_kernel");
     } else {
         return dd_fail(h, DD_ERR_INVALID_ARG, "dd_block_filter: unknown mode");
     }
-    block_accept_kernel<<<grid_for(h->g.nblocks, 128), 128, 0, h->stream>>>(h->g, colour_mask, ln_b, accept, seed, ctr);
+    DD_KLAUNCH(h, block_accept_kernel<<<grid_for(h->g.nblocks, 128), 128, 0, h->stream>>>(h->g, colour_mask, ln_b, accept, seed, ctr));
     if (h->n_active > 0)
-        restore_kernel<<<grid_for(h->n_active, 128), 128, 0, h->stream>>>(h->g, h->n_active, h->d_active_links, accept,
-                                                                        (const double*)U_old, (double*)U_new);
+        DD_KLAUNCH(h, restore_kernel<<<grid_for(h->n_active, 128), 128, 0, h->stream>>>(h->g, h->n_active, h->d_active_links, accept,
+                                                                        (const double*)U_old, (double*)U_new));
     DD_LAUNCH_CHECK(h, "block accept");
     return DD_OK;
 }
@@ -385,10 +385,10 @@ extern "C" int dd_det_ratio_estimate(dd_t h, const void* U_old, const void* U_ne
     const long long dd64_fs = (long long)(h->fields[1].dd64 - h->fields[0].dd64);
     dim3 gv(grid_for(g.V, 128), n);
     // 1. eta on black sites
-    noise_black_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], vs, DD_PURPOSE_GLOBAL_NOISE, seed, ctr);
+    DD_KLAUNCH(h, noise_black_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], vs, DD_PURPOSE_GLOBAL_NOISE, seed, ctr));
     // 2. w = C eta, w' = C' eta (onto white sites)
-    inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], bank[1], vs, (const double*)h->fields[0].canon, canon_fs, d_fold, 1);
-    inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], bank[2], vs, (const double*)h->fields[0].canon, canon_fs, d_fnew, 1);
+    DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], bank[1], vs, (const double*)h->fields[0].canon, canon_fs, d_fold, 1));
+    DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], bank[2], vs, (const double*)h->fields[0].canon, canon_fs, d_fnew, 1));
     DD_LAUNCH_CHECK(h, "schur stage 1-2");
     // 3. z = E^{-1} w, z' = E'^{-1} w'  (banks 1,2 are contiguous, so are 3,4)
     const int half = g.nblocks / 2;
@@ -401,8 +401,8 @@ extern "C" int dd_det_ratio_estimate(dd_t h, const void* U_old, const void* U_ne
     rc = launch_blocks(h, BLOCK_SOLVE, items, bank[1], bank[3], seed, ctr);
     if (rc) return rc;
     // 4. v = B z, v' = B' z' (onto black sites)
-    inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[3], bank[1], vs, (const double*)h->fields[0].canon, canon_fs, d_fold, 0);
-    inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[4], bank[2], vs, (const double*)h->fields[0].canon, canon_fs, d_fnew, 0);
+    DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[3], bank[1], vs, (const double*)h->fields[0].canon, canon_fs, d_fold, 0));
+    DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[4], bank[2], vs, (const double*)h->fields[0].canon, canon_fs, d_fnew, 0));
     DD_LAUNCH_CHECK(h, "schur stage 4");
     // 5. a = A^{-1} v
     items.clear();
@@ -411,10 +411,10 @@ extern "C" int dd_det_ratio_estimate(dd_t h, const void* U_old, const void* U_ne
     rc = launch_blocks(h, BLOCK_SOLVE, items, bank[1], bank[5], seed, ctr);
     if (rc) return rc;
     // 6. s = v' - A' a  -> bank 3
-    schur_source_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[2], bank[5], bank[3], vs, h->fields[0].dd64, dd64_fs, d_fnew);
+    DD_KLAUNCH(h, schur_source_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[2], bank[5], bank[3], vs, h->fields[0].dd64, dd64_fs, d_fnew));
     // 7. global solve D' y = (s, 0)
     SolverVecs& v = h->vecs[0];
-    dd_to_eo_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[3], vs, v.be, v.bo);
+    DD_KLAUNCH(h, dd_to_eo_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[3], vs, v.be, v.bo));
     DD_LAUNCH_CHECK(h, "schur stage 6-7");
     int iters = 0;
     rc = solve_packed(h, n, f_new[0], factors ? 1 : 0, h->prm.inner_prec, h->prm.tol_global, h->prm.maxit, &iters,
@@ -429,7 +429,7 @@ extern "C" int dd_det_ratio_estimate(dd_t h, const void* U_old, const void* U_ne
     red.op = FIN_STORE;
     red.status = h->d_status;
     dim3 gb(grid_for(g.V / 2, 128), n);
-    estimate_kernel<<<gb, 128, 0, h->stream>>>(g, c, bank[0], vs, v.xe, v.xo, red);
+    DD_KLAUNCH(h, estimate_kernel<<<gb, 128, 0, h->stream>>>(g, c, bank[0], vs, v.xe, v.xo, red));
     DD_LAUNCH_CHECK(h, "estimate_kernel");
     if (rc == DD_ERR_NOT_CONVERGED) return dd_fail(h, rc, "dd_det_ratio_estimate: global solve hit maxit");
     return DD_OK;
@@ -440,9 +440,9 @@ extern "C" int dd_global_accept(dd_t h, void* U, const void* U_old, const double
     int rc = dd_require_ws(h);
     if (rc) return rc;
     if (!U || !U_old || !ln_r || !accept || n < 1) return dd_fail(h, DD_ERR_INVALID_ARG, "dd_global_accept: bad arguments");
-    global_accept_kernel<<<1, 1, 0, h->stream>>>(ln_r, n, seed, ctr, accept, ln_margin);
+    DD_KLAUNCH(h, global_accept_kernel<<<1, 1, 0, h->stream>>>(ln_r, n, seed, ctr, accept, ln_margin));
     const long long m = (long long)h->g.V * 72;
-    conditional_copy_kernel<<<grid_for(m, 256), 256, 0, h->stream>>>(m, accept, (const double*)U_old, (double*)U);
+    DD_KLAUNCH(h, conditional_copy_kernel<<<grid_for(m, 256), 256, 0, h->stream>>>(m, accept, (const double*)U_old, (double*)U));
     DD_LAUNCH_CHECK(h, "global accept");
     return DD_OK;
 }

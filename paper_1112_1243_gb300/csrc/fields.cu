@@ -23,7 +23,7 @@ extern "C" int dd_noise(dd_t h, void* eta, int nrhs, int purpose, uint64_t seed,
     if (!eta || nrhs < 1 || purpose < 0 || purpose > 255) return dd_fail(h, DD_ERR_INVALID_ARG, "dd_noise: bad arguments");
     const long long n = (long long)h->g.V * 12;
     dim3 grid(grid_for(n, 256), nrhs);
-    noise_kernel<<<grid, 256, 0, h->stream>>>(h->g.V, (double*)eta, purpose, seed, ctr);
+    DD_KLAUNCH(h, noise_kernel<<<grid, 256, 0, h->stream>>>(h->g.V, (double*)eta, purpose, seed, ctr));
     DD_LAUNCH_CHECK(h, "noise_kernel");
     return DD_OK;
 }
@@ -53,7 +53,7 @@ __global__ void interpolate_kernel(long long nlinks, const double* __restrict__ 
 
 int launch_interpolate(dd_handle* h, const double* U, const double* Up, double* out, int num, int den) {
     const long long n = (long long)h->g.V * 4;
-    interpolate_kernel<<<grid_for(n, 128), 128, 0, h->stream>>>(n, U, Up, h->d_active_mask, out, num, den);
+    DD_KLAUNCH(h, interpolate_kernel<<<grid_for(n, 128), 128, 0, h->stream>>>(n, U, Up, h->d_active_mask, out, num, den));
     DD_LAUNCH_CHECK(h, "interpolate_kernel");
     return DD_OK;
 }
@@ -99,8 +99,8 @@ extern "C" int dd_plaquette(dd_t h, const void* U, double* out) {
     R_.out = out;
     R_.op = FIN_STORE;
     R_.status = h->d_status;
-    plaquette_kernel<<<grid_for(h->g.V, 128), 128, 0, h->stream>>>(h->g, (const double*)U, R_);
-    plaquette_scale_kernel<<<1, 1, 0, h->stream>>>(out, 1.0 / (18.0 * h->g.V));
+    DD_KLAUNCH(h, plaquette_kernel<<<grid_for(h->g.V, 128), 128, 0, h->stream>>>(h->g, (const double*)U, R_));
+    DD_KLAUNCH(h, plaquette_scale_kernel<<<1, 1, 0, h->stream>>>(out, 1.0 / (18.0 * h->g.V)));
     DD_LAUNCH_CHECK(h, "plaquette_kernel");
     return DD_OK;
 }

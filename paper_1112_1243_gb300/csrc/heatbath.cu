@@ -145,9 +145,9 @@ extern "C" int dd_gauge_update(dd_t h, void* U, int colour_mask, double beta, in
                         int gi = (col * 4 + a) * 2 + par;
                         int off = h->h_group_off[gi], cnt = h->h_group_off[gi + 1] - off;
                         if (cnt <= 0) continue;
-                        heatbath_kernel<<<grid_for(cnt, 64), 64, 0, h->stream>>>(
+                        DD_KLAUNCH(h, heatbath_kernel<<<grid_for(cnt, 64), 64, 0, h->stream>>>(
                             h->g, (double*)U, h->d_active_links + off, cnt, beta, kind > 0, sweep, seed, ctr,
-                            h->d_hb_fails);
+                            h->d_hb_fails));
                     }
     DD_LAUNCH_CHECK(h, "heatbath_kernel");
     return DD_OK;

@@ -172,7 +172,7 @@ int format_field(dd_handle* h, const double* U, FieldSlot& f, bool eo64, bool eo
     if (!eo16) t.eo16 = nullptr;
     if (!dd64) t.dd64 = nullptr;
     if (!dd32) t.dd32 = nullptr;
-    format_gauge_kernel<<<grid_for(h->g.V, 128), 128, 0, h->stream>>>(h->g, U, t);
+    DD_KLAUNCH(h, format_gauge_kernel<<<grid_for(h->g.V, 128), 128, 0, h->stream>>>(h->g, U, t));
     DD_LAUNCH_CHECK(h, "format_gauge_kernel");
     return DD_OK;
 }
@@ -230,19 +230,19 @@ __global__ void unpack_spinor_sub_kernel(long long Vh, const double2* __restrict
 }
 void launch_pack_spinor_sub(dd_handle* h, const double* in, double2* out, int nrhs) {
     dim3 grid(grid_for(h->g.Vh, 128), nrhs);
-    pack_spinor_sub_kernel<<<grid, 128, 0, h->stream>>>(h->g.Vh, in, out);
+    DD_KLAUNCH(h, pack_spinor_sub_kernel<<<grid, 128, 0, h->stream>>>(h->g.Vh, in, out));
 }
 void launch_unpack_spinor_sub(dd_handle* h, const double2* in, double* out, int nrhs) {
     dim3 grid(grid_for(h->g.Vh, 128), nrhs);
-    unpack_spinor_sub_kernel<<<grid, 128, 0, h->stream>>>(h->g.Vh, in, out);
+    DD_KLAUNCH(h, unpack_spinor_sub_kernel<<<grid, 128, 0, h->stream>>>(h->g.Vh, in, out));
 }
 void launch_pack_spinor_eo(dd_handle* h, const double* in, double2* out, int parity, int nrhs, long long in_rs) {
     dim3 grid(grid_for(h->g.Vh, 128), nrhs);
-    pack_spinor_eo_kernel<<<grid, 128, 0, h->stream>>>(h->g, in, out, parity, in_rs);
+    DD_KLAUNCH(h, pack_spinor_eo_kernel<<<grid, 128, 0, h->stream>>>(h->g, in, out, parity, in_rs));
 }
 void launch_unpack_spinor_eo(dd_handle* h, const double2* in, double* out, int parity, int nrhs, long long out_rs) {
     dim3 grid(grid_for(h->g.Vh, 128), nrhs);
-    unpack_spinor_eo_kernel<<<grid, 128, 0, h->stream>>>(h->g, in, out, parity, out_rs);
+    DD_KLAUNCH(h, unpack_spinor_eo_kernel<<<grid, 128, 0, h->stream>>>(h->g, in, out, parity, out_rs));
 }
 
 // canonical <-> block-ordered FP64 chunks ([blockpos][chunk][bsites])
@@ -276,11 +276,11 @@ __global__ void unpack_spinor_dd_kernel(Geo g, const double2* __restrict__ in, d
 }
 void launch_pack_spinor_dd(dd_handle* h, const double* in, double2* out, int nrhs) {
     dim3 grid(grid_for(h->g.V, 128), nrhs);
-    pack_spinor_dd_kernel<<<grid, 128, 0, h->stream>>>(h->g, in, out);
+    DD_KLAUNCH(h, pack_spinor_dd_kernel<<<grid, 128, 0, h->stream>>>(h->g, in, out));
 }
 void launch_unpack_spinor_dd(dd_handle* h, const double2* in, double* out, int nrhs) {
     dim3 grid(grid_for(h->g.V, 128), nrhs);
-    unpack_spinor_dd_kernel<<<grid, 128, 0, h->stream>>>(h->g, in, out);
+    DD_KLAUNCH(h, unpack_spinor_dd_kernel<<<grid, 128, 0, h->stream>>>(h->g, in, out));
 }
 
 // eo FP64 chunks -> FP32 / FP16 storage and back
@@ -379,11 +379,13 @@ void plan(dd_handle* h, char* base) {
     h->d_item_out = c.take<double>((size_t)h->items_cap);
     h->d_queue = c.take<int>(64);
     h->d_imap = c.take<int>((size_t)h->g.nblocks + 4 * R + 64);
-    // dense LU matrices of the exact check path (lattices up to 512 sites)
+    // dense LU matrices of the exact check path: D, the augmented block
+    // systems and Dhat of lattices up to 512 sites (at most 3 (12V)^2
+    // complex), or the batch of block operators of small blocks
     if (V <= 512) {
-        h->lu_bytes = (size_t)(12 * V) * (12 * V) * 16 * 2 + (size_t)(12 * V) * 64;
+        h->lu_bytes = (size_t)(12 * V) * (12 * V) * 16 * 3 + (size_t)(12 * V) * 64;
         h->d_lu = c.take<double>(h->lu_bytes / 8);
-    } else if (nb <= 256) {
+    } else if (nb <= 16 && h->g.nblocks <= 1024) {
         h->lu_bytes = (size_t)h->g.nblocks * (12 * nb) * (12 * nb) * 16 + (size_t)h->g.nblocks * 12 * nb * 8;
         h->d_lu = c.take<double>(h->lu_bytes / 8);
     } else {
@@ -495,11 +497,14 @@ extern "C" int dd_init(dd_t* out, const dd_params* p, void* stream) {
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_hb_fails, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(h->d_hb_fails, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_sites, 3 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(h->d_sites, 0, 3 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         cudaFree(h->d_active_links);
         cudaFree(h->d_active_mask);
         cudaFree(h->d_status);
         cudaFree(h->d_hb_fails);
+        cudaFree(h->d_sites);
         delete h;
         return DD_ERR_CUDA;
     }
@@ -584,12 +589,56 @@ extern "C" const char* dd_last_error(dd_t h) {
     return h->last_error.c_str();
 }
 
+extern "C" int dd_launch_count(dd_t h, long long* launches) {
+    if (!h || !launches) return DD_ERR_INVALID_ARG;
+    *launches = (long long)h->launches;
+    return DD_OK;
+}
+
+extern "C" int dd_kernel_timer(dd_t h, int op, int kind, int every, double* total_ms, long long* timed,
+                               long long* sites) {
+    if (!h || kind < 0 || kind > 2) return DD_ERR_INVALID_ARG;
+    if (op == 1) {
+        h->timer_on = 1;
+        h->timer_every = every > 0 ? every : 1;
+        for (int k = 0; k < 3; ++k) {
+            h->timer_used[k] = 0;
+            h->timer_seen[k] = 0;
+        }
+        DD_CUDA(h, cudaMemsetAsync(h->d_sites, 0, 3 * sizeof(unsigned long long), h->stream));
+        return DD_OK;
+    }
+    if (op == 0) {
+        h->timer_on = 0;
+        return DD_OK;
+    }
+    if (op != 2) return DD_ERR_INVALID_ARG;
+    DD_CUDA(h, cudaStreamSynchronize(h->stream));
+    double tot = 0.0;
+    long long cnt = 0;
+    for (size_t i = 0; i + 1 < h->timer_used[kind]; i += 2) {
+        float ms = 0.f;
+        DD_CUDA(h, cudaEventElapsedTime(&ms, h->timer_ev[kind][i], h->timer_ev[kind][i + 1]));
+        tot += ms;
+        ++cnt;
+    }
+    unsigned long long ns[3] = {0, 0, 0};
+    DD_CUDA(h, cudaMemcpy(ns, h->d_sites, sizeof(ns), cudaMemcpyDeviceToHost));
+    if (total_ms) *total_ms = tot;
+    if (timed) *timed = cnt;
+    if (sites) *sites = (long long)ns[kind];
+    return DD_OK;
+}
+
 extern "C" int dd_finalize(dd_t h) {
     if (!h) return DD_ERR_INVALID_ARG;
+    for (int k = 0; k < 3; ++k)
+        for (cudaEvent_t e : h->timer_ev[k]) cudaEventDestroy(e);
     cudaFree(h->d_active_links);
     cudaFree(h->d_active_mask);
     cudaFree(h->d_status);
     cudaFree(h->d_hb_fails);
+    cudaFree(h->d_sites);
     delete h;
     return DD_OK;
 }
@@ -628,17 +677,17 @@ int apply_eo_ops(dd_handle* h, int op, SS in_e, SS in_o, SS out_e, SS out_o, LK 
         auto A0 = mk_args(0, in_o, in_e, out_e, 1.0, -k, 1, g5);
         auto A1 = mk_args(1, in_e, in_o, out_o, 1.0, -k, 1, g5);
         if (mask_mode == 1) {
-            launch_hop<R, SS, SS, SS, LK, 1>(A0, nrhs, s);
-            launch_hop<R, SS, SS, SS, LK, 1>(A1, nrhs, s);
+            launch_hop<R, SS, SS, SS, LK, 1>(A0, nrhs, h);
+            launch_hop<R, SS, SS, SS, LK, 1>(A1, nrhs, h);
         } else {
-            launch_hop<R, SS, SS, SS, LK, 0>(A0, nrhs, s);
-            launch_hop<R, SS, SS, SS, LK, 0>(A1, nrhs, s);
+            launch_hop<R, SS, SS, SS, LK, 0>(A0, nrhs, h);
+            launch_hop<R, SS, SS, SS, LK, 0>(A1, nrhs, h);
         }
     } else if (op == DD_OP_INTER) {
         auto A0 = mk_args(0, in_o, in_e, out_e, 0.0, -k, 0, 0);
         auto A1 = mk_args(1, in_e, in_o, out_o, 0.0, -k, 0, 0);
-        launch_hop<R, SS, SS, SS, LK, 2>(A0, nrhs, s);
-        launch_hop<R, SS, SS, SS, LK, 2>(A1, nrhs, s);
+        launch_hop<R, SS, SS, SS, LK, 2>(A0, nrhs, h);
+        launch_hop<R, SS, SS, SS, LK, 2>(A1, nrhs, h);
     } else if (op == DD_OP_DTILDE || op == DD_OP_DTILDE_DAG) {
         // out_o used as the odd temporary: t = H_oe psi_e; out_e = psi_e - k^2 H_eo t
         int g5 = (op == DD_OP_DTILDE_DAG);
@@ -648,11 +697,11 @@ int apply_eo_ops(dd_handle* h, int op, SS in_e, SS in_o, SS out_e, SS out_o, LK 
         auto A0 = mk_args(0, out_o, in_e, out_e, 1.0, -k * k, 1, 0);
         A0.g5in = 0;
         A0.g5out = g5;
-        launch_hop<R, SS, SS, SS, LK, 0>(A1, nrhs, s);
-        launch_hop<R, SS, SS, SS, LK, 0>(A0, nrhs, s);
+        launch_hop<R, SS, SS, SS, LK, 0>(A1, nrhs, h);
+        launch_hop<R, SS, SS, SS, LK, 0>(A0, nrhs, h);
     } else if (op == DD_OP_HEO) {
         auto A0 = mk_args(0, in_o, in_e, out_e, 0.0, 1.0, 0, 0);
-        launch_hop<R, SS, SS, SS, LK, 0>(A0, nrhs, s);
+        launch_hop<R, SS, SS, SS, LK, 0>(A0, nrhs, h);
     } else {
         return DD_ERR_INVALID_ARG;
     }
@@ -694,20 +743,20 @@ static int apply_common(dd_handle* h, void* out, const void* in, const void* U, 
         rc = apply_eo_ops(h, op, be, bo, xe, xo, lk, nrhs, colour_mask, mask_mode);
     } else if (prec == DD_PREC_F32) {
         SpinorF32 ie{v.r32, Vh}, io{v.t32, Vh}, oe{v.p32, Vh}, oo{v.q32, Vh};
-        convert_from64_kernel<<<cg, 128, 0, h->stream>>>(Vh, be, ie);
-        convert_from64_kernel<<<cg, 128, 0, h->stream>>>(Vh, bo, io);
+        DD_KLAUNCH(h, convert_from64_kernel<<<cg, 128, 0, h->stream>>>(Vh, be, ie));
+        DD_KLAUNCH(h, convert_from64_kernel<<<cg, 128, 0, h->stream>>>(Vh, bo, io));
         LinkF32 lk{f.eo32, Vh};
         rc = apply_eo_ops(h, op, ie, io, oe, oo, lk, nrhs, colour_mask, mask_mode);
-        convert_to64_kernel<<<cg, 128, 0, h->stream>>>(Vh, oe, xe);
-        convert_to64_kernel<<<cg, 128, 0, h->stream>>>(Vh, oo, xo);
+        DD_KLAUNCH(h, convert_to64_kernel<<<cg, 128, 0, h->stream>>>(Vh, oe, xe));
+        DD_KLAUNCH(h, convert_to64_kernel<<<cg, 128, 0, h->stream>>>(Vh, oo, xo));
     } else {
         SpinorF16 ie{v.r16, v.r16n, Vh}, io{v.t16, v.t16n, Vh}, oe{v.p16, v.p16n, Vh}, oo{v.q16, v.q16n, Vh};
-        convert_from64_kernel<<<cg, 128, 0, h->stream>>>(Vh, be, ie);
-        convert_from64_kernel<<<cg, 128, 0, h->stream>>>(Vh, bo, io);
+        DD_KLAUNCH(h, convert_from64_kernel<<<cg, 128, 0, h->stream>>>(Vh, be, ie));
+        DD_KLAUNCH(h, convert_from64_kernel<<<cg, 128, 0, h->stream>>>(Vh, bo, io));
         LinkF16 lk{f.eo16, Vh};
         rc = apply_eo_ops(h, op, ie, io, oe, oo, lk, nrhs, colour_mask, mask_mode);
-        convert_to64_kernel<<<cg, 128, 0, h->stream>>>(Vh, oe, xe);
-        convert_to64_kernel<<<cg, 128, 0, h->stream>>>(Vh, oo, xo);
+        DD_KLAUNCH(h, convert_to64_kernel<<<cg, 128, 0, h->stream>>>(Vh, oe, xe));
+        DD_KLAUNCH(h, convert_to64_kernel<<<cg, 128, 0, h->stream>>>(Vh, oo, xo));
     }
     if (rc) return dd_fail(h, rc, "apply: unsupported operator");
     DD_LAUNCH_CHECK(h, "apply");

@@ -237,32 +237,32 @@ struct NormalCG {
     // z = Dtilde^dag r  (two hops), |z|^2 -> op
     void apply_dag_r(int op) {
         const double k2 = h->prm.kappa * h->prm.kappa;
-        launch_hop<R, SH, SM, SH, LK, 0>(args(1, rh, r, th, 0.0, 1.0, 0, 1, 0, FIN_NONE), nrhs, h->stream);
-        launch_hop<R, SH, SM, SM, LK, 0>(args(0, th, r, z, 1.0, -k2, 1, 0, 1, op), nrhs, h->stream);
+        launch_hop<R, SH, SM, SH, LK, 0>(args(1, rh, r, th, 0.0, 1.0, 0, 1, 0, FIN_NONE), nrhs, h);
+        launch_hop<R, SH, SM, SM, LK, 0>(args(0, th, r, z, 1.0, -k2, 1, 0, 1, op), nrhs, h);
     }
     // q = Dtilde p, |q|^2 -> alpha
     void apply_p() {
         const double k2 = h->prm.kappa * h->prm.kappa;
-        launch_hop<R, SH, SM, SH, LK, 0>(args(1, ph, p, th, 0.0, 1.0, 0, 0, 0, FIN_NONE), nrhs, h->stream);
-        launch_hop<R, SH, SM, SM, LK, 0>(args(0, th, p, q, 1.0, -k2, 1, 0, 0, FIN_ALPHA), nrhs, h->stream);
+        launch_hop<R, SH, SM, SH, LK, 0>(args(1, ph, p, th, 0.0, 1.0, 0, 0, 0, FIN_NONE), nrhs, h);
+        launch_hop<R, SH, SM, SM, LK, 0>(args(0, th, p, q, 1.0, -k2, 1, 0, 0, FIN_ALPHA), nrhs, h);
     }
     // solve Dtilde x = r (r holds the right-hand side; x starts at 0)
     int run(const double* rr0, double tol, double abs_fac, int maxit, int chunk, int* iters_out) {
         const long long n = h->g.Vh;
         dim3 grid(grid_for(n, 128), nrhs);
         if (maxit < 1) maxit = 1;
-        cg_arm_kernel<<<1, 64, 0, h->stream>>>(nrhs, st, outer, rr0, tol, abs_fac, maxit);
-        cg_start_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(n, x, r, rh, copies, st, outer);
+        DD_KLAUNCH(h, cg_arm_kernel<<<1, 64, 0, h->stream>>>(nrhs, st, outer, rr0, tol, abs_fac, maxit));
+        DD_KLAUNCH(h, cg_start_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(n, x, r, rh, copies, st, outer));
         apply_dag_r(FIN_ZZ_INIT);
-        cg_p_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(n, p, z, ph, copies, st);
+        DD_KLAUNCH(h, cg_p_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(n, p, z, ph, copies, st));
         std::vector<CGState> hs(nrhs);
         int done_iters = 0;
         for (;;) {
             for (int it = 0; it < chunk; ++it) {
                 apply_p();
-                cg_xr_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(n, x, r, p, q, rh, copies, st, red(FIN_RR));
+                DD_KLAUNCH(h, cg_xr_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(n, x, r, p, q, rh, copies, st, red(FIN_RR)));
                 apply_dag_r(FIN_BETA);
-                cg_p_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(n, p, z, ph, copies, st);
+                DD_KLAUNCH(h, cg_p_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(n, p, z, ph, copies, st));
             }
             done_iters += chunk;
             if (cudaGetLastError() != cudaSuccess) return DD_ERR_CUDA;
@@ -336,7 +336,7 @@ void hop64(dd_handle* h, int nrhs, int par, SpinorF64 in, SpinorF64 xin, SpinorF
     A.colour_mask = 3;
     A.st = st;
     A.red = red;
-    launch_hop<double, SpinorF64, SpinorF64, SpinorF64, LinkF64, 0>(A, nrhs, h->stream);
+    launch_hop<double, SpinorF64, SpinorF64, SpinorF64, LinkF64, 0>(A, nrhs, h);
 }
 
 __global__ void add_scalars_kernel(int n, double* a, const double* b) {
@@ -365,34 +365,34 @@ int defect_correction(dd_handle* h, int nrhs, int field0, int step, NormalCG<R, 
     Reduce none;
     none.op = FIN_NONE;
     // |b|^2 over both parities, then b~ = b_e + kappa H_eo b_o (in place)
-    norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(Vh, be, store_reduce(h, bb));
-    norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(Vh, bo, store_reduce(h, tmp));
-    add_scalars_kernel<<<1, 64, 0, h->stream>>>(nrhs, bb, tmp);
+    DD_KLAUNCH(h, norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(Vh, be, store_reduce(h, bb)));
+    DD_KLAUNCH(h, norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(Vh, bo, store_reduce(h, tmp)));
+    DD_KLAUNCH(h, add_scalars_kernel<<<1, 64, 0, h->stream>>>(nrhs, bb, tmp));
     hop64(h, nrhs, 0, bo, be, be, 1.0, kappa, 1, lk64, rs64, nullptr, none);
-    outer_arm_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, bb, tol);
-    zero64_kernel<<<grid, 128, 0, h->stream>>>(Vh, xe);
-    copy_kernel<SpinorF64, SpinorF64><<<grid, 128, 0, h->stream>>>(Vh, be, re, nullptr);
-    norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(Vh, re, store_reduce(h, rr));
-    outer_update_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, rr);
+    DD_KLAUNCH(h, outer_arm_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, bb, tol));
+    DD_KLAUNCH(h, zero64_kernel<<<grid, 128, 0, h->stream>>>(Vh, xe));
+    DD_KLAUNCH(h, copy_kernel<SpinorF64, SpinorF64><<<grid, 128, 0, h->stream>>>(Vh, be, re, nullptr));
+    DD_KLAUNCH(h, norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(Vh, re, store_reduce(h, rr)));
+    DD_KLAUNCH(h, outer_update_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, rr));
     if (cudaGetLastError() != cudaSuccess) return DD_ERR_CUDA;
     const double tol_inner = fp64_inner ? 0.0 : h->prm.tol_inner;
     int total = 0;
     std::vector<CGState> hs(nrhs);
     for (int cycle = 0; cycle < 200; ++cycle) {
         // inner right-hand side: the current FP64 residual
-        if (!fp64_inner) copy_kernel<SpinorF64, SM><<<grid, 128, 0, h->stream>>>(Vh, re, cg.r, outer);
+        if (!fp64_inner) DD_KLAUNCH(h, copy_kernel<SpinorF64, SM><<<grid, 128, 0, h->stream>>>(Vh, re, cg.r, outer));
         // inner stopping rule: FP64 inner aims at the outer target directly
         // (with margin), the mixed inner at a relative reduction tol_inner
         int it = 0;
         int rc = cg.run(rr, tol_inner, fp64_inner ? 0.25 : -1.0, maxit - total, 16, &it);
         total += it;
         if (rc) return rc;
-        add_correction_kernel<SM><<<grid, 128, 0, h->stream>>>(Vh, xe, cg.x, outer);
+        DD_KLAUNCH(h, add_correction_kernel<SM><<<grid, 128, 0, h->stream>>>(Vh, xe, cg.x, outer));
         // true residual r = b~ - Dtilde x (FP64)
         hop64(h, nrhs, 1, xe, xe, t64, 0.0, 1.0, 0, lk64, rs64, outer, none);
         hop64(h, nrhs, 0, t64, xe, t64b, 1.0, -kappa * kappa, 1, lk64, rs64, outer, none);
-        residual_kernel<<<grid, 128, 0, h->stream>>>(Vh, be, t64b, re, outer, store_reduce(h, rr));
-        outer_update_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, rr);
+        DD_KLAUNCH(h, residual_kernel<<<grid, 128, 0, h->stream>>>(Vh, be, t64b, re, outer, store_reduce(h, rr)));
+        DD_KLAUNCH(h, outer_update_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, rr));
         if (cudaGetLastError() != cudaSuccess) return DD_ERR_CUDA;
         if (cudaMemcpyAsync(hs.data(), outer, sizeof(CGState) * nrhs, cudaMemcpyDeviceToHost, h->stream) !=
             cudaSuccess)

@@ -18,6 +18,8 @@ The exponential is taken through the Hermitian eigendecomposition, and the
 result is re-unitarised (rows 1-2 orthonormalised, row 3 = conj(row1 x row2))
 so that every link is in SU(3) to rounding.
 """
+import os
+
 import numpy as np
 
 __all__ = ["gell_mann", "random_su3", "random_gauge", "random_spinor",
@@ -61,19 +63,27 @@ def _reunitarise(u):
     return np.stack([r0, r1, r2], axis=-2)
 
 
-def random_su3(shape, eps, rng, chunk=1 << 18):
-    """exp(i*eps*H) for H a Gaussian combination of Gell-Mann matrices."""
+def random_su3(shape, eps, rng, chunk=1 << 16):
+    """exp(i*eps*H) for H a Gaussian combination of Gell-Mann matrices.
+
+    The Gaussian weights are drawn in one sequential pass (so the result does
+    not depend on the chunking); the exponentials run in parallel chunks."""
+    from concurrent.futures import ThreadPoolExecutor
     lam = gell_mann()
     n = int(np.prod(shape)) if len(shape) else 1
+    w_all = rng.standard_normal((n, 8))
     out = np.empty((n, 3, 3), dtype=np.complex128)
-    for lo in range(0, n, chunk):
+
+    def work(lo):
         hi = min(n, lo + chunk)
-        w = rng.standard_normal((hi - lo, 8))
-        h = np.einsum("nk,kij->nij", w, lam)
+        h = np.einsum("nk,kij->nij", w_all[lo:hi], lam)
         ev, vec = np.linalg.eigh(h)
         ph = np.exp(1j * eps * ev)
         u = np.einsum("nik,nk,njk->nij", vec, ph, np.conj(vec))
         out[lo:hi] = _reunitarise(u)
+
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        list(ex.map(work, range(0, n, chunk)))
     return out.reshape(tuple(shape) + (3, 3))
 
 
