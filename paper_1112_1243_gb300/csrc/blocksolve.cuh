@@ -303,22 +303,26 @@ __global__ void __launch_bounds__(256) block_solve_kernel(BlockArgs A) {
         double rr = bb;
         int outer = 0;
         while (rr > A.tol2 * bb && outer < A.max_outer) {
-            // inner right-hand side: the FP64 residual
+            // inner right-hand side: the FP64 residual, normalised to unit norm
+            const double rn = sqrt(rr), rinv = 1.0 / rn;
             for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
-                Spinor<RI> v;
+                Spinor<double> v;
                 rv.load(j, v);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) v.c[k] = rinv * v.c[k];
                 ri.store(j, v);
             }
             __syncthreads();
             block_cgnr<RI>(c, xi, ri, pi, qi, zi, lsoli, A.tol2_inner, A.maxit_inner, sh);
-            // x += e; r = b - D_b x (FP64)
+            // x += |r| e; r = b - D_b x (FP64)
             for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
                 Spinor<double> a;
                 Spinor<RI> e;
                 xv.load(j, a);
                 xi.load(j, e);
 #pragma unroll
-                for (int k = 0; k < 12; ++k) a.c[k] = a.c[k] + mk<double>((double)e.c[k].x, (double)e.c[k].y);
+                for (int k = 0; k < 12; ++k)
+                    a.c[k] = a.c[k] + rn * mk<double>((double)e.c[k].x, (double)e.c[k].y);
                 xv.store(j, a);
             }
             __syncthreads();

@@ -144,7 +144,9 @@ struct SpinorF16 {
         float m = 0.f;
 #pragma unroll
         for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf((float)s.c[k].x), fabsf((float)s.c[k].y)));
-        float inv = m > 0.f ? 1.0f / m : 0.f;
+        // a site whose largest entry is below 1e-30 is stored as zero (1/m would overflow)
+        float inv = m > 1e-30f ? 1.0f / m : 0.f;
+        if (!(m > 1e-30f)) m = 0.f;
         nrm[i] = m;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {

@@ -126,19 +126,40 @@ __global__ void outer_arm_kernel(int nrhs, CGState* outer, const double* bb, dou
     outer[r] = c;
 }
 
-// x64 += e (any storage), r64 = b - t (with |r|^2), v = 0, copies
+// x64 += scale * e (any storage; scale = |r_outer| when the inner system was
+// normalised, rr = null: 1), r64 = b - t (with |r|^2), v = 0, copies
 template <class SE>
-__global__ void add_correction_kernel(long long n, SpinorF64 x, SE e, const CGState* outer) {
+__global__ void add_correction_kernel(long long n, SpinorF64 x, SE e, const double* rr, const CGState* outer) {
     const int rhs = blockIdx.y;
     if (outer && !outer[rhs].active) return;
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const double sc = rr ? sqrt(rr[rhs]) : 1.0;
     Spinor<double> a, b;
     at_rhs(x, rhs).load(i, a);
     at_rhs(e, rhs).load(i, b);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) a.c[k] = a.c[k] + b.c[k];
+    for (int k = 0; k < 12; ++k) a.c[k] = a.c[k] + sc * b.c[k];
     at_rhs(x, rhs).store(i, a);
+}
+// out = in / |in| (|in|^2 given per rhs): the inner solver always sees a
+// unit-norm right-hand side, so FP32 squares neither underflow nor overflow
+template <class SOut>
+__global__ void normalised_copy_kernel(long long n, SpinorF64 in, SOut out, const double* rr, const CGState* outer) {
+    const int rhs = blockIdx.y;
+    if (outer && !outer[rhs].active) return;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double inv = rr[rhs] > 0.0 ? 1.0 / sqrt(rr[rhs]) : 0.0;
+    Spinor<double> a;
+    at_rhs(in, rhs).load(i, a);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) a.c[k] = inv * a.c[k];
+    at_rhs(out, rhs).store(i, a);
+}
+__global__ void fill_kernel(int n, double* p, double v) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
 }
 __global__ void __launch_bounds__(128) residual_kernel(long long n, SpinorF64 b, SpinorF64 t, SpinorF64 r,
                                                        const CGState* outer, Reduce red) {
@@ -362,6 +383,7 @@ int defect_correction(dd_handle* h, int nrhs, int field0, int step, NormalCG<R, 
     double* bb = h->d_scalars;
     double* tmp = h->d_scalars + nrhs;
     double* rr = h->d_scalars + 2 * nrhs;
+    double* ones = h->d_scalars + 3 * nrhs;
     Reduce none;
     none.op = FIN_NONE;
     // |b|^2 over both parities, then b~ = b_e + kappa H_eo b_o (in place)
@@ -380,14 +402,19 @@ int defect_correction(dd_handle* h, int nrhs, int field0, int step, NormalCG<R, 
     std::vector<CGState> hs(nrhs);
     for (int cycle = 0; cycle < 200; ++cycle) {
         // inner right-hand side: the current FP64 residual
-        if (!fp64_inner) DD_KLAUNCH(h, copy_kernel<SpinorF64, SM><<<grid, 128, 0, h->stream>>>(Vh, re, cg.r, outer));
+        // (the mixed inner system is normalised to |r| = 1)
+        if (!fp64_inner) {
+            DD_KLAUNCH(h, normalised_copy_kernel<SM><<<grid, 128, 0, h->stream>>>(Vh, re, cg.r, rr, outer));
+            DD_KLAUNCH(h, fill_kernel<<<1, 64, 0, h->stream>>>(nrhs, ones, 1.0));
+        }
         // inner stopping rule: FP64 inner aims at the outer target directly
         // (with margin), the mixed inner at a relative reduction tol_inner
         int it = 0;
-        int rc = cg.run(rr, tol_inner, fp64_inner ? 0.25 : -1.0, maxit - total, 16, &it);
+        int rc = cg.run(fp64_inner ? rr : ones, tol_inner, fp64_inner ? 0.25 : -1.0, maxit - total, 16, &it);
         total += it;
         if (rc) return rc;
-        DD_KLAUNCH(h, add_correction_kernel<SM><<<grid, 128, 0, h->stream>>>(Vh, xe, cg.x, outer));
+        DD_KLAUNCH(h, add_correction_kernel<SM><<<grid, 128, 0, h->stream>>>(Vh, xe, cg.x, fp64_inner ? nullptr : rr,
+                                                                          outer));
         // true residual r = b~ - Dtilde x (FP64)
         hop64(h, nrhs, 1, xe, xe, t64, 0.0, 1.0, 0, lk64, rs64, outer, none);
         hop64(h, nrhs, 0, t64, xe, t64b, 1.0, -kappa * kappa, 1, lk64, rs64, outer, none);
