@@ -254,6 +254,36 @@ const char* dd_last_error(dd_t h);
 int dd_launch_count(dd_t h, long long* launches);
 int dd_kernel_timer(dd_t h, int op, int kind, int every, double* total_ms, long long* timed, long long* sites);
 
+/* Allocation-free block log-ratios (the paper has no counterpart: this is an
+ * interface variant for callers that cannot allocate device memory — code
+ * running while a CUDA graph is captured in global mode, where cudaMalloc is
+ * illegal; plug-ins whose host application owns all device memory; loops that
+ * cannot afford the implicit device synchronisation of cudaMalloc/cudaFree).
+ * It needs no handle and no workspace and calls no allocating routine.
+ * Computes, for every block of the colours in colour_mask, the one-factor
+ * stochastic log-ratio of the block filter,
+ *   ln_b[block id] = -(2 Re<eta, d> + |d|^2),  d = D_b[U_new]^{-1} (D_b[U_old] - D_b[U_new]) eta_b,
+ * eta_b from purpose DD_PURPOSE_BLOCK_NOISE, sub 0 (the values dd_block_filter
+ * gives for n = 1 when U_new differs from U_old only on active links);
+ * 0 for the other blocks.  Same solver as dd_block_filter: FP32 inner CG,
+ * FP64 defect correction to relative residual tol_block.
+ * dims/block: host arrays (extents even, blocks per direction even and >= 2);
+ * U_old, U_new: device, canonical FP64 gauge fields; ln_b: device, nblocks
+ * doubles.  Work is enqueued on `stream` (a cudaStream_t, NULL = default).
+ * Scratch: one file-scope device array of 64 MiB, held by every GPU that
+ * loads the library until the process exits; a block may have at most
+ * 64 MiB / 1248 B (about 53000) sites, else DD_ERR_UNSUPPORTED.  The first
+ * call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream
+ * capture.  Every call shares the array: calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  Returns DD_OK, DD_ERR_INVALID_ARG, DD_ERR_UNSUPPORTED or
+ * DD_ERR_CUDA (launch errors only; results are valid after the stream is
+ * synchronised). */
+int dd_block_ratios_noalloc(const int dims[4], const int block[4], double kappa, int bc_time, int colour_mask,
+                            const void* U_old, const void* U_new, uint64_t seed, uint64_t ctr, double tol_block,
+                            double* ln_b, void* stream);
+
 /* Release the handle's own tables; the workspace stays with the caller. */
 int dd_finalize(dd_t h);
 

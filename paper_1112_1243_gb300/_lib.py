@@ -88,6 +88,8 @@ SIGNATURES = {
     "dd_launch_count": [_P, ctypes.POINTER(ctypes.c_longlong)],
     "dd_kernel_timer": [_P, _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong),
                         ctypes.POINTER(ctypes.c_longlong)],
+    "dd_block_ratios_noalloc": [ctypes.POINTER(_I), ctypes.POINTER(_I), _D, _I, _I, _P, _P, _U64, _U64, _D, _P,
+                                _P],
     "dd_finalize": [_P],
 }
 

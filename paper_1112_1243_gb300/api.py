@@ -228,6 +228,21 @@ def dd_kernel_timer(h, op, kind=0, every=1):
     return ms.value, cnt.value, sites.value
 
 
+def dd_block_ratios_noalloc(dims, block, kappa, bc_time, colour_mask, U_old, U_new, seed, ctr, tol_block, ln_b,
+                            stream=None):
+    """Allocation-free one-factor block log-ratios (no handle, no workspace);
+    ln_b is a caller-owned device tensor of nblocks doubles."""
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    b = (ctypes.c_int * 4)(*[int(v) for v in block])
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    rc = _lib.load().dd_block_ratios_noalloc(d, b, float(kappa), int(bc_time), int(colour_mask), _ptr(U_old),
+                                             _ptr(U_new), int(seed), int(ctr), float(tol_block), _ptr(ln_b),
+                                             ctypes.c_void_p(s))
+    if rc != _lib.DD_OK:
+        raise DDError(rc, "dd_block_ratios_noalloc failed")
+    return ln_b
+
+
 def dd_finalize(h):
     if h.ptr:
         rc = _lib.load().dd_finalize(h.ptr)
