@@ -36,6 +36,8 @@ CONFIGS = {
     "c2": dict(dims=(8, 8, 8, 8), block=(4, 4, 4, 4), eps=0.3, kappa=0.13, seed=2, n_global=16, n_block=4),
     "c3": dict(dims=(16, 16, 16, 16), block=(8, 8, 8, 8), eps=0.25, kappa=0.135, seed=3, n_global=8, n_block=4),
     "c5": dict(dims=(32, 32, 32, 64), block=(8, 8, 8, 8), eps=0.2, kappa=0.1355, seed=5, n_global=12, n_block=4),
+    # smaller volume of the same physics for kernel captures (inputs still larger than L2)
+    "c5s": dict(dims=(32, 32, 32, 48), block=(8, 8, 8, 8), eps=0.2, kappa=0.1355, seed=5, n_global=12, n_block=4),
 }
 BETA = 5.3
 # algorithmic bytes per output site of the eo hop kernels (input spinor + 8
@@ -57,6 +59,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--fp64-steps", type=int, default=0,
                    help="also time this many steps with the plain FP64 solver (same workload)")
+    p.add_argument("--mode", default="step", choices=["step", "solve"],
+                   help="step: the hierarchical step (the benchmark); solve: one-rhs global solves on a lean "
+                        "handle (kernel captures and Dslash GB/s)")
     return p.parse_args()
 
 
@@ -276,6 +281,9 @@ def run_gpu(args, cfg):
         "gpu_launches": launches,
         "clocks": clocks.summary(),
         "D_applications_per_estimate": D_apps_per_est,
+        "dslash_GBps": {name: (timing[k][2] * HOP_BYTES[k] / 1e9 / (timing[k][0] / 1e3) if timing[k][0] > 0 else None)
+                        for k, name in ((0, "fp16_to_fp16"), (1, "fp16_to_fp32_xpay"), (2, "fp64"))},
+        "block_accept_rate_last_step": float(chain.acc_b.float().mean().item()),
     }
     # end to end through the public API with host buffers
     if not args.no_e2e:
@@ -331,11 +339,48 @@ def run_gpu(args, cfg):
     return 0
 
 
+def run_solve(args, cfg):
+    """Global solves D x = b (one right-hand side) on a handle planned for
+    solves only: the hop kernels of the hot path at a few GB of device memory."""
+    import torch
+    from paper_1112_1243_gb300 import api, build, synthetic
+    build.build()
+    dev = torch.device("cuda", 0)
+    prec = {"f16": api.DD_PREC_F16, "f32": api.DD_PREC_F32, "f64": api.DD_PREC_F64}[args.prec]
+    h = api.dd_init(cfg["dims"], cfg["block"], cfg["kappa"], max_rhs=1, inner_prec=prec, tol_global=1e-10,
+                    maxit=40000, features=api.DD_FEAT_SOLVE, device=dev)
+    U = torch.from_numpy(synthetic.random_gauge(cfg["dims"], cfg["eps"], cfg["seed"])).to(dev)
+    b = torch.from_numpy(synthetic.random_spinor(cfg["dims"], 1)).to(dev)
+    x = torch.zeros_like(b)
+    for _ in range(args.warmup):
+        api.dd_solve(h, x, b, U, 1, prec)
+    torch.cuda.synchronize()
+    api.dd_kernel_timer(h, 1, 0, 1)
+    t0 = time.perf_counter()
+    its = 0
+    for _ in range(args.steps):
+        it, res, _ = api.dd_solve(h, x, b, U, 1, prec)
+        its += it
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    out = {"mode": "solve", "config": args.config, "prec": args.prec, "seconds_per_solve": t / args.steps,
+           "inner_iterations_per_solve": its / args.steps, "relres": res[0]}
+    for kind in (0, 1, 2):
+        ms, cnt, sites = api.dd_kernel_timer(h, 2, kind)
+        if cnt:
+            out[f"hop_kind{kind}"] = {"launches": cnt, "avg_us": 1e3 * ms / cnt,
+                                      "GB_per_s": sites * HOP_BYTES[kind] / 1e9 / (ms / 1e3)}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     cfg = CONFIGS[args.config]
     if args.impl == "reference":
         return run_reference(args, cfg)
+    if args.mode == "solve":
+        return run_solve(args, cfg)
     return run_gpu(args, cfg)
 
 

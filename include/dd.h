@@ -107,7 +107,14 @@ typedef struct {
     double tol_block;  /* true relative residual of Dirichlet block solves */
     double tol_inner;  /* residual reduction asked of one inner solve (defect correction) */
     int maxit;         /* iteration cap of any single Krylov solve */
+    int features;      /* workspace parts to plan: DD_FEAT_* bits, 0 = all */
 } dd_params;
+
+/* workspace features (dd_params.features); entry points that need a part the
+ * workspace was not planned with fail with DD_ERR_UNSUPPORTED */
+#define DD_FEAT_SOLVE 1    /* dd_apply_D, dd_apply_D_block, dd_solve */
+#define DD_FEAT_ESTIMATE 2 /* dd_det_ratio_estimate, dd_block_filter (stochastic), dd_interpolate-based paths */
+#define DD_FEAT_EXACT 4    /* dd_logdet_exact, exact block filter */
 
 /* Fill p with defaults: kappa 0.125, bc_time -1, DD_ACTIVE_AUTO, max_rhs 1,
  * inner F16, block F32, tol_global 1e-10, tol_block 1e-12, tol_inner 1e-3,

@@ -56,7 +56,11 @@ class dd_params(ctypes.Structure):
         ("tol_block", ctypes.c_double),
         ("tol_inner", ctypes.c_double),
         ("maxit", ctypes.c_int),
+        ("features", ctypes.c_int),
     ]
+
+
+DD_FEAT_SOLVE, DD_FEAT_ESTIMATE, DD_FEAT_EXACT = 1, 2, 4
 
 
 _P = ctypes.c_void_p

@@ -70,7 +70,7 @@ def dd_default_params():
 
 def dd_init(dims, block, kappa, bc_time=-1, active_mode=_lib.DD_ACTIVE_AUTO, max_rhs=1,
             inner_prec=_lib.DD_PREC_F16, block_prec=_lib.DD_PREC_F32, tol_global=1e-10,
-            tol_block=1e-12, tol_inner=1e-3, maxit=20000, stream=None, device=None):
+            tol_block=1e-12, tol_inner=1e-3, maxit=20000, stream=None, device=None, features=0):
     """Create a handle and give it a torch-allocated workspace on `device`."""
     lib = _lib.load()
     p = dd_default_params()
@@ -87,6 +87,7 @@ def dd_init(dims, block, kappa, bc_time=-1, active_mode=_lib.DD_ACTIVE_AUTO, max
     p.tol_block = float(tol_block)
     p.tol_inner = float(tol_inner)
     p.maxit = int(maxit)
+    p.features = int(features)
     device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
     if stream is None:
         stream = torch.cuda.current_stream(device)

@@ -111,6 +111,7 @@ struct dd_handle {
     size_t lu_bytes = 0;
     std::string last_error;
     int num_sms = 0;
+    bool feat_solve = true, feat_estimate = true, feat_exact = true;  // planned workspace parts
     // instrumentation: kernels launched by this handle, and CUDA-event timing
     // of the even-odd hop kernels (kinds: 0 FP16 -> FP16, 1 FP16 -> FP32 with
     // xpay, 2 FP64), recorded on the handle's stream around every
@@ -153,6 +154,10 @@ int dd_cuda_check(dd_handle* h, cudaError_t e, const char* where);
     } while (0)
 
 int dd_require_ws(dd_handle* h);
+// DD_ERR_UNSUPPORTED unless the workspace was planned with the feature
+inline int dd_require_feature(dd_handle* h, bool planned, const char* what) {
+    return planned ? DD_OK : dd_fail(h, DD_ERR_UNSUPPORTED, std::string(what) + ": workspace planned without this feature");
+}
 
 // exact block log-determinant ratios of the block filter (lu.cu)
 int block_filter_exact(dd_handle* h, const double* U_old, const double* U_new, int colour_mask, double* ln_b);

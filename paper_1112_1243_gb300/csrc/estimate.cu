@@ -309,6 +309,8 @@ extern "C" int dd_block_filter(dd_t h, const void* U_old, void* U_new, int colou
                                uint64_t seed, uint64_t ctr, double* ln_b, uint8_t* accept) {
     int rc = dd_require_ws(h);
     if (rc) return rc;
+    rc = dd_require_feature(h, h->feat_estimate, "dd_block_filter");
+    if (rc) return rc;
     if (!U_old || !U_new || !ln_b || !accept || n < 1 || n > h->prm.max_rhs || colour_mask < 1 || colour_mask > 3)
         return dd_fail(h, DD_ERR_INVALID_ARG, "dd_block_filter: bad arguments");
     if (mode == DD_FILTER_EXACT) {
@@ -359,6 +361,8 @@ extern "C" int dd_block_filter(dd_t h, const void* U_old, void* U_new, int colou
 extern "C" int dd_det_ratio_estimate(dd_t h, const void* U_old, const void* U_new, int n, uint64_t seed,
                                      uint64_t ctr, int mode, double* ln_out) {
     int rc = dd_require_ws(h);
+    if (rc) return rc;
+    rc = dd_require_feature(h, h->feat_estimate, "dd_det_ratio_estimate");
     if (rc) return rc;
     if (!U_old || !U_new || !ln_out || n < 1 || n > h->prm.max_rhs || (mode != DD_EST_FACTORS && mode != DD_EST_REPLICAS))
         return dd_fail(h, DD_ERR_INVALID_ARG, "dd_det_ratio_estimate: bad arguments");

@@ -323,19 +323,32 @@ void plan(dd_handle* h, char* base) {
     Carver c{base};
     const long long V = h->g.V, Vh = h->g.Vh;
     const int R = h->prm.max_rhs;
+    const int feat = h->prm.features ? h->prm.features : (DD_FEAT_SOLVE | DD_FEAT_ESTIMATE | DD_FEAT_EXACT);
+    const bool est = feat & DD_FEAT_ESTIMATE;
+    const bool solve = est || (feat & DD_FEAT_SOLVE);
+    // gauge-field slots: slot 0 always (eo formats; block-order copies with
+    // the estimator), slots 1..R (interpolated fields) with the estimator
     h->fields.assign(R + 1, FieldSlot{});
-    for (int k = 0; k <= R; ++k) {
+    for (int k = 0; k <= (est ? R : 0); ++k) {
         FieldSlot& f = h->fields[k];
         f.eo64 = c.take<double2>((size_t)2 * 4 * 9 * Vh);
         f.eo32 = c.take<float4>((size_t)2 * 4 * 3 * Vh);
         f.eo16 = c.take<uint2>((size_t)2 * 4 * 3 * Vh);
-        f.dd64 = c.take<double2>((size_t)4 * 9 * V);
-        f.dd32 = c.take<float4>((size_t)4 * 3 * V);
-        f.canon = c.take<double2>((size_t)4 * 9 * V);
+        if (est) {
+            f.dd64 = c.take<double2>((size_t)4 * 9 * V);
+            f.dd32 = c.take<float4>((size_t)4 * 3 * V);
+            f.canon = c.take<double2>((size_t)4 * 9 * V);
+        }
     }
+    h->feat_solve = solve;
+    h->feat_estimate = est;
+    h->feat_exact = feat & DD_FEAT_EXACT;
     // global-solver vectors: each array holds R consecutive systems
     h->vecs.assign(1, SolverVecs{});
     SolverVecs& v = h->vecs[0];
+    const int Rv = solve ? R : 0;  // no solver vectors without the solver
+    {
+    const int R = Rv;
     v.be = c.take<double2>((size_t)R * 12 * Vh);
     v.bo = c.take<double2>((size_t)R * 12 * Vh);
     v.xe = c.take<double2>((size_t)R * 12 * Vh);
@@ -361,8 +374,9 @@ void plan(dd_handle* h, char* base) {
     v.t16n = c.take<float>((size_t)R * Vh);
     v.q16 = c.take<uint4>((size_t)R * 3 * Vh);
     v.q16n = c.take<float>((size_t)R * Vh);
-    // block-ordered FP64 vectors: 6 banks of R vectors
-    h->dd_vec = c.take<double2>((size_t)6 * R * 12 * V);
+    }
+    // block-ordered FP64 vectors: 6 banks of R vectors (estimator)
+    h->dd_vec = c.take<double2>(est ? (size_t)6 * R * 12 * V : 0);
     h->d_cg = c.take<CGState>((size_t)2 * R + 2);
     h->partials_cap = (size_t)(grid_for(std::max(Vh, V), 128) + 64) * (R + 1) * 2;
     h->d_partials = c.take<double>(h->partials_cap);
@@ -373,7 +387,7 @@ void plan(dd_handle* h, char* base) {
     // 4 FP64 vectors + 5 inner vectors (FP64 at most) of one block
     h->block_slot_bytes = ((size_t)nb * (4 * 192 + 5 * 192) + 4096 + 255) & ~(size_t)255;
     h->block_slots = std::max(1, h->num_sms) * 2;
-    h->block_scratch = c.take<char>(h->block_slot_bytes * h->block_slots);
+    h->block_scratch = c.take<char>(est ? h->block_slot_bytes * h->block_slots : 0);
     h->items_cap = h->g.nblocks * 2 * R + 64;
     h->d_items = c.take<int>((size_t)4 * h->items_cap);
     h->d_item_out = c.take<double>((size_t)h->items_cap);
@@ -382,7 +396,10 @@ void plan(dd_handle* h, char* base) {
     // dense LU matrices of the exact check path: D, the augmented block
     // systems and Dhat of lattices up to 512 sites (at most 3 (12V)^2
     // complex), or the batch of block operators of small blocks
-    if (V <= 512) {
+    if (!(feat & DD_FEAT_EXACT)) {
+        h->lu_bytes = 0;
+        h->d_lu = nullptr;
+    } else if (V <= 512) {
         h->lu_bytes = (size_t)(12 * V) * (12 * V) * 16 * 3 + (size_t)(12 * V) * 64;
         h->d_lu = c.take<double>(h->lu_bytes / 8);
     } else if (nb <= 16 && h->g.nblocks <= 1024) {
@@ -713,6 +730,8 @@ int apply_eo_ops(dd_handle* h, int op, SS in_e, SS in_o, SS out_e, SS out_o, LK 
 static int apply_common(dd_handle* h, void* out, const void* in, const void* U, int op, int prec, int nrhs,
                         int colour_mask, int mask_mode) {
     int rc = dd_require_ws(h);
+    if (rc) return rc;
+    rc = dd_require_feature(h, h->feat_solve, "dd_apply_D");
     if (rc) return rc;
     if (!out || !in || !U || nrhs < 1 || nrhs > h->prm.max_rhs) return dd_fail(h, DD_ERR_INVALID_ARG, "apply: bad arguments");
     if (op < DD_OP_D || op > DD_OP_INTER) return dd_fail(h, DD_ERR_INVALID_ARG, "apply: unknown operator");

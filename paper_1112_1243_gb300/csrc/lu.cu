@@ -367,6 +367,8 @@ int block_filter_exact(dd_handle* h, const double* U_old, const double* U_new, i
 extern "C" int dd_logdet_exact(dd_t h, const void* U, int which, double* out) {
     int rc = dd_require_ws(h);
     if (rc) return rc;
+    rc = dd_require_feature(h, h->feat_exact, "dd_logdet_exact");
+    if (rc) return rc;
     if (!U || !out) return dd_fail(h, DD_ERR_INVALID_ARG, "dd_logdet_exact: bad arguments");
     if (which == 0) return logdet_full(h, (const double*)U, out);
     if (which == 1) return logdet_blocks(h, (const double*)U, out);

@@ -519,6 +519,8 @@ extern "C" int dd_solve(dd_t h, void* x, const void* b, const void* U, int nrhs,
                         double* relres) {
     int rc = dd_require_ws(h);
     if (rc) return rc;
+    rc = dd_require_feature(h, h->feat_solve, "dd_solve");
+    if (rc) return rc;
     if (!x || !b || !U || nrhs < 1 || nrhs > h->prm.max_rhs) return dd_fail(h, DD_ERR_INVALID_ARG, "dd_solve: bad arguments");
     if (prec < DD_PREC_F64 || prec > DD_PREC_F16) return dd_fail(h, DD_ERR_INVALID_ARG, "dd_solve: unknown precision");
     const long long V = h->g.V;

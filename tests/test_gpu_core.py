@@ -186,6 +186,25 @@ def test_interpolation_far_apart(api):
     assert np.max(np.abs(np.linalg.det(a) - 1)) < 1e-12
 
 
+def test_lean_workspace_features(api):
+    """A handle planned for solves only has a smaller workspace, solves, and
+    refuses the estimator with DD_ERR_UNSUPPORTED (no out-of-plan access)."""
+    dims, block, kappa = (8, 8, 8, 8), (4, 4, 4, 4), 0.13
+    full = api.dd_init(dims, block, kappa, max_rhs=2)
+    lean = api.dd_init(dims, block, kappa, max_rhs=2, features=api.DD_FEAT_SOLVE)
+    assert lean.workspace.numel() < full.workspace.numel() / 2
+    lat = geometry.Lattice(dims, block)
+    U = synthetic.random_gauge(dims, 0.3, 2)
+    b = synthetic.random_spinor(dims, 11)
+    x = dev(np.zeros_like(b))
+    api.dd_solve(lean, x, dev(b), dev(U), 1, api.DD_PREC_F16)
+    true = np.linalg.norm(b - dirac.apply_D(U, host(x), lat, kappa)) / np.linalg.norm(b)
+    assert true <= 1.01e-10
+    with pytest.raises(api.DDError) as e:
+        api.dd_det_ratio_estimate(lean, dev(U), dev(U), 1, 1, 1)
+    assert e.value.code == api.DD_ERR_UNSUPPORTED
+
+
 def test_plaquette(api):
     dims = (6, 4, 4, 10)
     h = api.dd_init(dims, (3, 2, 2, 5), 0.12)
