@@ -69,6 +69,44 @@ DD_DEV void dirichlet_hop(const BlockCtx& c, int j, const SIn& in, const LK& lk,
     }
 }
 
+// acc = (H_b[lk1] - H_b[lk2]) in at local site j: only hops whose two links
+// differ contribute (the proposal changes the active links only)
+template <class SIn, class LK>
+DD_DEV void dirichlet_hop_diff(const BlockCtx& c, int j, const SIn& in, const LK& lk1, const LK& lk2,
+                               Spinor<double>& acc) {
+    int l[4];
+    local_coords(c, j, l);
+    zero(acc);
+    for (int a = 0; a < 4; ++a) {
+        for (int dir = +1; dir >= -1; dir -= 2) {
+            if (dir > 0 ? (l[a] >= c.bd[a] - 1) : (l[a] <= 0)) continue;
+            const int jn = j + dir * c.st[a];
+            const int jl = dir > 0 ? j : jn;  // the link sits at the lower end
+            Link<double> u1, u2;
+            lk1.load(jl, a, u1);
+            lk2.load(jl, a, u2);
+            bool same = true;
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int s = 0; s < 3; ++s) {
+                    u1.m[r][s] = u1.m[r][s] - u2.m[r][s];
+                    same = same && u1.m[r][s].x == 0.0 && u1.m[r][s].y == 0.0;
+                }
+            if (same) continue;
+            Spinor<double> sp;
+            in.load(jn, sp);
+            Half<double> hf, uh;
+            project<double>(a, dir, sp, hf);
+            if (dir > 0)
+                mul_link(u1, hf, uh);
+            else
+                mul_link_dag(u1, hf, uh);
+            accumulate<double>(a, dir, uh, 1.0, acc);
+        }
+    }
+}
+
 // out = D_b in (dag: gamma5 D_b gamma5); returns this thread's |out|^2 (block-reduce it)
 template <class R, class SIn, class SOut, class LK>
 DD_DEV double dirichlet_apply(const BlockCtx& c, const SIn& in, const SOut& out, const LK& lk, int dag) {
@@ -231,7 +269,7 @@ DD_DEV SpinorF64 scratch_spinor<SpinorF64>(char* base, int index, long long nb) 
 }
 
 template <class RI, class SI, class LKI>
-__global__ void __launch_bounds__(256) block_solve_kernel(BlockArgs A) {
+__global__ void __launch_bounds__(256, 2) block_solve_kernel(BlockArgs A) {
     __shared__ double sh[34];
     __shared__ int s_item;
     const BlockCtx& c = A.c;
@@ -274,11 +312,10 @@ __global__ void __launch_bounds__(256) block_solve_kernel(BlockArgs A) {
             __syncthreads();
             // b = (D_b[src] - D_b[sol]) eta = -kappa (H[src] - H[sol]) eta
             for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
-                Spinor<double> h1, h2;
-                dirichlet_hop<double>(c, j, eta, lsrc, 0, h1);
-                dirichlet_hop<double>(c, j, eta, lsol, 0, h2);
+                Spinor<double> h1;
+                dirichlet_hop_diff(c, j, eta, lsrc, lsol, h1);
 #pragma unroll
-                for (int k = 0; k < 12; ++k) h1.c[k] = (-c.kappa) * (h1.c[k] - h2.c[k]);
+                for (int k = 0; k < 12; ++k) h1.c[k] = (-c.kappa) * h1.c[k];
                 bv.store(j, h1);
             }
         } else {

@@ -254,7 +254,7 @@ static int prepare_fields(dd_handle* h, const double* U_old, const double* U_new
         int den = factors ? n : 1;
         int rc = launch_interpolate(h, U_old, U_new, (double*)f.canon, num, den);
         if (rc) return rc;
-        bool need_eo = eo && (k > 0);
+        bool need_eo = eo;  // old and new fields both enter even-odd solves
         rc = format_field(h, (const double*)f.canon, f, need_eo, need_eo && ip == DD_PREC_F32,
                           need_eo && ip == DD_PREC_F16, true, true);
         if (rc) return rc;
@@ -301,6 +301,50 @@ static int launch_blocks(dd_handle* h, int mode, const std::vector<BlockItem>& i
     else
         DD_KLAUNCH(h, block_solve_kernel<float, SpinorF32, LinkF32><<<grid, 256, 0, h->stream>>>(A));
     DD_LAUNCH_CHECK(h, "block_solve_kernel");
+    return DD_OK;
+}
+
+__global__ void set_status_kernel(int* status, int code) { raise_status(status, code); }
+static void raise_status_host(dd_handle* h, int code) {
+    DD_KLAUNCH(h, set_status_kernel<<<1, 1, 0, h->stream>>>(h->d_status, code));
+}
+
+// eo FP64 chunks of the global solver -> block order (FP64)
+__global__ void eo_to_dd_kernel(Geo g, BlockCtx c, const double2* xe, const double2* xo, double2* bank,
+                                long long vs) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y;
+    if (s >= g.V) return;
+    int x[4];
+    canon_coords(g, s, x);
+    long long q = dd_position(g, x);
+    const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+    SpinorF64 src{(double2*)(par ? xo : xe) + (long long)i * 12 * g.Vh, g.Vh};
+    Spinor<double> v;
+    src.load(s >> 1, v);
+    SpinorF64 dst{bank + (long long)i * vs + (q / c.nb) * 12 * c.nb, c.nb};
+    dst.store(q % c.nb, v);
+}
+
+// out_bank[i] = (D_bb + D_ww)^{-1} in_bank[i] for i < n, with the gauge field
+// of slot field0 + i * step: every Dirichlet block solve of every factor in
+// one batched even-odd CG (inner precision of the handle, FP64 defect
+// correction to tol_block relative to the whole right-hand side).
+static int dirichlet_solve_bank(dd_handle* h, const double2* in_bank, double2* out_bank, int n, int field0,
+                                int step) {
+    const Geo& g = h->g;
+    const BlockCtx c = block_ctx(h);
+    const long long vs = 12LL * g.V;
+    SolverVecs& v = h->vecs[0];
+    dim3 gv(grid_for(g.V, 128), n);
+    DD_KLAUNCH(h, dd_to_eo_kernel<<<gv, 128, 0, h->stream>>>(g, c, in_bank, vs, v.be, v.bo));
+    DD_LAUNCH_CHECK(h, "dd_to_eo_kernel");
+    int it = 0;
+    int rc = solve_packed(h, n, field0, step, h->prm.inner_prec, h->prm.tol_block, h->prm.maxit, &it, nullptr, 1);
+    if (rc && rc != DD_ERR_NOT_CONVERGED) return dd_fail(h, rc, "Dirichlet block solves failed");
+    if (rc == DD_ERR_NOT_CONVERGED) raise_status_host(h, DD_ERR_NOT_CONVERGED);
+    DD_KLAUNCH(h, eo_to_dd_kernel<<<gv, 128, 0, h->stream>>>(g, c, v.xe, v.xo, out_bank, vs));
+    DD_LAUNCH_CHECK(h, "eo_to_dd_kernel");
     return DD_OK;
 }
 
@@ -394,25 +438,18 @@ extern "C" int dd_det_ratio_estimate(dd_t h, const void* U_old, const void* U_ne
     DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], bank[1], vs, (const double*)h->fields[0].canon, canon_fs, d_fold, 1));
     DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], bank[2], vs, (const double*)h->fields[0].canon, canon_fs, d_fnew, 1));
     DD_LAUNCH_CHECK(h, "schur stage 1-2");
-    // 3. z = E^{-1} w, z' = E'^{-1} w'  (banks 1,2 are contiguous, so are 3,4)
-    const int half = g.nblocks / 2;
-    std::vector<BlockItem> items;
-    for (int i = 0; i < n; ++i)
-        for (int pos = half; pos < g.nblocks; ++pos) {
-            items.push_back(BlockItem{pos, 0, f_old[i], i});
-            items.push_back(BlockItem{pos, 0, f_new[i], R + i});
-        }
-    rc = launch_blocks(h, BLOCK_SOLVE, items, bank[1], bank[3], seed, ctr);
+    // 3. z = E^{-1} w, z' = E'^{-1} w': all white-block solves of all factors
+    //    as one batched even-odd CG on the Dirichlet operator
+    rc = dirichlet_solve_bank(h, bank[1], bank[3], n, 0, factors ? 1 : 0);
+    if (rc) return rc;
+    rc = dirichlet_solve_bank(h, bank[2], bank[4], n, 1, factors ? 1 : 0);
     if (rc) return rc;
     // 4. v = B z, v' = B' z' (onto black sites)
     DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[3], bank[1], vs, (const double*)h->fields[0].canon, canon_fs, d_fold, 0));
     DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[4], bank[2], vs, (const double*)h->fields[0].canon, canon_fs, d_fnew, 0));
     DD_LAUNCH_CHECK(h, "schur stage 4");
-    // 5. a = A^{-1} v
-    items.clear();
-    for (int i = 0; i < n; ++i)
-        for (int pos = 0; pos < half; ++pos) items.push_back(BlockItem{pos, 0, f_old[i], i});
-    rc = launch_blocks(h, BLOCK_SOLVE, items, bank[1], bank[5], seed, ctr);
+    // 5. a = A^{-1} v (black-block solves)
+    rc = dirichlet_solve_bank(h, bank[1], bank[5], n, 0, factors ? 1 : 0);
     if (rc) return rc;
     // 6. s = v' - A' a  -> bank 3
     DD_KLAUNCH(h, schur_source_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[2], bank[5], bank[3], vs, h->fields[0].dd64, dd64_fs, d_fnew));

@@ -45,6 +45,13 @@ __global__ void interpolate_kernel(long long nlinks, const double* __restrict__ 
         for (int k = 0; k < 18; ++k) o[k] = b[k];
         return;
     }
+    // an unchanged link (e.g. in a rejected block) stays on the path: W = 1, W^t = 1
+    bool same = true;
+    for (int k = 0; k < 18; ++k) same = same && (a[k] == b[k]);
+    if (same) {
+        for (int k = 0; k < 18; ++k) o[k] = a[k];
+        return;
+    }
     M3 u = load_m3(a), up = load_m3(b);
     M3 w = mul_dag_left(u, up);  // U^dag U'
     M3 wt = su3_power(w, (double)num / (double)den);

@@ -212,7 +212,7 @@ __global__ void zero64_kernel(long long n, SpinorF64 v) {
 }
 
 // ------------------------------------------------------------ CGNR runner
-template <class R, class SM, class SH, class LK>
+template <class R, class SM, class SH, class LK, int MASK = 0>
 struct NormalCG {
     dd_handle* h;
     int nrhs;
@@ -258,14 +258,14 @@ struct NormalCG {
     // z = Dtilde^dag r  (two hops), |z|^2 -> op
     void apply_dag_r(int op) {
         const double k2 = h->prm.kappa * h->prm.kappa;
-        launch_hop<R, SH, SM, SH, LK, 0>(args(1, rh, r, th, 0.0, 1.0, 0, 1, 0, FIN_NONE), nrhs, h);
-        launch_hop<R, SH, SM, SM, LK, 0>(args(0, th, r, z, 1.0, -k2, 1, 0, 1, op), nrhs, h);
+        launch_hop<R, SH, SM, SH, LK, MASK>(args(1, rh, r, th, 0.0, 1.0, 0, 1, 0, FIN_NONE), nrhs, h);
+        launch_hop<R, SH, SM, SM, LK, MASK>(args(0, th, r, z, 1.0, -k2, 1, 0, 1, op), nrhs, h);
     }
     // q = Dtilde p, |q|^2 -> alpha
     void apply_p() {
         const double k2 = h->prm.kappa * h->prm.kappa;
-        launch_hop<R, SH, SM, SH, LK, 0>(args(1, ph, p, th, 0.0, 1.0, 0, 0, 0, FIN_NONE), nrhs, h);
-        launch_hop<R, SH, SM, SM, LK, 0>(args(0, th, p, q, 1.0, -k2, 1, 0, 0, FIN_ALPHA), nrhs, h);
+        launch_hop<R, SH, SM, SH, LK, MASK>(args(1, ph, p, th, 0.0, 1.0, 0, 0, 0, FIN_NONE), nrhs, h);
+        launch_hop<R, SH, SM, SM, LK, MASK>(args(0, th, p, q, 1.0, -k2, 1, 0, 0, FIN_ALPHA), nrhs, h);
     }
     // solve Dtilde x = r (r holds the right-hand side; x starts at 0)
     int run(const double* rr0, double tol, double abs_fac, int maxit, int chunk, int* iters_out) {
@@ -339,6 +339,7 @@ Reduce store_reduce(dd_handle* h, double* out) {
 }
 
 // FP64 hop helper on eo FP64 vectors
+template <int MASK>
 void hop64(dd_handle* h, int nrhs, int par, SpinorF64 in, SpinorF64 xin, SpinorF64 out, double a, double b,
            int hasx, LinkF64 lk, long long lk_rs, const CGState* st, Reduce red) {
     HopArgs<SpinorF64, SpinorF64, SpinorF64, LinkF64> A;
@@ -357,7 +358,7 @@ void hop64(dd_handle* h, int nrhs, int par, SpinorF64 in, SpinorF64 xin, SpinorF
     A.colour_mask = 3;
     A.st = st;
     A.red = red;
-    launch_hop<double, SpinorF64, SpinorF64, SpinorF64, LinkF64, 0>(A, nrhs, h);
+    launch_hop<double, SpinorF64, SpinorF64, SpinorF64, LinkF64, MASK>(A, nrhs, h);
 }
 
 __global__ void add_scalars_kernel(int n, double* a, const double* b) {
@@ -368,8 +369,8 @@ __global__ void add_scalars_kernel(int n, double* a, const double* b) {
 // One defect-correction solve.  Inner vectors: x (correction), r (inner
 // residual, starts as the FP64 outer residual), p, q, z (storage SM) and the
 // hop copies ph, rh, th (storage SH; th lives on odd sites).
-template <class R, class SM, class SH, class LK>
-int defect_correction(dd_handle* h, int nrhs, int field0, int step, NormalCG<R, SM, SH, LK>& cg, bool fp64_inner,
+template <class R, class SM, class SH, class LK, int MASK>
+int defect_correction(dd_handle* h, int nrhs, int field0, int step, NormalCG<R, SM, SH, LK, MASK>& cg, bool fp64_inner,
                       double tol, int maxit, int* iters, double* relres) {
     SolverVecs& v = h->vecs[0];
     const long long Vh = h->g.Vh;
@@ -390,7 +391,7 @@ int defect_correction(dd_handle* h, int nrhs, int field0, int step, NormalCG<R, 
     DD_KLAUNCH(h, norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(Vh, be, store_reduce(h, bb)));
     DD_KLAUNCH(h, norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(Vh, bo, store_reduce(h, tmp)));
     DD_KLAUNCH(h, add_scalars_kernel<<<1, 64, 0, h->stream>>>(nrhs, bb, tmp));
-    hop64(h, nrhs, 0, bo, be, be, 1.0, kappa, 1, lk64, rs64, nullptr, none);
+    hop64<MASK>(h, nrhs, 0, bo, be, be, 1.0, kappa, 1, lk64, rs64, nullptr, none);
     DD_KLAUNCH(h, outer_arm_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, bb, tol));
     DD_KLAUNCH(h, zero64_kernel<<<grid, 128, 0, h->stream>>>(Vh, xe));
     DD_KLAUNCH(h, copy_kernel<SpinorF64, SpinorF64><<<grid, 128, 0, h->stream>>>(Vh, be, re, nullptr));
@@ -416,8 +417,8 @@ int defect_correction(dd_handle* h, int nrhs, int field0, int step, NormalCG<R, 
         DD_KLAUNCH(h, add_correction_kernel<SM><<<grid, 128, 0, h->stream>>>(Vh, xe, cg.x, fp64_inner ? nullptr : rr,
                                                                           outer));
         // true residual r = b~ - Dtilde x (FP64)
-        hop64(h, nrhs, 1, xe, xe, t64, 0.0, 1.0, 0, lk64, rs64, outer, none);
-        hop64(h, nrhs, 0, t64, xe, t64b, 1.0, -kappa * kappa, 1, lk64, rs64, outer, none);
+        hop64<MASK>(h, nrhs, 1, xe, xe, t64, 0.0, 1.0, 0, lk64, rs64, outer, none);
+        hop64<MASK>(h, nrhs, 0, t64, xe, t64b, 1.0, -kappa * kappa, 1, lk64, rs64, outer, none);
         DD_KLAUNCH(h, residual_kernel<<<grid, 128, 0, h->stream>>>(Vh, be, t64b, re, outer, store_reduce(h, rr)));
         DD_KLAUNCH(h, outer_update_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, rr));
         if (cudaGetLastError() != cudaSuccess) return DD_ERR_CUDA;
@@ -430,7 +431,7 @@ int defect_correction(dd_handle* h, int nrhs, int field0, int step, NormalCG<R, 
         if (!any || total >= maxit) break;
     }
     // x_o = b_o + kappa H_oe x_e
-    hop64(h, nrhs, 1, xe, bo, xo, 1.0, kappa, 1, lk64, rs64, nullptr, none);
+    hop64<MASK>(h, nrhs, 1, xe, bo, xo, 1.0, kappa, 1, lk64, rs64, nullptr, none);
     if (cudaGetLastError() != cudaSuccess) return DD_ERR_CUDA;
     std::vector<double> hb(nrhs);
     if (cudaMemcpyAsync(hb.data(), bb, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
@@ -450,17 +451,19 @@ int defect_correction(dd_handle* h, int nrhs, int field0, int step, NormalCG<R, 
 
 }  // namespace
 
-int solve_packed(dd_handle* h, int nrhs, int field0, int step, int prec, double tol, int maxit, int* iters,
-                 double* relres) {
+template <int MASK>
+static int solve_packed_mask(dd_handle* h, int nrhs, int field0, int step, int prec, double tol, int maxit,
+                             int* iters, double* relres) {
     SolverVecs& v = h->vecs[0];
     const long long Vh = h->g.Vh;
     CGState* inner = h->d_cg;
     CGState* outer = h->d_cg + h->prm.max_rhs;
     if (prec == DD_PREC_F64) {
-        NormalCG<double, SpinorF64, SpinorF64, LinkF64> cg;
+        NormalCG<double, SpinorF64, SpinorF64, LinkF64, MASK> cg;
         cg.h = h;
         cg.nrhs = nrhs;
-        cg.x = SpinorF64{v.t64b, Vh};
+        // the inner x must not alias the residual temporaries: x64
+        cg.x = SpinorF64{v.x64, Vh};
         cg.r = SpinorF64{v.re, Vh};
         cg.p = SpinorF64{v.p64, Vh};
         cg.q = SpinorF64{v.q64, Vh};
@@ -473,11 +476,9 @@ int solve_packed(dd_handle* h, int nrhs, int field0, int step, int prec, double 
         cg.lk_rs = field_stride<LinkF64>(h, step);
         cg.st = inner;
         cg.outer = outer;
-        // the inner x must not alias the residual temporaries: use x64
-        cg.x = SpinorF64{v.x64, Vh};
         return defect_correction(h, nrhs, field0, step, cg, true, tol, maxit, iters, relres);
     } else if (prec == DD_PREC_F32) {
-        NormalCG<float, SpinorF32, SpinorF32, LinkF32> cg;
+        NormalCG<float, SpinorF32, SpinorF32, LinkF32, MASK> cg;
         cg.h = h;
         cg.nrhs = nrhs;
         cg.x = SpinorF32{v.x32, Vh};
@@ -495,7 +496,7 @@ int solve_packed(dd_handle* h, int nrhs, int field0, int step, int prec, double 
         cg.outer = outer;
         return defect_correction(h, nrhs, field0, step, cg, false, tol, maxit, iters, relres);
     } else {
-        NormalCG<float, SpinorF32, SpinorF16, LinkF16> cg;
+        NormalCG<float, SpinorF32, SpinorF16, LinkF16, MASK> cg;
         cg.h = h;
         cg.nrhs = nrhs;
         cg.x = SpinorF32{v.x32, Vh};
@@ -513,6 +514,12 @@ int solve_packed(dd_handle* h, int nrhs, int field0, int step, int prec, double 
         cg.outer = outer;
         return defect_correction(h, nrhs, field0, step, cg, false, tol, maxit, iters, relres);
     }
+}
+
+int solve_packed(dd_handle* h, int nrhs, int field0, int step, int prec, double tol, int maxit, int* iters,
+                 double* relres, int mask) {
+    if (mask == 1) return solve_packed_mask<1>(h, nrhs, field0, step, prec, tol, maxit, iters, relres);
+    return solve_packed_mask<0>(h, nrhs, field0, step, prec, tol, maxit, iters, relres);
 }
 
 extern "C" int dd_solve(dd_t h, void* x, const void* b, const void* U, int nrhs, int prec, int* iters,

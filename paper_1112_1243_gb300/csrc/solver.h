@@ -14,5 +14,9 @@
 // be null) the total inner iterations.  prec: DD_PREC_F64 (plain FP64 CG) or
 // DD_PREC_F32 / DD_PREC_F16 (inner solver in that precision, FP64 defect
 // correction).  Returns DD_ERR_NOT_CONVERGED if maxit was reached.
+// mask = 0: the whole operator D; mask = 1: the Dirichlet block operators
+// D_bb + D_ww (every hop that leaves a block dropped), i.e. all block solves
+// of the right-hand side's blocks at once, even-odd preconditioned (hops
+// inside a block still connect opposite site parities).
 int solve_packed(dd_handle* h, int nrhs, int field0, int field_step, int prec, double tol, int maxit, int* iters,
-                 double* relres);
+                 double* relres, int mask = 0);
