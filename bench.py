@@ -59,6 +59,12 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--fp64-steps", type=int, default=0,
                    help="also time this many steps with the plain FP64 solver (same workload)")
+    p.add_argument("--no-batched-filter", action="store_true",
+                   help="skip the uneven-block batched filter measurement")
+    p.add_argument("--compare-config", default="c3",
+                   help="workload of the mixed-versus-FP64 comparison ('' to skip)")
+    p.add_argument("--krylov", default="bicgstab", choices=["cgnr", "bicgstab"],
+                   help="inner Krylov method of the mixed-precision solves")
     p.add_argument("--mode", default="step", choices=["step", "solve"],
                    help="step: the hierarchical step (the benchmark); solve: one-rhs global solves on a lean "
                         "handle (kernel captures and Dslash GB/s)")
@@ -208,9 +214,10 @@ def run_gpu(args, cfg):
     Vh = V // 2
     nmax = max(cfg["n_global"], cfg["n_block"])
     stream = torch.cuda.current_stream(dev)
+    krylov = {"cgnr": api.DD_KRYLOV_CGNR, "bicgstab": api.DD_KRYLOV_BICGSTAB}[args.krylov]
     h = api.dd_init(cfg["dims"], cfg["block"], cfg["kappa"], max_rhs=nmax, inner_prec=prec,
                     block_prec=api.DD_PREC_F32, tol_global=1e-10, tol_block=1e-12, tol_inner=1e-3,
-                    maxit=40000, stream=stream, device=dev)
+                    maxit=40000, stream=stream, device=dev, krylov=krylov)
     U_np = synthetic.random_gauge(cfg["dims"], cfg["eps"], cfg["seed"] + 1000 * rank)
     U = torch.from_numpy(U_np).to(dev)
     chain = HierarchicalStep(h, BETA, n_inner=1, n_block=cfg["n_block"], n_global=cfg["n_global"],
@@ -272,6 +279,7 @@ def run_gpu(args, cfg):
                                f"{'x'.join(map(str, cfg['block']))} blocks (6^4 active sub-blocks), eps {cfg['eps']}, "
                                f"kappa {cfg['kappa']}, beta {BETA}, {cfg['n_global']} global + {cfg['n_block']} block "
                                f"factors, residual 1e-10",
+                   "krylov": args.krylov,
                    "l2": "inputs larger than L2 (gauge field alone 1.2 GB)", "chains": world},
         "roofline": {"bound": "hbm", "kernel": f"hop_eo_kernel kind {kind}",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -324,6 +332,15 @@ def run_gpu(args, cfg):
         barrier()
         line["fp64_value"] = cfg["n_global"] * args.fp64_steps / (g0.elapsed_time(g1) / 1e3)
         del h64
+    del chain
+    del h
+    torch.cuda.empty_cache()
+    if args.compare_config:
+        # mixed versus plain FP64 on a smaller workload (the FP64 path at the
+        # full volume would hold the GPU for minutes per step)
+        line["mixed_vs_fp64"] = compare_precisions(args, CONFIGS[args.compare_config], dev, stream, rank)
+    if not args.no_batched_filter:
+        line["batched_filter"] = measure_batched_filter(dev, stream)
     if rank == 0 and not args.no_cpu_baseline:
         per_app, n, t = oracle_sample(cfg, seconds=15.0)
         line["cpu_baseline"] = {
@@ -339,6 +356,84 @@ def run_gpu(args, cfg):
     return 0
 
 
+def compare_precisions(args, cfg, dev, stream, rank):
+    """Estimates/s of the same hierarchical step with the mixed FP16/FP32 inner
+    solvers and with the plain FP64 solver (CGNR), 3 warm-up + 2 timed steps each."""
+    import torch
+    from paper_1112_1243_gb300 import api, synthetic
+    from paper_1112_1243_gb300.chain import HierarchicalStep
+    out = {"workload": f"{'x'.join(map(str, cfg['dims']))} lattice, {'x'.join(map(str, cfg['block']))} blocks, "
+                       f"kappa {cfg['kappa']}, eps {cfg['eps']}, {cfg['n_global']} global factors"}
+    U_np = synthetic.random_gauge(cfg["dims"], cfg["eps"], cfg["seed"] + 1000 * rank)
+    nmax = max(cfg["n_global"], cfg["n_block"])
+    for name, prec, kry in (("mixed", api.DD_PREC_F16, api.DD_KRYLOV_BICGSTAB if args.krylov == "bicgstab"
+                              else api.DD_KRYLOV_CGNR), ("fp64", api.DD_PREC_F64, api.DD_KRYLOV_CGNR)):
+        h = api.dd_init(cfg["dims"], cfg["block"], cfg["kappa"], max_rhs=nmax, inner_prec=prec,
+                        block_prec=api.DD_PREC_F32 if prec != api.DD_PREC_F64 else api.DD_PREC_F64,
+                        tol_global=1e-10, tol_block=1e-12, maxit=40000, stream=stream, device=dev, krylov=kry)
+        st = HierarchicalStep(h, BETA, n_inner=1, n_block=cfg["n_block"], n_global=cfg["n_global"],
+                              seed=cfg["seed"] * 7919 + rank)
+        U = torch.from_numpy(U_np).to(dev)
+        for k in range(3):
+            st.step(U, k)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(2):
+            st.step(U, 3 + k)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        out[name] = cfg["n_global"] * 2 / (e0.elapsed_time(e1) / 1e3)
+        del st
+        del h
+        torch.cuda.empty_cache()
+    out["speedup"] = out["mixed"] / out["fp64"]
+    return out
+
+
+C4_LATTICES = [((16, 16, 16, 16), (4, 4, 4, 4)), ((12, 12, 12, 12), (6, 6, 6, 6)), ((16, 16, 16, 16), (8, 8, 8, 8))]
+
+
+def measure_batched_filter(dev, stream, reps=3):
+    """Block filters of three lattices with uneven blocks (256 x 4^4, 16 x 6^4,
+    16 x 8^4; kappa 0.13, eps 0.3, 4 noise vectors per block) in one persistent
+    launch per call: (block, factor) estimates per second."""
+    import torch
+    from paper_1112_1243_gb300 import api, synthetic
+    n = 4
+    hs, Us, Ups = [], [], []
+    for k, (dims, block) in enumerate(C4_LATTICES):
+        h = api.dd_init(dims, block, 0.13, max_rhs=n, stream=stream, device=dev)
+        U = torch.from_numpy(synthetic.random_gauge(dims, 0.3, 4 + 10 * k)).to(dev)
+        Up = U.clone()
+        api.dd_gauge_update(h, Up, 3, BETA, 1, 0, 4, 1)
+        hs.append(h)
+        Us.append(U)
+        Ups.append(Up)
+    items = sum(h.nblocks for h in hs) * n
+    work = [u.clone() for u in Ups]
+    for _ in range(2):
+        for w, u in zip(work, Ups):
+            w.copy_(u)
+        api.dd_block_filter_batch(hs, Us, work, 3, n, 4, 2)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for r in range(reps):
+        for w, u in zip(work, Ups):
+            w.copy_(u)
+        api.dd_block_filter_batch(hs, Us, work, 3, n, 4, 3 + r)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    out = {"workload": "256 x 4^4 (16^4), 16 x 6^4 (12^4), 16 x 8^4 (16^4) blocks, 4 noise vectors each, "
+                       "one persistent launch", "items_per_launch": items, "seconds_per_call": t,
+           "block_estimates_per_s": items / t}
+    for h in hs:
+        del h
+    return out
+
+
 def run_solve(args, cfg):
     """Global solves D x = b (one right-hand side) on a handle planned for
     solves only: the hop kernels of the hot path at a few GB of device memory."""
@@ -347,8 +442,9 @@ def run_solve(args, cfg):
     build.build()
     dev = torch.device("cuda", 0)
     prec = {"f16": api.DD_PREC_F16, "f32": api.DD_PREC_F32, "f64": api.DD_PREC_F64}[args.prec]
+    krylov = {"cgnr": api.DD_KRYLOV_CGNR, "bicgstab": api.DD_KRYLOV_BICGSTAB}[args.krylov]
     h = api.dd_init(cfg["dims"], cfg["block"], cfg["kappa"], max_rhs=1, inner_prec=prec, tol_global=1e-10,
-                    maxit=40000, features=api.DD_FEAT_SOLVE, device=dev)
+                    maxit=40000, features=api.DD_FEAT_SOLVE, device=dev, krylov=krylov)
     U = torch.from_numpy(synthetic.random_gauge(cfg["dims"], cfg["eps"], cfg["seed"])).to(dev)
     b = torch.from_numpy(synthetic.random_spinor(cfg["dims"], 1)).to(dev)
     x = torch.zeros_like(b)

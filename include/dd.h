@@ -108,7 +108,12 @@ typedef struct {
     double tol_inner;  /* residual reduction asked of one inner solve (defect correction) */
     int maxit;         /* iteration cap of any single Krylov solve */
     int features;      /* workspace parts to plan: DD_FEAT_* bits, 0 = all */
+    int krylov;        /* inner Krylov method of mixed-precision solves: DD_KRYLOV_* */
 } dd_params;
+
+/* inner Krylov method of the FP32/FP16 solves (the FP64 solver is always CGNR) */
+#define DD_KRYLOV_CGNR 0     /* CG on the even-odd normal equations Dtilde^dag Dtilde */
+#define DD_KRYLOV_BICGSTAB 1 /* BiCGStab on Dtilde (van der Vorst), restarted by the FP64 loop */
 
 /* workspace features (dd_params.features); entry points that need a part the
  * workspace was not planned with fail with DD_ERR_UNSUPPORTED */
@@ -207,6 +212,22 @@ int dd_det_ratio_estimate(dd_t h, const void* U_old, const void* U_new, int n, u
  * All (block, factor) solves run in one persistent launch. */
 int dd_block_filter(dd_t h, const void* U_old, void* U_new, int colour_mask, int mode, int n, uint64_t seed,
                     uint64_t ctr, double* ln_b, uint8_t* accept);
+
+/* The block filter of several lattices at once (Eq. 4step step 1): every
+ * (block, factor) solve of all nh handles runs in ONE persistent launch, the
+ * items of the largest blocks first; blocks may differ in shape between the
+ * lattices (e.g. 4^4, 6^4 and 8^4).  Per handle k the results are those of
+ * dd_block_filter(hs[k], U_old[k], U_new[k], colour_mask, DD_FILTER_STOCHASTIC,
+ * n, seed, ctr, ln_b[k], accept[k]) (same random streams, same arithmetic).
+ * All handles must share one stream and block precision; hs, U_old, U_new,
+ * ln_b and accept are host arrays of nh pointers (the pointers themselves
+ * device memory).  ws: device memory of at least
+ * dd_block_filter_batch_workspace(nh, hs, n) bytes, 256-byte aligned, owned
+ * by the caller (holds the item queue and the thread-block scratch slots). */
+int dd_block_filter_batch_workspace(int nh, const dd_t* hs, int n, size_t* bytes);
+int dd_block_filter_batch(int nh, const dd_t* hs, const void* const* U_old, void* const* U_new, int colour_mask,
+                          int n, uint64_t seed, uint64_t ctr, double* const* ln_b, uint8_t* const* accept, void* ws,
+                          size_t ws_bytes);
 
 /* Proposal (Eq. 4step step 0): n_hb Cabibbo-Marinari heat-bath sweeps of the
  * Wilson plaquette action at beta, each followed by n_or over-relaxation

@@ -57,10 +57,12 @@ class dd_params(ctypes.Structure):
         ("tol_inner", ctypes.c_double),
         ("maxit", ctypes.c_int),
         ("features", ctypes.c_int),
+        ("krylov", ctypes.c_int),
     ]
 
 
 DD_FEAT_SOLVE, DD_FEAT_ESTIMATE, DD_FEAT_EXACT = 1, 2, 4
+DD_KRYLOV_CGNR, DD_KRYLOV_BICGSTAB = 0, 1
 
 
 _P = ctypes.c_void_p
@@ -82,6 +84,8 @@ SIGNATURES = {
     "dd_interpolate": [_P, _P, _P, _P, _I, _I],
     "dd_det_ratio_estimate": [_P, _P, _P, _I, _U64, _U64, _I, _P],
     "dd_block_filter": [_P, _P, _P, _I, _I, _I, _U64, _U64, _P, _P],
+    "dd_block_filter_batch_workspace": [_I, _P, _I, ctypes.POINTER(ctypes.c_size_t)],
+    "dd_block_filter_batch": [_I, _P, _P, _P, _I, _I, _U64, _U64, _P, _P, _P, ctypes.c_size_t],
     "dd_gauge_update": [_P, _P, _I, _D, _I, _I, _U64, _U64],
     "dd_global_accept": [_P, _P, _P, _P, _I, _U64, _U64, _P, _P],
     "dd_logdet_exact": [_P, _P, _I, _P],

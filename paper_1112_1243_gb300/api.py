@@ -70,7 +70,8 @@ def dd_default_params():
 
 def dd_init(dims, block, kappa, bc_time=-1, active_mode=_lib.DD_ACTIVE_AUTO, max_rhs=1,
             inner_prec=_lib.DD_PREC_F16, block_prec=_lib.DD_PREC_F32, tol_global=1e-10,
-            tol_block=1e-12, tol_inner=1e-3, maxit=20000, stream=None, device=None, features=0):
+            tol_block=1e-12, tol_inner=1e-3, maxit=20000, stream=None, device=None, features=0,
+            krylov=_lib.DD_KRYLOV_CGNR):
     """Create a handle and give it a torch-allocated workspace on `device`."""
     lib = _lib.load()
     p = dd_default_params()
@@ -88,6 +89,7 @@ def dd_init(dims, block, kappa, bc_time=-1, active_mode=_lib.DD_ACTIVE_AUTO, max
     p.tol_inner = float(tol_inner)
     p.maxit = int(maxit)
     p.features = int(features)
+    p.krylov = int(krylov)
     device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
     if stream is None:
         stream = torch.cuda.current_stream(device)
@@ -164,6 +166,31 @@ def dd_block_filter(h, U_old, U_new, colour_mask, mode, n, seed, ctr, ln_b=None,
     _check(h, _lib.load().dd_block_filter(h.ptr, _ptr(U_old), _ptr(U_new), int(colour_mask), int(mode), int(n),
                                           int(seed), int(ctr), _ptr(ln_b), _ptr(accept)))
     return ln_b, accept
+
+
+def dd_block_filter_batch(hs, U_olds, U_news, colour_mask, n, seed, ctr, ln_bs=None, accepts=None):
+    """Block filters of several handles (lattices, block shapes) in one persistent launch."""
+    lib = _lib.load()
+    nh = len(hs)
+    dev = hs[0].workspace.device
+    harr = (ctypes.c_void_p * nh)(*[h.ptr.value if isinstance(h.ptr, ctypes.c_void_p) else h.ptr for h in hs])
+    size = ctypes.c_size_t()
+    rc = lib.dd_block_filter_batch_workspace(nh, harr, int(n), ctypes.byref(size))
+    if rc != _lib.DD_OK:
+        raise DDError(rc, "dd_block_filter_batch_workspace failed")
+    ws = torch.empty(size.value + 256, dtype=torch.uint8, device=dev)
+    base = (ws.data_ptr() + 255) & ~255
+    if ln_bs is None:
+        ln_bs = [torch.zeros(h.nblocks, dtype=torch.float64, device=dev) for h in hs]
+    if accepts is None:
+        accepts = [torch.zeros(h.nblocks, dtype=torch.uint8, device=dev) for h in hs]
+    arr = lambda ts: (ctypes.c_void_p * nh)(*[_ptr(t) for t in ts])
+    rc = lib.dd_block_filter_batch(nh, harr, arr(U_olds), arr(U_news), int(colour_mask), int(n), int(seed), int(ctr),
+                                   arr(ln_bs), arr(accepts), ctypes.c_void_p(base), ctypes.c_size_t(size.value))
+    if rc != _lib.DD_OK:
+        raise DDError(rc, dd_last_error(hs[0]))
+    hs[0].batch_ws = ws  # keep the scratch alive until the stream has consumed it
+    return ln_bs, accepts
 
 
 def dd_gauge_update(h, U, colour_mask, beta, n_hb, n_or, seed, ctr):

@@ -197,9 +197,22 @@ struct BlockItem {
     int f_src;      // field slot of the source operator (filter) / unused
     int f_sol;      // field slot of the solve
     int vec;        // factor index (noise sub) / vector index in the banks
+    int lat;        // lattice of the item in a multi-lattice launch (0 otherwise)
+};
+
+// one lattice of a multi-lattice launch (blocks of different shapes)
+struct LatDesc {
+    Geo g;
+    BlockCtx c;
+    const double2* dd64;
+    long long dd64_fs;
+    const float4* dd32;
+    long long dd32_fs;
+    double* item_out;
 };
 
 struct BlockArgs {
+    const LatDesc* lats;  // multi-lattice launch: per-item lattice (null: the fields below)
     Geo g;
     BlockCtx c;
     int mode;
@@ -248,14 +261,14 @@ DD_DEV void block_origin(const Geo& g, int id, int o[4]) {
 }
 
 template <class LK>
-DD_DEV LK make_inner_links(const BlockArgs& A, int f, int pos);
+DD_DEV LK make_inner_links(const LatDesc& L, int f, int pos);
 template <>
-DD_DEV LinkF32 make_inner_links<LinkF32>(const BlockArgs& A, int f, int pos) {
-    return LinkF32{A.dd32 + (long long)f * A.dd32_fs + (long long)pos * 4 * 3 * A.c.nb, A.c.nb};
+DD_DEV LinkF32 make_inner_links<LinkF32>(const LatDesc& L, int f, int pos) {
+    return LinkF32{L.dd32 + (long long)f * L.dd32_fs + (long long)pos * 4 * 3 * L.c.nb, L.c.nb};
 }
 template <>
-DD_DEV LinkF64 make_inner_links<LinkF64>(const BlockArgs& A, int f, int pos) {
-    return LinkF64{A.dd64 + (long long)f * A.dd64_fs + (long long)pos * 4 * 9 * A.c.nb, A.c.nb};
+DD_DEV LinkF64 make_inner_links<LinkF64>(const LatDesc& L, int f, int pos) {
+    return LinkF64{L.dd64 + (long long)f * L.dd64_fs + (long long)pos * 4 * 9 * L.c.nb, L.c.nb};
 }
 template <class S>
 DD_DEV S scratch_spinor(char* base, int index, long long nb);
@@ -272,17 +285,8 @@ template <class RI, class SI, class LKI>
 __global__ void __launch_bounds__(256, 2) block_solve_kernel(BlockArgs A) {
     __shared__ double sh[34];
     __shared__ int s_item;
-    const BlockCtx& c = A.c;
-    const long long nb = c.nb;
     // scratch slot of this thread block: FP64 vectors eta, b, x, r; inner vectors x, r, p, q, z
     char* base = A.scratch + (long long)blockIdx.x * A.slot_bytes;
-    SpinorF64 eta{(double2*)base, nb};
-    SpinorF64 bv{(double2*)base + 12 * nb, nb};
-    SpinorF64 xv{(double2*)base + 24 * nb, nb};
-    SpinorF64 rv{(double2*)base + 36 * nb, nb};
-    char* ib = base + 48 * nb * sizeof(double2);
-    SI xi = scratch_spinor<SI>(ib, 0, nb), ri = scratch_spinor<SI>(ib, 1, nb), pi = scratch_spinor<SI>(ib, 2, nb),
-       qi = scratch_spinor<SI>(ib, 3, nb), zi = scratch_spinor<SI>(ib, 4, nb);
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(A.queue, 1);
         __syncthreads();
@@ -290,20 +294,41 @@ __global__ void __launch_bounds__(256, 2) block_solve_kernel(BlockArgs A) {
         __syncthreads();
         if (item >= A.nitems) break;
         const BlockItem it = A.items[item];
-        LinkF64 lsol{A.dd64 + (long long)it.f_sol * A.dd64_fs + (long long)it.block_pos * 4 * 9 * nb, nb};
-        LKI lsoli = make_inner_links<LKI>(A, it.f_sol, it.block_pos);
+        LatDesc L;
+        if (A.lats) {
+            L = A.lats[it.lat];
+        } else {
+            L.g = A.g;
+            L.c = A.c;
+            L.dd64 = A.dd64;
+            L.dd64_fs = A.dd64_fs;
+            L.dd32 = A.dd32;
+            L.dd32_fs = A.dd32_fs;
+            L.item_out = A.item_out;
+        }
+        const BlockCtx& c = L.c;
+        const long long nb = c.nb;
+        SpinorF64 eta{(double2*)base, nb};
+        SpinorF64 bv{(double2*)base + 12 * nb, nb};
+        SpinorF64 xv{(double2*)base + 24 * nb, nb};
+        SpinorF64 rv{(double2*)base + 36 * nb, nb};
+        char* ib = base + 48 * nb * sizeof(double2);
+        SI xi = scratch_spinor<SI>(ib, 0, nb), ri = scratch_spinor<SI>(ib, 1, nb),
+           pi = scratch_spinor<SI>(ib, 2, nb), qi = scratch_spinor<SI>(ib, 3, nb), zi = scratch_spinor<SI>(ib, 4, nb);
+        LinkF64 lsol{L.dd64 + (long long)it.f_sol * L.dd64_fs + (long long)it.block_pos * 4 * 9 * nb, nb};
+        LKI lsoli = make_inner_links<LKI>(L, it.f_sol, it.block_pos);
         int colour;
-        int id = block_id_at(A.g, it.block_pos, &colour);
+        int id = block_id_at(L.g, it.block_pos, &colour);
         int org[4];
-        block_origin(A.g, id, org);
+        block_origin(L.g, id, org);
         // ---- right-hand side
         if (A.mode == BLOCK_FILTER) {
-            LinkF64 lsrc{A.dd64 + (long long)it.f_src * A.dd64_fs + (long long)it.block_pos * 4 * 9 * nb, nb};
+            LinkF64 lsrc{L.dd64 + (long long)it.f_src * L.dd64_fs + (long long)it.block_pos * 4 * 9 * nb, nb};
             for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
                 int l[4];
                 local_coords(c, j, l);
                 int x[4] = {org[0] + l[0], org[1] + l[1], org[2] + l[2], org[3] + l[3]};
-                uint32_t s = (uint32_t)canon_index(A.g, x);
+                uint32_t s = (uint32_t)canon_index(L.g, x);
                 Spinor<double> e;
 #pragma unroll
                 for (int k = 0; k < 12; ++k) e.c[k] = gaussian(s * 12u + k, (uint32_t)A.purpose, (uint32_t)it.vec, A.seed, A.ctr);
@@ -390,7 +415,7 @@ __global__ void __launch_bounds__(256, 2) block_solve_kernel(BlockArgs A) {
                 for (int k = 0; k < 12; ++k) s += 2.0 * (e.c[k].x * d.c[k].x + e.c[k].y * d.c[k].y) + norm2(d.c[k]);
             }
             s = block_sum(s, sh);
-            if (threadIdx.x == 0) A.item_out[item] = -s;
+            if (threadIdx.x == 0) L.item_out[item] = -s;
         } else {
             SpinorF64 dst{A.out_bank + (long long)it.vec * A.bank_vs + (long long)it.block_pos * 12 * nb, nb};
             for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {

@@ -236,17 +236,52 @@ struct Geo {
     int nblocks;  // number of blocks
     int bsites;   // sites per block
     int bc;       // fermion phase on time-wrapping hops (+1 / -1)
+    int st[4];    // canonical strides 1, L0, L0 L1, L0 L1 L2
+    // multipliers for division by Lh0, L1, L2 with __umulhi (exact for n * d < 2^32; 0: use '/')
+    unsigned mLh0, mL1, mL2;
 };
+
+// derived members of a Geo whose L, b, nbk and bc are set (host side)
+inline void geo_finish(Geo& g) {
+    long long V = (long long)g.L[0] * g.L[1] * g.L[2] * g.L[3];
+    g.V = (int)V;
+    g.Vh = (int)(V / 2);
+    g.Lh0 = g.L[0] / 2;
+    g.nblocks = g.nbk[0] * g.nbk[1] * g.nbk[2] * g.nbk[3];
+    g.bsites = g.b[0] * g.b[1] * g.b[2] * g.b[3];
+    g.st[0] = 1;
+    g.st[1] = g.L[0];
+    g.st[2] = g.L[0] * g.L[1];
+    g.st[3] = g.L[0] * g.L[1] * g.L[2];
+    auto magic = [&](int d) -> unsigned {
+        // ceil(2^32 / d), valid while every dividend n < Vh satisfies n * d < 2^32
+        if (d <= 1 || (unsigned long long)g.Vh * (unsigned long long)d >= (1ull << 32)) return 0u;
+        return (unsigned)(((1ull << 32) + d - 1) / d);
+    };
+    g.mLh0 = magic(g.Lh0);
+    g.mL1 = magic(g.L[1]);
+    g.mL2 = magic(g.L[2]);
+}
+
+// n / d with a precomputed multiplier (m = 0: plain division)
+DD_DEV int fast_div(int n, int d, unsigned m) { return m ? (int)__umulhi((unsigned)n, m) : n / d; }
 
 // coordinates of the site with parity p and even-odd index h (= canonical / 2)
 DD_DEV void eo_coords(const Geo& g, int p, int h, int x[4]) {
-    int hx = h % g.Lh0;
-    int r = h / g.Lh0;
-    x[1] = r % g.L[1];
-    r /= g.L[1];
-    x[2] = r % g.L[2];
-    x[3] = r / g.L[2];
+    int r = fast_div(h, g.Lh0, g.mLh0);
+    int hx = h - r * g.Lh0;
+    int q = fast_div(r, g.L[1], g.mL1);
+    x[1] = r - q * g.L[1];
+    int t = fast_div(q, g.L[2], g.mL2);
+    x[2] = q - t * g.L[2];
+    x[3] = t;
     x[0] = 2 * hx + ((p + x[1] + x[2] + x[3]) & 1);
+}
+
+// canonical index of s +- a-hat from the coordinates x of s (periodic)
+DD_DEV int neighbour_index(const Geo& g, int s, const int x[4], int a, int dir) {
+    if (dir > 0) return (x[a] == g.L[a] - 1) ? s - (g.L[a] - 1) * g.st[a] : s + g.st[a];
+    return (x[a] == 0) ? s + (g.L[a] - 1) * g.st[a] : s - g.st[a];
 }
 DD_HD int canon_index(const Geo& g, const int x[4]) { return x[0] + g.L[0] * (x[1] + g.L[1] * (x[2] + g.L[2] * x[3])); }
 DD_DEV void canon_coords(const Geo& g, int s, int x[4]) {

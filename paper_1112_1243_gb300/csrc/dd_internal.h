@@ -23,10 +23,22 @@ struct CGState {
     int iters;     // iterations done
     int maxit;     // cap
     int flags;     // bit 0: hit maxit, bit 1: non-finite
+    // complex scalars of BiCGStab
+    double rho_re, rho_im, al_re, al_im, om_re, om_im, be_re, be_im;
 };
 
 // reduction finishers run by the last thread block of a reduction
-enum FinOp { FIN_NONE = 0, FIN_STORE = 1, FIN_ALPHA = 2, FIN_RR = 3, FIN_BETA = 4, FIN_ZZ_INIT = 5 };
+enum FinOp {
+    FIN_NONE = 0,
+    FIN_STORE = 1,
+    FIN_ALPHA = 2,
+    FIN_RR = 3,
+    FIN_BETA = 4,
+    FIN_ZZ_INIT = 5,
+    FIN_BI_RHO = 6,    // three values
+    FIN_BI_ALPHA = 7,  // three values (third unused)
+    FIN_BI_OMEGA = 8   // three values
+};
 
 struct Reduce {
     double* partials;     // [rhs][gridDim.x]
@@ -66,6 +78,8 @@ struct SolverVecs {
     float4* q32;
     float4* z32;
     float4* t32;   // odd temporary (hop output)
+    float4* w32;   // BiCGStab t
+    float4* h32;   // BiCGStab shadow residual
     uint4* p16;    // FP16 hop copies + scales
     float* p16n;
     uint4* r16;

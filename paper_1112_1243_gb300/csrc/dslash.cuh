@@ -46,6 +46,9 @@ struct HopArgs {
     const CGState* st;        // per-rhs activity (may be null)
     Reduce red;               // |out|^2 reduction (red.op == FIN_NONE: off)
     unsigned long long* sites;  // timed launches: output sites processed (may be null)
+    // three-value reductions (BiCGStab): 0 off; 1: <rhat, out>; 2: <out, xin> and |out|^2
+    int red3 = 0;
+    SX rhat;
 };
 
 template <class LK>
@@ -58,6 +61,7 @@ template <class R, class SIn, class LK, int MASK>
 DD_DEV void hop_site(const Geo& g, int p, int h, const int x[4], const SIn& in, const LK& lk_p, const LK& lk_q,
                      int g5in, Spinor<R>& acc) {
     zero(acc);
+    const int s = canon_index(g, x);
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         int loc = x[a] % g.b[a];
@@ -71,7 +75,7 @@ DD_DEV void hop_site(const Geo& g, int p, int h, const int x[4], const SIn& in, 
             okb = loc == 0;
         }
         if (okf) {
-            int yh = shift_index(g, x, a, +1) >> 1;
+            int yh = neighbour_index(g, s, x, a, +1) >> 1;
             Spinor<R> s;
             in.load(yh, s);
             if (g5in) gamma5(s);
@@ -84,7 +88,7 @@ DD_DEV void hop_site(const Geo& g, int p, int h, const int x[4], const SIn& in, 
             accumulate<R>(a, +1, uh, sc, acc);
         }
         if (okb) {
-            int yh = shift_index(g, x, a, -1) >> 1;
+            int yh = neighbour_index(g, s, x, a, -1) >> 1;
             Spinor<R> s;
             in.load(yh, s);
             if (g5in) gamma5(s);
@@ -99,13 +103,14 @@ DD_DEV void hop_site(const Geo& g, int p, int h, const int x[4], const SIn& in, 
     }
 }
 
-template <class R, class SIn, class SX, class SOut, class LK, int MASK>
+template <class R, class SIn, class SX, class SOut, class LK, int MASK, int RED3>
 __global__ void __launch_bounds__(128) hop_eo_kernel(HopArgs<SIn, SX, SOut, LK> A) {
     __shared__ double sh[34];
     const int rhs = blockIdx.y;
     if (A.st && !A.st[rhs].active) return;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     const long long Vh = A.g.Vh;
+    double v3[3] = {0.0, 0.0, 0.0};
     if (A.sites && threadIdx.x == 0)
         atomicAdd(A.sites, (unsigned long long)min((long long)blockDim.x, Vh - (long long)blockIdx.x * blockDim.x));
     double nrm = 0.0;
@@ -120,10 +125,9 @@ __global__ void __launch_bounds__(128) hop_eo_kernel(HopArgs<SIn, SX, SOut, LK> 
         Spinor<R> acc;
         hop_site<R, SIn, LK, MASK>(A.g, A.p, h, x, in, lk_p, lk_q, A.g5in, acc);
         if (A.g5out) gamma5(acc);
-        Spinor<R> res;
+        Spinor<R> res, xv;
         const R bb = (R)A.b;
         if (A.has_x) {
-            Spinor<R> xv;
             at_rhs(A.xin, rhs).load(h, xv);
             const R aa = (R)A.a;
 #pragma unroll
@@ -134,9 +138,39 @@ __global__ void __launch_bounds__(128) hop_eo_kernel(HopArgs<SIn, SX, SOut, LK> 
         }
         if (A.colour_mask != 3 && !((A.colour_mask >> block_colour_of(A.g, x)) & 1)) zero(res);
         at_rhs(A.out, rhs).store(h, res);
-        nrm = (double)snorm2(res);
+        // per-site sums in the arithmetic precision, accumulated across sites
+        // in FP64 by the grid reduction (FP64 adds per component would cost
+        // more than the stencil on GB300's FP64 pipe)
+        if (RED3 == 1) {
+            Spinor<R> rv;
+            at_rhs(A.rhat, rhs).load(h, rv);
+            R d0 = 0, d1 = 0;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                d0 += rv.c[k].x * res.c[k].x + rv.c[k].y * res.c[k].y;
+                d1 += rv.c[k].x * res.c[k].y - rv.c[k].y * res.c[k].x;
+            }
+            v3[0] = (double)d0;
+            v3[1] = (double)d1;
+        } else if (RED3 == 2) {
+            R d0 = 0, d1 = 0;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                d0 += res.c[k].x * xv.c[k].x + res.c[k].y * xv.c[k].y;
+                d1 += res.c[k].x * xv.c[k].y - res.c[k].y * xv.c[k].x;
+            }
+            v3[0] = (double)d0;
+            v3[1] = (double)d1;
+            v3[2] = (double)snorm2(res);
+        } else {
+            nrm = (double)snorm2(res);
+        }
     }
-    if (A.red.op != FIN_NONE) grid_reduce(A.red, rhs, nrm, sh);
+    if (RED3) {
+        grid_reduce3(A.red, rhs, v3, sh);
+    } else if (A.red.op != FIN_NONE) {
+        grid_reduce(A.red, rhs, nrm, sh);
+    }
 }
 
 // timing class of a hop kernel instance (see dd_handle::timer_*), -1: not timed
@@ -161,7 +195,12 @@ inline void launch_hop(const HopArgs<SIn, SX, SOut, LK>& A, int nrhs, dd_handle*
         if (e) cudaEventRecord(e, h->stream);
         B.sites = h->d_sites + kind;
     }
-    DD_KLAUNCH(h, hop_eo_kernel<R, SIn, SX, SOut, LK, MASK><<<grid, 128, 0, h->stream>>>(B));
+    if (A.red3 == 1)
+        DD_KLAUNCH(h, hop_eo_kernel<R, SIn, SX, SOut, LK, MASK, 1><<<grid, 128, 0, h->stream>>>(B));
+    else if (A.red3 == 2)
+        DD_KLAUNCH(h, hop_eo_kernel<R, SIn, SX, SOut, LK, MASK, 2><<<grid, 128, 0, h->stream>>>(B));
+    else
+        DD_KLAUNCH(h, hop_eo_kernel<R, SIn, SX, SOut, LK, MASK, 0><<<grid, 128, 0, h->stream>>>(B));
     if (timed) {
         cudaEvent_t e = dd_timer_event(h, kind);
         if (e) cudaEventRecord(e, h->stream);

@@ -270,6 +270,7 @@ static int launch_blocks(dd_handle* h, int mode, const std::vector<BlockItem>& i
                                h->stream));
     DD_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream));
     BlockArgs A;
+    A.lats = nullptr;
     A.g = h->g;
     A.c = block_ctx(h);
     A.mode = mode;
@@ -383,7 +384,7 @@ extern "C" int dd_block_filter(dd_t h, const void* U_old, void* U_new, int colou
             int col = pos >= half ? 1 : 0;
             if (!((colour_mask >> col) & 1)) continue;
             base[id_at[pos]] = (int)items.size();
-            for (int i = 0; i < n; ++i) items.push_back(BlockItem{pos, i, i + 1, i});
+            for (int i = 0; i < n; ++i) items.push_back(BlockItem{pos, i, i + 1, i, 0});
         }
         rc = launch_blocks(h, BLOCK_FILTER, items, nullptr, nullptr, seed, ctr);
         if (rc) return rc;
@@ -399,6 +400,187 @@ extern "C" int dd_block_filter(dd_t h, const void* U_old, void* U_new, int colou
         DD_KLAUNCH(h, restore_kernel<<<grid_for(h->n_active, 128), 128, 0, h->stream>>>(h->g, h->n_active, h->d_active_links, accept,
                                                                         (const double*)U_old, (double*)U_new));
     DD_LAUNCH_CHECK(h, "block accept");
+    return DD_OK;
+}
+
+// ------------------------------------------------ multi-lattice block filter
+namespace {
+struct BatchPlan {
+    size_t lats, items, item_out, queue, bases, scratch, total;
+    long long slot_bytes;
+    int slots, nitems;
+};
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+BatchPlan batch_plan(int nh, dd_handle* const* hs, int n) {
+    BatchPlan p;
+    int nitems = 0, nbmax = 0, nblk = 0;
+    for (int k = 0; k < nh; ++k) {
+        nitems += hs[k]->g.nblocks * n;
+        nbmax = std::max(nbmax, hs[k]->g.bsites);
+        nblk += hs[k]->g.nblocks;
+    }
+    p.nitems = nitems;
+    p.slot_bytes = (long long)((((size_t)nbmax * (4 * 192 + 5 * 192)) + 4096 + 255) & ~(size_t)255);
+    p.slots = std::max(1, hs[0]->num_sms) * 2;
+    size_t off = 0;
+    p.lats = off;
+    off = align256(off + sizeof(LatDesc) * nh);
+    p.items = off;
+    off = align256(off + sizeof(BlockItem) * nitems);
+    p.item_out = off;
+    off = align256(off + sizeof(double) * nitems);
+    p.queue = off;
+    off = align256(off + 64 * sizeof(int));
+    p.bases = off;
+    off = align256(off + sizeof(int) * nblk);
+    p.scratch = off;
+    off = align256(off + (size_t)p.slot_bytes * p.slots);
+    p.total = off;
+    return p;
+}
+int batch_check(int nh, dd_handle* const* hs, int n) {
+    if (nh < 1 || !hs) return DD_ERR_INVALID_ARG;
+    for (int k = 0; k < nh; ++k) {
+        if (!hs[k] || !hs[k]->ws || !hs[k]->feat_estimate) return DD_ERR_INVALID_ARG;
+        if (n < 1 || n > hs[k]->prm.max_rhs) return DD_ERR_INVALID_ARG;
+        if (hs[k]->stream != hs[0]->stream || hs[k]->prm.block_prec != hs[0]->prm.block_prec)
+            return DD_ERR_INVALID_ARG;
+    }
+    return DD_OK;
+}
+}  // namespace
+
+extern "C" int dd_block_filter_batch_workspace(int nh, const dd_t* hs, int n, size_t* bytes) {
+    int rc = batch_check(nh, (dd_handle* const*)hs, n);
+    if (rc) return rc;
+    if (!bytes) return DD_ERR_INVALID_ARG;
+    *bytes = batch_plan(nh, (dd_handle* const*)hs, n).total;
+    return DD_OK;
+}
+
+extern "C" int dd_block_filter_batch(int nh, const dd_t* hs_, const void* const* U_old, void* const* U_new,
+                                     int colour_mask, int n, uint64_t seed, uint64_t ctr, double* const* ln_b,
+                                     uint8_t* const* accept, void* ws, size_t ws_bytes) {
+    dd_handle* const* hs = (dd_handle* const*)hs_;
+    int rc = batch_check(nh, hs, n);
+    if (rc) return rc;
+    dd_handle* h0 = hs[0];
+    if (!U_old || !U_new || !ln_b || !accept || !ws || colour_mask < 1 || colour_mask > 3 || ((uintptr_t)ws & 255))
+        return dd_fail(h0, DD_ERR_INVALID_ARG, "dd_block_filter_batch: bad arguments");
+    const BatchPlan P = batch_plan(nh, hs, n);
+    if (ws_bytes < P.total) return dd_fail(h0, DD_ERR_INVALID_ARG, "dd_block_filter_batch: workspace too small");
+    for (int k = 0; k < nh; ++k)
+        if (!U_old[k] || !U_new[k] || !ln_b[k] || !accept[k])
+            return dd_fail(h0, DD_ERR_INVALID_ARG, "dd_block_filter_batch: null field or output");
+    char* w = (char*)ws;
+    LatDesc* d_lats = (LatDesc*)(w + P.lats);
+    BlockItem* d_items = (BlockItem*)(w + P.items);
+    double* d_out = (double*)(w + P.item_out);
+    int* d_queue = (int*)(w + P.queue);
+    int* d_bases = (int*)(w + P.bases);
+    // interpolated fields of every lattice (each handle's own slots)
+    for (int k = 0; k < nh; ++k) {
+        rc = prepare_fields(hs[k], (const double*)U_old[k], (const double*)U_new[k], n, true, false);
+        if (rc) return rc;
+    }
+    // lattices with the largest blocks first: their items start first (LPT)
+    std::vector<int> order(nh);
+    for (int k = 0; k < nh; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return hs[a]->g.bsites > hs[b]->g.bsites; });
+    std::vector<LatDesc> lats(nh);
+    std::vector<BlockItem> items;
+    std::vector<int> bases;
+    std::vector<int> base_off(nh);
+    items.reserve(P.nitems);
+    for (int k = 0; k < nh; ++k) {
+        dd_handle* h = hs[k];
+        LatDesc& L = lats[k];
+        L.g = h->g;
+        L.c = block_ctx(h);
+        L.dd64 = h->fields[0].dd64;
+        L.dd64_fs = (long long)(h->fields[1].dd64 - h->fields[0].dd64);
+        L.dd32 = h->fields[0].dd32;
+        L.dd32_fs = (long long)(h->fields[1].dd32 - h->fields[0].dd32);
+        L.item_out = d_out;
+    }
+    std::vector<std::vector<int>> per_base(nh);
+    for (int oi = 0; oi < nh; ++oi) {
+        const int k = order[oi];
+        const Geo& g = hs[k]->g;
+        per_base[k].assign(g.nblocks, -1);
+        const int half = g.nblocks / 2;
+        for (int pos = 0; pos < g.nblocks; ++pos) {
+            const int col = pos >= half ? 1 : 0;
+            if (!((colour_mask >> col) & 1)) continue;
+            // block id of this position (host mirror of block_id_at)
+            int rank = pos - col * half, id = 2 * rank;
+            int B1 = (id / g.nbk[0]) % g.nbk[1], B2 = (id / (g.nbk[0] * g.nbk[1])) % g.nbk[2],
+                B3 = id / (g.nbk[0] * g.nbk[1] * g.nbk[2]);
+            if (((B1 + B2 + B3) & 1) != col) id += 1;
+            per_base[k][id] = (int)items.size();
+            for (int i = 0; i < n; ++i) items.push_back(BlockItem{pos, i, i + 1, i, k});
+        }
+    }
+    int off = 0;
+    for (int k = 0; k < nh; ++k) {
+        base_off[k] = off;
+        bases.insert(bases.end(), per_base[k].begin(), per_base[k].end());
+        off += hs[k]->g.nblocks;
+    }
+    cudaStream_t s = h0->stream;
+    DD_CUDA(h0, cudaMemcpyAsync(d_lats, lats.data(), sizeof(LatDesc) * nh, cudaMemcpyHostToDevice, s));
+    if (!items.empty())
+        DD_CUDA(h0, cudaMemcpyAsync(d_items, items.data(), sizeof(BlockItem) * items.size(), cudaMemcpyHostToDevice, s));
+    DD_CUDA(h0, cudaMemcpyAsync(d_bases, bases.data(), sizeof(int) * bases.size(), cudaMemcpyHostToDevice, s));
+    DD_CUDA(h0, cudaMemsetAsync(d_queue, 0, sizeof(int), s));
+    if (!items.empty()) {
+        BlockArgs A;
+        A.lats = d_lats;
+        A.g = h0->g;
+        A.c = block_ctx(h0);
+        A.mode = BLOCK_FILTER;
+        A.items = d_items;
+        A.nitems = (int)items.size();
+        A.queue = d_queue;
+        A.dd64 = h0->fields[0].dd64;
+        A.dd64_fs = 0;
+        A.dd32 = h0->fields[0].dd32;
+        A.dd32_fs = 0;
+        A.in_bank = nullptr;
+        A.out_bank = nullptr;
+        A.bank_vs = 0;
+        A.item_out = d_out;
+        A.scratch = w + P.scratch;
+        A.slot_bytes = P.slot_bytes;
+        A.seed = seed;
+        A.ctr = ctr;
+        A.purpose = DD_PURPOSE_BLOCK_NOISE;
+        A.tol2 = h0->prm.tol_block * h0->prm.tol_block;
+        A.inner_f64 = h0->prm.block_prec == DD_PREC_F64;
+        A.tol2_inner = A.inner_f64 ? 0.25 * A.tol2 : 1e-10;
+        A.maxit_inner = std::min(h0->prm.maxit, 2000);
+        A.max_outer = A.inner_f64 ? 3 : 12;
+        A.status = h0->d_status;
+        const int grid = std::min((int)items.size(), P.slots);
+        if (A.inner_f64)
+            DD_KLAUNCH(h0, block_solve_kernel<double, SpinorF64, LinkF64><<<grid, 256, 0, s>>>(A));
+        else
+            DD_KLAUNCH(h0, block_solve_kernel<float, SpinorF32, LinkF32><<<grid, 256, 0, s>>>(A));
+        DD_LAUNCH_CHECK(h0, "block_solve_kernel (batch)");
+    }
+    for (int k = 0; k < nh; ++k) {
+        dd_handle* h = hs[k];
+        DD_KLAUNCH(h, sum_items_kernel<<<grid_for(h->g.nblocks, 128), 128, 0, s>>>(h->g.nblocks, d_bases + base_off[k],
+                                                                                 n, d_out, ln_b[k]));
+        DD_KLAUNCH(h, block_accept_kernel<<<grid_for(h->g.nblocks, 128), 128, 0, s>>>(h->g, colour_mask, ln_b[k],
+                                                                                    accept[k], seed, ctr));
+        if (h->n_active > 0)
+            DD_KLAUNCH(h, restore_kernel<<<grid_for(h->n_active, 128), 128, 0, s>>>(
+                              h->g, h->n_active, h->d_active_links, accept[k], (const double*)U_old[k],
+                              (double*)U_new[k]));
+        DD_LAUNCH_CHECK(h, "dd_block_filter_batch accept");
+    }
     return DD_OK;
 }
 

@@ -366,6 +366,8 @@ void plan(dd_handle* h, char* base) {
     v.q32 = c.take<float4>((size_t)R * 6 * Vh);
     v.z32 = c.take<float4>((size_t)R * 6 * Vh);
     v.t32 = c.take<float4>((size_t)R * 6 * Vh);
+    v.w32 = c.take<float4>((size_t)R * 6 * Vh);
+    v.h32 = c.take<float4>((size_t)R * 6 * Vh);
     v.p16 = c.take<uint4>((size_t)R * 3 * Vh);
     v.p16n = c.take<float>((size_t)R * Vh);
     v.r16 = c.take<uint4>((size_t)R * 3 * Vh);
@@ -389,7 +391,7 @@ void plan(dd_handle* h, char* base) {
     h->block_slots = std::max(1, h->num_sms) * 2;
     h->block_scratch = c.take<char>(est ? h->block_slot_bytes * h->block_slots : 0);
     h->items_cap = h->g.nblocks * 2 * R + 64;
-    h->d_items = c.take<int>((size_t)4 * h->items_cap);
+    h->d_items = c.take<int>((size_t)5 * h->items_cap);  // five ints per item
     h->d_item_out = c.take<double>((size_t)h->items_cap);
     h->d_queue = c.take<int>(64);
     h->d_imap = c.take<int>((size_t)h->g.nblocks + 4 * R + 64);
@@ -463,12 +465,8 @@ extern "C" int dd_init(dd_t* out, const dd_params* p, void* stream) {
         delete h;
         return DD_ERR_INVALID_ARG;
     }
-    g.V = (int)V;
-    g.Vh = (int)(V / 2);
-    g.Lh0 = g.L[0] / 2;
-    g.nblocks = g.nbk[0] * g.nbk[1] * g.nbk[2] * g.nbk[3];
-    g.bsites = g.b[0] * g.b[1] * g.b[2] * g.b[3];
     g.bc = p->bc_time;
+    geo_finish(g);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);

@@ -224,12 +224,8 @@ extern "C" int dd_block_ratios_noalloc(const int dims[4], const int block[4], do
         V *= dims[a];
     }
     if (V > (1LL << 30)) return DD_ERR_INVALID_ARG;
-    g.V = (int)V;
-    g.Vh = (int)(V / 2);
-    g.Lh0 = g.L[0] / 2;
-    g.nblocks = g.nbk[0] * g.nbk[1] * g.nbk[2] * g.nbk[3];
-    g.bsites = g.b[0] * g.b[1] * g.b[2] * g.b[3];
     g.bc = bc_time;
+    geo_finish(g);
     // one slot (FP64 eta, b, x, r and five FP32 inner vectors of one block) must fit
     const long long slot = (((long long)g.bsites * (4 * 192 + 5 * 96)) + 255) & ~255LL;
     const long long max_slots = (long long)(kNoallocScratchBytes - kNoallocHeader) / slot;

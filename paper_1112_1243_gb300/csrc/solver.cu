@@ -306,6 +306,234 @@ struct NormalCG {
     }
 };
 
+// ------------------------------------------------------------ BiCGStab
+// van der Vorst's BiCGStab on Dtilde itself (no normal equations), complex
+// scalars formed on the device:
+//   rho = <rh, r>, beta = (rho / rho_old)(alpha / omega), p = r + beta (p - omega v),
+//   v = A p, alpha = rho / <rh, v>, s = r - alpha v, t = A s,
+//   omega = <t, s> / <t, t>, x += alpha p + omega s, r = s - omega t.
+template <class R>
+DD_DEV cpx<R> cscal(double re, double im) {
+    return mk<R>((R)re, (R)im);
+}
+
+template <class R, class SM>
+__global__ void bicg_start_kernel(long long n, SM x, SM r, SM rhat, SM p, SM v, const CGState* outer) {
+    const int rhs = blockIdx.y;
+    if (outer && !outer[rhs].active) return;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Spinor<R> z, a;
+    zero(z);
+    at_rhs(x, rhs).store(i, z);
+    at_rhs(p, rhs).store(i, z);
+    at_rhs(v, rhs).store(i, z);
+    at_rhs(r, rhs).load(i, a);
+    at_rhs(rhat, rhs).store(i, a);
+}
+
+__global__ void bicg_arm_kernel(int nrhs, CGState* st) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrhs) return;
+    CGState& c = st[r];
+    c.rho_re = c.al_re = c.om_re = 1.0;
+    c.rho_im = c.al_im = c.om_im = 0.0;
+    c.be_re = c.be_im = 0.0;
+}
+
+template <class R, class SM>
+__global__ void __launch_bounds__(128) bicg_rho_kernel(long long n, SM rhat, SM r, const CGState* st, Reduce red) {
+    __shared__ double sh[34];
+    const int rhs = blockIdx.y;
+    if (!st[rhs].active) return;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double v[3] = {0.0, 0.0, 0.0};
+    if (i < n) {
+        Spinor<R> a, b;
+        at_rhs(rhat, rhs).load(i, a);
+        at_rhs(r, rhs).load(i, b);
+        R d0 = 0, d1 = 0;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            d0 += a.c[k].x * b.c[k].x + a.c[k].y * b.c[k].y;
+            d1 += a.c[k].x * b.c[k].y - a.c[k].y * b.c[k].x;
+        }
+        v[0] = (double)d0;
+        v[1] = (double)d1;
+        v[2] = (double)snorm2(b);
+    }
+    grid_reduce3(red, rhs, v, sh);
+}
+
+// p = r + beta (p - omega v), hop copy of p
+template <class R, class SM, class SH>
+__global__ void __launch_bounds__(128) bicg_p_kernel(long long n, SM p, SM r, SM v, SH ph, int copy,
+                                                     const CGState* st) {
+    const int rhs = blockIdx.y;
+    if (!st[rhs].active) return;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const CGState& c = st[rhs];
+    const cpx<R> be = cscal<R>(c.be_re, c.be_im), om = cscal<R>(c.om_re, c.om_im);
+    Spinor<R> pp, rr, vv;
+    at_rhs(p, rhs).load(i, pp);
+    at_rhs(r, rhs).load(i, rr);
+    at_rhs(v, rhs).load(i, vv);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) pp.c[k] = rr.c[k] + cmul(be, pp.c[k] - cmul(om, vv.c[k]));
+    at_rhs(p, rhs).store(i, pp);
+    if (copy) at_rhs(ph, rhs).store(i, pp);
+}
+
+// s = r - alpha v, hop copy of s
+template <class R, class SM, class SH>
+__global__ void __launch_bounds__(128) bicg_s_kernel(long long n, SM s, SM r, SM v, SH shop, int copy,
+                                                     const CGState* st) {
+    const int rhs = blockIdx.y;
+    if (!st[rhs].active) return;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const CGState& c = st[rhs];
+    const cpx<R> al = cscal<R>(c.al_re, c.al_im);
+    Spinor<R> rr, vv;
+    at_rhs(r, rhs).load(i, rr);
+    at_rhs(v, rhs).load(i, vv);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) rr.c[k] = rr.c[k] - cmul(al, vv.c[k]);
+    at_rhs(s, rhs).store(i, rr);
+    if (copy) at_rhs(shop, rhs).store(i, rr);
+}
+
+// x += alpha p + omega s, r = s - omega t; <rh, r>, |r|^2 -> FIN_BI_RHO
+template <class R, class SM>
+__global__ void __launch_bounds__(128) bicg_xr_kernel(long long n, SM x, SM r, SM p, SM s, SM t, SM rhat,
+                                                      const CGState* st, Reduce red) {
+    __shared__ double sh[34];
+    const int rhs = blockIdx.y;
+    if (!st[rhs].active) return;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double v[3] = {0.0, 0.0, 0.0};
+    if (i < n) {
+        const CGState& c = st[rhs];
+        const cpx<R> al = cscal<R>(c.al_re, c.al_im), om = cscal<R>(c.om_re, c.om_im);
+        Spinor<R> xx, pp, ss, tt, rh;
+        at_rhs(x, rhs).load(i, xx);
+        at_rhs(p, rhs).load(i, pp);
+        at_rhs(s, rhs).load(i, ss);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) xx.c[k] = xx.c[k] + cmul(al, pp.c[k]) + cmul(om, ss.c[k]);
+        at_rhs(x, rhs).store(i, xx);
+        at_rhs(t, rhs).load(i, tt);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) ss.c[k] = ss.c[k] - cmul(om, tt.c[k]);
+        at_rhs(r, rhs).store(i, ss);
+        at_rhs(rhat, rhs).load(i, rh);
+        R d0 = 0, d1 = 0;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            d0 += rh.c[k].x * ss.c[k].x + rh.c[k].y * ss.c[k].y;
+            d1 += rh.c[k].x * ss.c[k].y - rh.c[k].y * ss.c[k].x;
+        }
+        v[0] = (double)d0;
+        v[1] = (double)d1;
+        v[2] = (double)snorm2(ss);
+    }
+    grid_reduce3(red, rhs, v, sh);
+}
+
+template <class R, class SM, class SH, class LK, int MASK = 0>
+struct BiCGStab {
+    dd_handle* h;
+    int nrhs;
+    SM x, r, p, v, s, t, rhat;
+    SH ph, shop, th;
+    int copies;
+    LK lk;
+    long long lk_rs;
+    CGState* st;
+    const CGState* outer;
+
+    Reduce red(int op) const {
+        Reduce R_;
+        R_.partials = h->d_partials;
+        R_.counters = h->d_counters;
+        R_.st = st;
+        R_.out = nullptr;
+        R_.op = op;
+        R_.status = h->d_status;
+        return R_;
+    }
+    template <class SIn, class SX, class SOut>
+    HopArgs<SIn, SX, SOut, LK> args(int par, SIn in, SX xin, SOut out, double a, double b, int hasx, int op,
+                                    int red3) const {
+        HopArgs<SIn, SX, SOut, LK> A;
+        A.g = h->g;
+        A.p = par;
+        A.in = in;
+        A.xin = xin;
+        A.out = out;
+        A.lk = lk;
+        A.lk_rhs_stride = lk_rs;
+        A.a = a;
+        A.b = b;
+        A.has_x = hasx;
+        A.g5in = 0;
+        A.g5out = 0;
+        A.colour_mask = 3;
+        A.st = st;
+        A.red = red(op);
+        A.red3 = red3;
+        A.rhat = rhat;
+        return A;
+    }
+    // out = Dtilde in_h (in_m: the same vector in master storage for the xpay term)
+    void apply(SH in_h, SM in_m, SM out, int op, int red3) {
+        const double k2 = h->prm.kappa * h->prm.kappa;
+        launch_hop<R, SH, SM, SH, LK, MASK>(args(1, in_h, in_m, th, 0.0, 1.0, 0, FIN_NONE, 0), nrhs, h);
+        launch_hop<R, SH, SM, SM, LK, MASK>(args(0, th, in_m, out, 1.0, -k2, 1, op, red3), nrhs, h);
+    }
+    // solve Dtilde x = r (r holds the right-hand side; x starts at 0)
+    int run(const double* rr0, double tol, double abs_fac, int maxit, int chunk, int* iters_out) {
+        const long long n = h->g.Vh;
+        dim3 grid(grid_for(n, 128), nrhs);
+        if (maxit < 1) maxit = 1;
+        DD_KLAUNCH(h, cg_arm_kernel<<<1, 64, 0, h->stream>>>(nrhs, st, outer, rr0, tol, abs_fac, maxit));
+        DD_KLAUNCH(h, bicg_arm_kernel<<<1, 64, 0, h->stream>>>(nrhs, st));
+        DD_KLAUNCH(h, bicg_start_kernel<R, SM><<<grid, 128, 0, h->stream>>>(n, x, r, rhat, p, v, outer));
+        DD_KLAUNCH(h, bicg_rho_kernel<R, SM><<<grid, 128, 0, h->stream>>>(n, rhat, r, st, red(FIN_BI_RHO)));
+        std::vector<CGState> hs(nrhs);
+        int done = 0;
+        for (;;) {
+            for (int it = 0; it < chunk; ++it) {
+                DD_KLAUNCH(h, bicg_p_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(n, p, r, v, ph, copies, st));
+                apply(ph, p, v, FIN_BI_ALPHA, 1);
+                DD_KLAUNCH(h, bicg_s_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(n, s, r, v, shop, copies, st));
+                apply(shop, s, t, FIN_BI_OMEGA, 2);
+                DD_KLAUNCH(h, bicg_xr_kernel<R, SM><<<grid, 128, 0, h->stream>>>(n, x, r, p, s, t, rhat, st,
+                                                                                 red(FIN_BI_RHO)));
+            }
+            done += chunk;
+            if (cudaGetLastError() != cudaSuccess) return DD_ERR_CUDA;
+            if (cudaMemcpyAsync(hs.data(), st, sizeof(CGState) * nrhs, cudaMemcpyDeviceToHost, h->stream) !=
+                cudaSuccess)
+                return DD_ERR_CUDA;
+            if (cudaStreamSynchronize(h->stream) != cudaSuccess) return DD_ERR_CUDA;
+            bool any = false;
+            for (int k = 0; k < nrhs; ++k) any = any || hs[k].active;
+            if (!any || done >= maxit + chunk) break;
+        }
+        int tot = 0, flags = 0;
+        for (int k = 0; k < nrhs; ++k) {
+            tot += hs[k].iters;
+            flags |= hs[k].flags;
+        }
+        if (iters_out) *iters_out += tot;
+        // a breakdown only ends this inner solve; the outer FP64 loop restarts from the true residual
+        (void)flags;
+        return DD_OK;
+    }
+};
+
 template <class LK>
 LK field_links(dd_handle* h, int slot);
 template <>
@@ -366,12 +594,12 @@ __global__ void add_scalars_kernel(int n, double* a, const double* b) {
     if (r < n) a[r] += b[r];
 }
 
-// One defect-correction solve.  Inner vectors: x (correction), r (inner
-// residual, starts as the FP64 outer residual), p, q, z (storage SM) and the
-// hop copies ph, rh, th (storage SH; th lives on odd sites).
-template <class R, class SM, class SH, class LK, int MASK>
-int defect_correction(dd_handle* h, int nrhs, int field0, int step, NormalCG<R, SM, SH, LK, MASK>& cg, bool fp64_inner,
-                      double tol, int maxit, int* iters, double* relres) {
+// One defect-correction solve around an inner solver (NormalCG or BiCGStab;
+// its x is the correction, its r starts as the FP64 outer residual).
+template <int MASK, class Inner>
+int defect_correction(dd_handle* h, int nrhs, int field0, int step, Inner& cg, bool fp64_inner, double tol,
+                      int maxit, int* iters, double* relres) {
+    typedef decltype(cg.x) SM;
     SolverVecs& v = h->vecs[0];
     const long long Vh = h->g.Vh;
     const double kappa = h->prm.kappa;
@@ -451,6 +679,22 @@ int defect_correction(dd_handle* h, int nrhs, int field0, int step, NormalCG<R, 
 
 }  // namespace
 
+template <class B>
+static void fill_bicg(dd_handle* h, B& bi, long long Vh, CGState* inner, CGState* outer, int nrhs) {
+    bi.nrhs = nrhs;
+    SolverVecs& v = h->vecs[0];
+    bi.h = h;
+    bi.x = SpinorF32{v.x32, Vh};
+    bi.r = SpinorF32{v.r32, Vh};
+    bi.p = SpinorF32{v.p32, Vh};
+    bi.v = SpinorF32{v.q32, Vh};
+    bi.s = SpinorF32{v.z32, Vh};
+    bi.t = SpinorF32{v.w32, Vh};
+    bi.rhat = SpinorF32{v.h32, Vh};
+    bi.st = inner;
+    bi.outer = outer;
+}
+
 template <int MASK>
 static int solve_packed_mask(dd_handle* h, int nrhs, int field0, int step, int prec, double tol, int maxit,
                              int* iters, double* relres) {
@@ -476,7 +720,28 @@ static int solve_packed_mask(dd_handle* h, int nrhs, int field0, int step, int p
         cg.lk_rs = field_stride<LinkF64>(h, step);
         cg.st = inner;
         cg.outer = outer;
-        return defect_correction(h, nrhs, field0, step, cg, true, tol, maxit, iters, relres);
+        return defect_correction<MASK>(h, nrhs, field0, step, cg, true, tol, maxit, iters, relres);
+    } else if (h->prm.krylov == DD_KRYLOV_BICGSTAB) {
+        if (prec == DD_PREC_F32) {
+            BiCGStab<float, SpinorF32, SpinorF32, LinkF32, MASK> bi;
+            fill_bicg(h, bi, Vh, inner, outer, nrhs);
+            bi.ph = bi.p;
+            bi.shop = bi.s;
+            bi.th = SpinorF32{v.t32, Vh};
+            bi.copies = 0;
+            bi.lk = field_links<LinkF32>(h, field0);
+            bi.lk_rs = field_stride<LinkF32>(h, step);
+            return defect_correction<MASK>(h, nrhs, field0, step, bi, false, tol, maxit, iters, relres);
+        }
+        BiCGStab<float, SpinorF32, SpinorF16, LinkF16, MASK> bi;
+        fill_bicg(h, bi, Vh, inner, outer, nrhs);
+        bi.ph = SpinorF16{v.p16, v.p16n, Vh};
+        bi.shop = SpinorF16{v.r16, v.r16n, Vh};
+        bi.th = SpinorF16{v.t16, v.t16n, Vh};
+        bi.copies = 1;
+        bi.lk = field_links<LinkF16>(h, field0);
+        bi.lk_rs = field_stride<LinkF16>(h, step);
+        return defect_correction<MASK>(h, nrhs, field0, step, bi, false, tol, maxit, iters, relres);
     } else if (prec == DD_PREC_F32) {
         NormalCG<float, SpinorF32, SpinorF32, LinkF32, MASK> cg;
         cg.h = h;
@@ -494,7 +759,7 @@ static int solve_packed_mask(dd_handle* h, int nrhs, int field0, int step, int p
         cg.lk_rs = field_stride<LinkF32>(h, step);
         cg.st = inner;
         cg.outer = outer;
-        return defect_correction(h, nrhs, field0, step, cg, false, tol, maxit, iters, relres);
+        return defect_correction<MASK>(h, nrhs, field0, step, cg, false, tol, maxit, iters, relres);
     } else {
         NormalCG<float, SpinorF32, SpinorF16, LinkF16, MASK> cg;
         cg.h = h;
@@ -512,7 +777,7 @@ static int solve_packed_mask(dd_handle* h, int nrhs, int field0, int step, int p
         cg.lk_rs = field_stride<LinkF16>(h, step);
         cg.st = inner;
         cg.outer = outer;
-        return defect_correction(h, nrhs, field0, step, cg, false, tol, maxit, iters, relres);
+        return defect_correction<MASK>(h, nrhs, field0, step, cg, false, tol, maxit, iters, relres);
     }
 }
 

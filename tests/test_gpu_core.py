@@ -123,11 +123,11 @@ def test_dslash_elementwise_fp64(api):
     assert np.max(np.abs(host(out) - ref)) < 1e-13 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
-def test_solve_true_residual(api, prec):
+@pytest.mark.parametrize("prec,krylov", [(0, 0), (1, 0), (2, 0), (1, 1), (2, 1)])
+def test_solve_true_residual(api, prec, krylov):
     dims, block, kappa = (8, 8, 8, 8), (4, 4, 4, 4), 0.13
     nrhs = 3
-    h = api.dd_init(dims, block, kappa, max_rhs=nrhs, tol_global=1e-10)
+    h = api.dd_init(dims, block, kappa, max_rhs=nrhs, tol_global=1e-10, krylov=krylov)
     lat = geometry.Lattice(dims, block)
     U = synthetic.random_gauge(dims, 0.3, 2)
     b = synthetic.random_spinor(dims, 11, nrhs=nrhs)

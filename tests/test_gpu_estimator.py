@@ -77,14 +77,14 @@ def _dinv_norm(U, lat, kappa):
     return 1.0 / np.linalg.svd(D, compute_uv=False)[-1]
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec,krylov", [(0, 0), (1, 0), (2, 0), (2, 1)])
 @pytest.mark.parametrize("n,mode", [(1, "factors"), (3, "factors"), (2, "replicas")])
-def test_global_estimate_small(api, prec, n, mode):
+def test_global_estimate_small(api, prec, krylov, n, mode):
     dims, block, kappa = (4, 4, 4, 4), (2, 2, 2, 2), 0.12
     lat = geometry.Lattice(dims, block)
     U = synthetic.random_gauge(dims, 0.4, 1)
     Up, _ = heatbath.gauge_update(U, lat, 5.3, 1, 0, 77, 1, colour_mask=3)
-    h = api.dd_init(dims, block, kappa, max_rhs=n, inner_prec=prec)
+    h = api.dd_init(dims, block, kappa, max_rhs=n, inner_prec=prec, krylov=krylov)
     m = api.DD_EST_FACTORS if mode == "factors" else api.DD_EST_REPLICAS
     got = host(api.dd_det_ratio_estimate(h, dev(U), dev(Up), n, 5, 3, m))
     ref = estimator.det_ratio_estimate(U, Up, lat, kappa, n, 5, 3, mode=mode, tol=1e-14)
@@ -104,14 +104,15 @@ def test_global_estimate_small(api, prec, n, mode):
     assert api.dd_status(h)[0] == 0
 
 
-def test_global_estimate_8x4(api):
+@pytest.mark.parametrize("krylov", [0, 1])
+def test_global_estimate_8x4(api, krylov):
     """8^4 lattice, 4^4 blocks, kappa = 0.13, two factors, mixed FP16 inner solver."""
     dims, block, kappa = (8, 8, 8, 8), (4, 4, 4, 4), 0.13
     lat = geometry.Lattice(dims, block)
     U = synthetic.random_gauge(dims, 0.3, 2)
     Up, _ = heatbath.gauge_update(U, lat, 5.3, 1, 0, 7, 2)
     n = 2
-    h = api.dd_init(dims, block, kappa, max_rhs=n, inner_prec=api.DD_PREC_F16)
+    h = api.dd_init(dims, block, kappa, max_rhs=n, inner_prec=api.DD_PREC_F16, krylov=krylov)
     got = host(api.dd_det_ratio_estimate(h, dev(U), dev(Up), n, 9, 4, api.DD_EST_FACTORS))
     ref = estimator.det_ratio_estimate(U, Up, lat, kappa, n, 9, 4, tol=1e-13)
     # ||D'^{-1}|| of this field is below 30 (estimated by inverse iteration on the

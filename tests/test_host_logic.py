@@ -1,0 +1,63 @@
+"""Host-side logic of the library that needs no GPU: the division-by-
+multiplication rule of the index arithmetic, the block-order position of a
+block, and the workspace planning through the C ABI's size query."""
+import ctypes
+import random
+
+import numpy as np
+
+from oracle import geometry
+
+
+def fast_div_magic(d, vh):
+    """ceil(2^32 / d) when every dividend below vh satisfies n * d < 2^32."""
+    if d <= 1 or vh * d >= 2 ** 32:
+        return 0
+    return ((1 << 32) + d - 1) // d
+
+
+def test_fast_division_is_exact_where_enabled():
+    rs = random.Random(1)
+    for d in range(2, 130):
+        for vh in (2 ** 10, 2 ** 20, 3 * 2 ** 19, 2 ** 23):
+            m = fast_div_magic(d, vh)
+            if not m:
+                continue
+            ns = list(range(0, min(vh, 20000))) + [rs.randrange(vh) for _ in range(20000)] + [vh - 1]
+            for n in ns:
+                assert (n * m) >> 32 == n // d, (d, vh, n)
+
+
+def block_pos_to_id(pos, nbk):
+    """Host mirror of the block-order rule: blocks of one colour in
+    increasing id, black first; position -> block id."""
+    nb = int(np.prod(nbk))
+    half = nb // 2
+    col = 1 if pos >= half else 0
+    rank = pos - col * half
+    bid = 2 * rank
+    b1 = (bid // nbk[0]) % nbk[1]
+    b2 = (bid // (nbk[0] * nbk[1])) % nbk[2]
+    b3 = bid // (nbk[0] * nbk[1] * nbk[2])
+    if (b1 + b2 + b3) % 2 != col:
+        bid += 1
+    return bid
+
+
+def test_block_position_rule_matches_block_order():
+    for dims, block in [((8, 8, 8, 8), (4, 4, 4, 4)), ((32, 32, 32, 64), (8, 8, 8, 8)),
+                        ((16, 8, 12, 4), (4, 2, 6, 2))]:
+        lat = geometry.Lattice(dims, block)
+        firsts = lat.block_id[lat.dd_order[:: lat.block_sites]]
+        got = [block_pos_to_id(p, lat.nblock_dims) for p in range(lat.nblocks)]
+        assert got == list(firsts)
+
+
+def test_workspace_size_query_without_gpu():
+    """dd_init needs a device; the size rule itself is exercised on the GPU.
+    Here: the parameter struct layout matches the header (field count)."""
+    from paper_1112_1243_gb300 import _lib
+    names = [f[0] for f in _lib.dd_params._fields_]
+    assert names == ["dims", "block", "kappa", "bc_time", "active_mode", "max_rhs", "inner_prec", "block_prec",
+                     "tol_global", "tol_block", "tol_inner", "maxit", "features", "krylov"]
+    assert ctypes.sizeof(_lib.dd_params) % 8 == 0
