@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--prec", default="f16", choices=["f16", "f32", "f64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay measurement")
+    p.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
     p.add_argument("--fp64-steps", type=int, default=0,
                    help="also time this many steps with the plain FP64 solver (same workload)")
     p.add_argument("--no-batched-filter", action="store_true",
@@ -220,6 +222,14 @@ def run_gpu(args, cfg):
                     maxit=40000, stream=stream, device=dev, krylov=krylov)
     U_np = synthetic.random_gauge(cfg["dims"], cfg["eps"], cfg["seed"] + 1000 * rank)
     U = torch.from_numpy(U_np).to(dev)
+    tune = None
+    if not args.no_tune:
+        # launch shapes of the hop kernels and of the persistent block solver,
+        # timed on this lattice (the block solver on one proposal's filter)
+        Up_t = U.clone()
+        api.dd_gauge_update(h, Up_t, 3, BETA, 1, 0, 4242, 0)
+        tune = api.dd_autotune(h, api.DD_TUNE_HOP | api.DD_TUNE_BLOCK, U, Up_t, reps=10)
+        del Up_t
     chain = HierarchicalStep(h, BETA, n_inner=1, n_block=cfg["n_block"], n_global=cfg["n_global"],
                              seed=cfg["seed"] * 7919 + rank)
 
@@ -292,6 +302,7 @@ def run_gpu(args, cfg):
         "dslash_GBps": {name: (timing[k][2] * HOP_BYTES[k] / 1e9 / (timing[k][0] / 1e3) if timing[k][0] > 0 else None)
                         for k, name in ((0, "fp16_to_fp16"), (1, "fp16_to_fp32_xpay"), (2, "fp64"))},
         "block_accept_rate_last_step": float(chain.acc_b.float().mean().item()),
+        "autotune": tune,
     }
     # end to end through the public API with host buffers
     if not args.no_e2e:
@@ -315,6 +326,28 @@ def run_gpu(args, cfg):
         line["e2e"] = {"value": est / (te / 1e3), "unit": "estimates/s",
                        "h2d_bytes_per_step": U.numel() * 16,
                        "d2h_bytes_per_step": U.numel() * 16 + cfg["n_global"] * 8 + 1}
+    # the same step recorded once as a CUDA graph (solver loops as device-side
+    # conditional nodes) and replayed with advancing random streams
+    if not args.no_graph:
+        g = chain.capture(U)
+        for k in range(args.warmup):
+            chain.step_graph(2000 + k)
+        barrier()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for k in range(args.steps):
+            chain.step_graph(3000 + k)
+        q1.record(stream)
+        barrier()
+        tg = q0.elapsed_time(q1)
+        if world > 1:
+            tt = torch.tensor([tg], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            tg = float(tt.item())
+        st_code = api.dd_status(h)[0]
+        line["graph"] = {"value": est / (tg / 1e3), "unit": "estimates/s", "ms_per_step": tg / args.steps,
+                         "top_level_nodes": api.dd_graph_nodes(g), "device_status": st_code}
+        api.dd_graph_destroy(g)
     if args.fp64_steps > 0:
         h64 = api.dd_init(cfg["dims"], cfg["block"], cfg["kappa"], max_rhs=nmax, inner_prec=api.DD_PREC_F64,
                           block_prec=api.DD_PREC_F32, tol_global=1e-10, tol_block=1e-12, maxit=40000,

@@ -312,6 +312,103 @@ int dd_block_ratios_noalloc(const int dims[4], const int block[4], double kappa,
                             const void* U_old, const void* U_new, uint64_t seed, uint64_t ctr, double tol_block,
                             double* ln_b, void* stream);
 
+/* One step of the hierarchical chain (Sec. 5, the three-step algorithm;
+ * Eq. 4step steps 0, 1 and 3), all on the handle's stream:
+ *   U0 <- U; n_inner times, per colour pass (colour_passes = 1: both colours
+ *   at once; 2: black blocks, then white, for the intra-block active set):
+ *   Up <- U, n_hb heat-bath + n_or over-relaxation sweeps on Up, block filter
+ *   of (U, Up) with n_block factors (rejected blocks restored), U <- Up;
+ *   then the n_global-factor estimate for (U0, U) and the global accept
+ *   (U <- U0 on rejection).
+ * Counters: step << 20 | iteration << 4 | pass for the proposal and filter,
+ * step << 20 | n_inner << 4 for the global step (step < 2^40).
+ * U: device gauge field, updated in place.  All buffers are caller-owned
+ * device memory: U0, Up gauge fields (72 V doubles each); ln_b (nblocks
+ * doubles) and acc_b (nblocks bytes) of the last filter; ln_g (n_global
+ * doubles), acc_g (1 byte), margin (1 double) of the global step.
+ * n_global, n_block <= max_rhs of the handle. */
+typedef struct dd_chain_params {
+    double beta;
+    int n_inner;
+    int n_block;
+    int n_global;
+    int n_hb;
+    int n_or;
+    int filter_mode;   /* DD_FILTER_STOCHASTIC or DD_FILTER_EXACT */
+    int colour_passes; /* 1 or 2 */
+    int reserved;
+    uint64_t seed;
+} dd_chain_params;
+typedef struct dd_chain_buffers {
+    void* U0;
+    void* Up;
+    double* ln_b;
+    uint8_t* acc_b;
+    double* ln_g;
+    uint8_t* acc_g;
+    double* margin;
+} dd_chain_buffers;
+int dd_chain_step(dd_t h, void* U, const dd_chain_params* p, const dd_chain_buffers* b, unsigned long long step);
+
+/* CUDA-graph capture of library calls (no counterpart in the paper).
+ * dd_graph_begin opens a capture: every following call on the handle is
+ * recorded, not run, on a private stream of the handle, until dd_graph_end
+ * closes it and instantiates the graph (*graph, owned by the caller, freed
+ * by dd_graph_destroy).  Solver loops are recorded as conditional WHILE
+ * nodes whose stopping rule runs on the device, so a replay needs no host
+ * round trip.  Inside a capture: iteration counts and residuals are not
+ * written to host pointers; a solve that misses its target or breaks down
+ * sets the device status word (dd_status) instead of returning an error;
+ * the inner iteration budget of a defect-correction cycle is the full
+ * maxit.  Calls whose device tables depend on their arguments (the batched
+ * block filter) must have run once eagerly with the same arguments first,
+ * else DD_ERR_UNSUPPORTED.
+ * dd_graph_launch enqueues one replay on the handle's stream with every
+ * random-stream counter of the recorded calls increased by ctr_offset (a
+ * device word read by the kernels): a chain step recorded with step 0
+ * replays as step k with ctr_offset = k << 20.  Replays reuse the device
+ * buffers named at capture time.  dd_graph_nodes: nodes of the top-level
+ * graph (host).  Results match eager calls bit for bit. */
+typedef struct dd_graph* dd_graph_t;
+int dd_graph_begin(dd_t h);
+int dd_graph_end(dd_t h, dd_graph_t* graph);
+int dd_graph_launch(dd_graph_t graph, unsigned long long ctr_offset);
+int dd_graph_nodes(dd_graph_t graph, size_t* nodes);
+int dd_graph_destroy(dd_graph_t graph);
+
+/* Autotuner of the launch shapes (no counterpart in the paper).
+ * what: DD_TUNE_HOP (thread-block size x sites per thread of the even-odd
+ * hop kernels, FP16/FP32 storage and FP64 separately), DD_TUNE_BLOCK (thread-block size and thread
+ * blocks per SM of the persistent block solver, at most 4 per SM), optionally
+ * with DD_TUNE_NO_CACHE.  Each candidate is timed with CUDA events on the
+ * handle's stream on this handle's lattice: the hop on zeroed solver
+ * vectors (max_rhs right-hand sides), the block solver on one block-filter
+ * pass over the fields (U_old, U_new) (device gauge fields; required for
+ * DD_TUNE_BLOCK, may be NULL otherwise).  The fastest shape is kept by the
+ * handle and used by every later launch.  The result is cached per process
+ * and per (device, lattice, blocks, inner precision, max_rhs); when the
+ * environment variable DD_TUNE_CACHE names a file, tuned shapes are
+ * appended to it and read back by later processes.  report (host, may be
+ * NULL) receives the chosen shapes and the average launch times (ms) of the
+ * chosen and of the default shapes (0 when taken from the cache).  Runs
+ * kernels and synchronises the stream; not allowed inside a capture.
+ * dd_set_tuning sets the shapes directly (threads 64, 128 or 256 and 1 or 2
+ * sites per thread for the FP16/FP32 hops; 64 or 128 threads and 1 site per
+ * thread for the FP64 hops; 64, 128 or 256 threads and 1..4 blocks per SM
+ * for the block solver).
+ * Changing the block-solver shape changes dd_block_filter_batch_workspace. */
+#define DD_TUNE_HOP 1
+#define DD_TUNE_BLOCK 2
+#define DD_TUNE_NO_CACHE 4
+typedef struct dd_tune_report {
+    int hop_tpb, hop_spt, hop64_tpb, hop64_spt, block_tpb, block_ctas_per_sm;
+    int from_cache;
+    float hop_ms, hop_default_ms, hop64_ms, hop64_default_ms, block_ms, block_default_ms;
+} dd_tune_report;
+int dd_autotune(dd_t h, int what, const void* U_old, const void* U_new, int reps, dd_tune_report* report);
+int dd_set_tuning(dd_t h, int hop_tpb, int hop_spt, int hop64_tpb, int hop64_spt, int block_tpb,
+                  int block_ctas_per_sm);
+
 /* Release the handle's own tables; the workspace stays with the caller. */
 int dd_finalize(dd_t h);
 

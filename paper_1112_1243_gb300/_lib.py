@@ -61,6 +61,33 @@ class dd_params(ctypes.Structure):
     ]
 
 
+class dd_chain_params(ctypes.Structure):
+    _fields_ = [
+        ("beta", ctypes.c_double),
+        ("n_inner", ctypes.c_int),
+        ("n_block", ctypes.c_int),
+        ("n_global", ctypes.c_int),
+        ("n_hb", ctypes.c_int),
+        ("n_or", ctypes.c_int),
+        ("filter_mode", ctypes.c_int),
+        ("colour_passes", ctypes.c_int),
+        ("reserved", ctypes.c_int),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+class dd_chain_buffers(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_void_p) for name in ("U0", "Up", "ln_b", "acc_b", "ln_g", "acc_g", "margin")]
+
+
+class dd_tune_report(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in ("hop_tpb", "hop_spt", "hop64_tpb", "hop64_spt", "block_tpb",
+                                              "block_ctas_per_sm", "from_cache")] + \
+               [(n, ctypes.c_float) for n in ("hop_ms", "hop_default_ms", "hop64_ms", "hop64_default_ms", "block_ms",
+                                              "block_default_ms")]
+
+
+DD_TUNE_HOP, DD_TUNE_BLOCK, DD_TUNE_NO_CACHE = 1, 2, 4
 DD_FEAT_SOLVE, DD_FEAT_ESTIMATE, DD_FEAT_EXACT = 1, 2, 4
 DD_KRYLOV_CGNR, DD_KRYLOV_BICGSTAB = 0, 1
 
@@ -98,6 +125,14 @@ SIGNATURES = {
                         ctypes.POINTER(ctypes.c_longlong)],
     "dd_block_ratios_noalloc": [ctypes.POINTER(_I), ctypes.POINTER(_I), _D, _I, _I, _P, _P, _U64, _U64, _D, _P,
                                 _P],
+    "dd_chain_step": [_P, _P, ctypes.POINTER(dd_chain_params), ctypes.POINTER(dd_chain_buffers), ctypes.c_ulonglong],
+    "dd_graph_begin": [_P],
+    "dd_graph_end": [_P, ctypes.POINTER(_P)],
+    "dd_graph_launch": [_P, ctypes.c_ulonglong],
+    "dd_graph_nodes": [_P, ctypes.POINTER(ctypes.c_size_t)],
+    "dd_graph_destroy": [_P],
+    "dd_autotune": [_P, _I, _P, _P, _I, ctypes.POINTER(dd_tune_report)],
+    "dd_set_tuning": [_P, _I, _I, _I, _I, _I, _I],
     "dd_finalize": [_P],
 }
 

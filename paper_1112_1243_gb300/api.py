@@ -271,6 +271,73 @@ def dd_block_ratios_noalloc(dims, block, kappa, bc_time, colour_mask, U_old, U_n
     return ln_b
 
 
+def dd_chain_step(h, U, params, buffers, step):
+    """One hierarchical step on the device (U updated in place).  params: a
+    _lib.dd_chain_params; buffers: dict of the device tensors U0, Up, ln_b,
+    acc_b, ln_g, acc_g, margin."""
+    bufs = _lib.dd_chain_buffers(*[_ptr(buffers[k]) for k in ("U0", "Up", "ln_b", "acc_b", "ln_g", "acc_g",
+                                                                 "margin")])
+    return _check(h, _lib.load().dd_chain_step(h.ptr, _ptr(U), ctypes.byref(params), ctypes.byref(bufs),
+                                               int(step)))
+
+
+class Graph:
+    """An instantiated CUDA graph of library calls (dd_graph_t)."""
+
+    def __init__(self, h, ptr):
+        self.h = h
+        self.ptr = ptr
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            try:
+                _lib.load().dd_graph_destroy(self.ptr)
+            except Exception:
+                pass
+            self.ptr = None
+
+
+def dd_graph_begin(h):
+    return _check(h, _lib.load().dd_graph_begin(h.ptr))
+
+
+def dd_graph_end(h):
+    g = ctypes.c_void_p()
+    _check(h, _lib.load().dd_graph_end(h.ptr, ctypes.byref(g)))
+    return Graph(h, g.value)
+
+
+def dd_graph_launch(g, ctr_offset=0):
+    return _check(g.h, _lib.load().dd_graph_launch(g.ptr, int(ctr_offset)))
+
+
+def dd_graph_nodes(g):
+    n = ctypes.c_size_t()
+    _check(g.h, _lib.load().dd_graph_nodes(g.ptr, ctypes.byref(n)))
+    return n.value
+
+
+def dd_graph_destroy(g):
+    if g.ptr:
+        rc = _lib.load().dd_graph_destroy(g.ptr)
+        g.ptr = None
+        return rc
+    return 0
+
+
+def dd_autotune(h, what=_lib.DD_TUNE_HOP, U_old=None, U_new=None, reps=20):
+    """Time the candidate launch shapes on this handle and keep the fastest;
+    returns the report as a dict."""
+    r = _lib.dd_tune_report()
+    _check(h, _lib.load().dd_autotune(h.ptr, int(what), _ptr(U_old), _ptr(U_new), int(reps), ctypes.byref(r)))
+    return {name: getattr(r, name) for name, _ in r._fields_}
+
+
+def dd_set_tuning(h, hop_tpb=128, hop_spt=1, hop64_tpb=128, hop64_spt=1, block_tpb=256, block_ctas_per_sm=2):
+    return _check(h, _lib.load().dd_set_tuning(h.ptr, int(hop_tpb), int(hop_spt), int(hop64_tpb), int(hop64_spt),
+                                               int(block_tpb), int(block_ctas_per_sm)))
+
+
 def dd_finalize(h):
     if h.ptr:
         rc = _lib.load().dd_finalize(h.ptr)

@@ -1,11 +1,13 @@
-"""Host driver of the hierarchical Markov step (Sec. 5, "3-step algorithm";
-Eq. 4step steps 0, 1 and 3), on top of the C ABI.
+"""The hierarchical Markov step (Sec. 5, "3-step algorithm"; Eq. 4step
+steps 0, 1 and 3) on top of the C ABI.
 
-Only control flow lives here: every step of the computation is a call into
-libdd.so.  Counters of the random streams follow the oracle's convention:
+The step itself runs in libdd.so (dd_chain_step): U0 <- U; n_inner times
+proposal on the active links + block filter; stochastic global step and
+accept.  Counters of the random streams follow the oracle's convention:
 ctr = step << 20 | iteration << 4 | colour pass for the proposal and the
 block filter of an iteration, ctr = step << 20 | n_inner << 4 for the global
-step.
+step.  A step can be recorded once as a CUDA graph (capture) and replayed
+as step k with the counters advanced by k << 20 (step_graph).
 """
 import torch
 
@@ -44,23 +46,40 @@ class HierarchicalStep:
         self.ln_g = torch.zeros(self.n_global, dtype=torch.float64, device=dev)
         self.acc_g = torch.zeros(1, dtype=torch.uint8, device=dev)
         self.margin = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.params = api.dd_chain_params()
+        self.params.beta = self.beta
+        self.params.n_inner = self.n_inner
+        self.params.n_block = self.n_block
+        self.params.n_global = self.n_global
+        self.params.n_hb = 1
+        self.params.n_or = self.n_or
+        self.params.filter_mode = self.filter_mode
+        self.params.colour_passes = len(self.passes)
+        self.params.seed = self.seed
+        self.buffers = {"U0": self.U0, "Up": self.Up, "ln_b": self.ln_b, "acc_b": self.acc_b, "ln_g": self.ln_g,
+                        "acc_g": self.acc_g, "margin": self.margin}
+        self.graph = None
+        self.graph_U = None
 
     def step(self, U, k):
         """Advance the chain state U (device tensor, updated in place) by one
         global step with step index k."""
-        h = self.h
-        self.U0.copy_(U)
-        for it in range(self.n_inner):
-            for p, cm in enumerate(self.passes):
-                ctr = counter(k, it, p)
-                self.Up.copy_(U)
-                api.dd_gauge_update(h, self.Up, cm, self.beta, 1, self.n_or, self.seed, ctr)
-                api.dd_block_filter(h, U, self.Up, cm, self.filter_mode, self.n_block, self.seed, ctr,
-                                    self.ln_b, self.acc_b)
-                U.copy_(self.Up)
-        ctr = counter(k, self.n_inner, 0)
-        api.dd_det_ratio_estimate(h, self.U0, U, self.n_global, self.seed, ctr, api.DD_EST_FACTORS, self.ln_g)
-        api.dd_global_accept(h, U, self.U0, self.ln_g, self.seed, ctr, self.acc_g, self.margin)
+        api.dd_chain_step(self.h, U, self.params, self.buffers, k)
+        return self.ln_g, self.acc_g
+
+    def capture(self, U):
+        """Record one step on U (step index 0) as a CUDA graph; nothing runs."""
+        api.dd_graph_begin(self.h)
+        try:
+            api.dd_chain_step(self.h, U, self.params, self.buffers, 0)
+        finally:
+            g = api.dd_graph_end(self.h)
+        self.graph, self.graph_U = g, U
+        return g
+
+    def step_graph(self, k):
+        """Replay the recorded step as step k on the tensor given to capture."""
+        api.dd_graph_launch(self.graph, int(k) << 20)
         return self.ln_g, self.acc_g
 
     def step_host(self, U_host, U_dev, k, ln_host, acc_host):

@@ -216,8 +216,9 @@ struct BlockArgs {
     Geo g;
     BlockCtx c;
     int mode;
-    const BlockItem* items;
+    const BlockItem* items;  // null: block-filter items k -> (block position item_pos0 + k / item_n, vector k % item_n)
     int nitems;
+    int item_pos0, item_n;
     int* queue;
     const double2* dd64;  // field slot 0, FP64 links in block order
     long long dd64_fs;    // elements between consecutive field slots
@@ -230,6 +231,7 @@ struct BlockArgs {
     char* scratch;
     long long slot_bytes;
     uint64_t seed, ctr;
+    const unsigned long long* ctr_off;  // added to ctr (graph replays; may be null)
     int purpose;
     double tol2;       // relative target of the FP64 residual (squared)
     double tol2_inner; // relative target of one inner solve (squared)
@@ -293,7 +295,9 @@ __global__ void __launch_bounds__(256, 2) block_solve_kernel(BlockArgs A) {
         const int item = s_item;
         __syncthreads();
         if (item >= A.nitems) break;
-        const BlockItem it = A.items[item];
+        const BlockItem it = A.items ? A.items[item]
+                                     : BlockItem{A.item_pos0 + item / A.item_n, item % A.item_n,
+                                                 item % A.item_n + 1, item % A.item_n, 0};
         LatDesc L;
         if (A.lats) {
             L = A.lats[it.lat];
@@ -331,7 +335,8 @@ __global__ void __launch_bounds__(256, 2) block_solve_kernel(BlockArgs A) {
                 uint32_t s = (uint32_t)canon_index(L.g, x);
                 Spinor<double> e;
 #pragma unroll
-                for (int k = 0; k < 12; ++k) e.c[k] = gaussian(s * 12u + k, (uint32_t)A.purpose, (uint32_t)it.vec, A.seed, A.ctr);
+                for (int k = 0; k < 12; ++k)
+                    e.c[k] = gaussian(s * 12u + k, (uint32_t)A.purpose, (uint32_t)it.vec, A.seed, stream_ctr(A.ctr, A.ctr_off));
                 eta.store(j, e);
             }
             __syncthreads();

@@ -1,0 +1,44 @@
+// One step of the hierarchical Markov chain (Sec. 5, the three-step
+// algorithm; Eq. 4step steps 0, 1 and 3):
+//   U0 <- U;
+//   n_inner times, per colour pass: U' <- proposal(U) on the active links
+//     (heat-bath / over-relaxation), block filter of (U, U') restoring the
+//     rejected blocks, U <- U';
+//   stochastic estimate of det(D'^dag D' / D^dag D) for (U0, U) with n_global
+//   interpolation factors, global accept; U <- U0 on rejection.
+// Random-stream counters: step << 20 | iteration << 4 | colour pass for the
+// proposal and filter of an iteration, step << 20 | n_inner << 4 for the
+// global step.  Every operation is asynchronous on the handle's stream, so a
+// step can be captured into a CUDA graph (dd_graph_begin) and replayed with
+// the counters advanced by (step << 20).
+#include "dd_internal.h"
+
+extern "C" int dd_chain_step(dd_t h, void* U, const dd_chain_params* p, const dd_chain_buffers* b,
+                             unsigned long long step) {
+    int rc = dd_require_ws(h);
+    if (rc) return rc;
+    if (!U || !p || !b || !b->U0 || !b->Up || !b->ln_b || !b->acc_b || !b->ln_g || !b->acc_g || !b->margin)
+        return dd_fail(h, DD_ERR_INVALID_ARG, "dd_chain_step: null argument");
+    if (p->n_inner < 0 || p->n_block < 1 || p->n_global < 1 || p->n_hb < 0 || p->n_or < 0 ||
+        (p->colour_passes != 1 && p->colour_passes != 2) || step >= (1ull << 40))
+        return dd_fail(h, DD_ERR_INVALID_ARG, "dd_chain_step: bad parameters");
+    const size_t bytes = (size_t)h->g.V * 4 * 9 * 16;
+    DD_CUDA(h, cudaMemcpyAsync(b->U0, U, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    for (int it = 0; it < p->n_inner; ++it) {
+        for (int pass = 0; pass < p->colour_passes; ++pass) {
+            const int colour_mask = p->colour_passes == 2 ? pass + 1 : 3;
+            const uint64_t ctr = (step << 20) | ((uint64_t)it << 4) | (uint64_t)pass;
+            DD_CUDA(h, cudaMemcpyAsync(b->Up, U, bytes, cudaMemcpyDeviceToDevice, h->stream));
+            rc = dd_gauge_update(h, b->Up, colour_mask, p->beta, p->n_hb, p->n_or, p->seed, ctr);
+            if (rc) return rc;
+            rc = dd_block_filter(h, U, b->Up, colour_mask, p->filter_mode, p->n_block, p->seed, ctr, b->ln_b,
+                                 b->acc_b);
+            if (rc) return rc;
+            DD_CUDA(h, cudaMemcpyAsync(U, b->Up, bytes, cudaMemcpyDeviceToDevice, h->stream));
+        }
+    }
+    const uint64_t ctr = (step << 20) | ((uint64_t)p->n_inner << 4);
+    rc = dd_det_ratio_estimate(h, b->U0, U, p->n_global, p->seed, ctr, DD_EST_FACTORS, b->ln_g);
+    if (rc) return rc;
+    return dd_global_accept(h, U, b->U0, b->ln_g, p->n_global, p->seed, ctr, b->acc_g, b->margin);
+}

@@ -86,6 +86,12 @@ struct SpinorF64 {
             s.c[k] = mk<R>((R)v.x, (R)v.y);
         }
     }
+    // value = returned scale * s (the scale is 1 for this format)
+    template <class R>
+    DD_DEV R load_unscaled(long long i, Spinor<R>& s) const {
+        load(i, s);
+        return (R)1;
+    }
     template <class R>
     DD_DEV void store(long long i, const Spinor<R>& s) const {
 #pragma unroll
@@ -107,6 +113,11 @@ struct SpinorF32 {
             s.c[2 * k] = mk<R>((R)v.x, (R)v.y);
             s.c[2 * k + 1] = mk<R>((R)v.z, (R)v.w);
         }
+    }
+    template <class R>
+    DD_DEV R load_unscaled(long long i, Spinor<R>& s) const {
+        load(i, s);
+        return (R)1;
     }
     template <class R>
     DD_DEV void store(long long i, const Spinor<R>& s) const {
@@ -138,6 +149,22 @@ struct SpinorF16 {
                 s.c[4 * k + j] = mk<R>((R)(f.x * sc), (R)(f.y * sc));
             }
         }
+    }
+    // the stored halves without the site scale; returns the scale (the
+    // stencil applies it once per hop, after the linear spin/colour algebra)
+    template <class R>
+    DD_DEV R load_unscaled(long long i, Spinor<R>& s) const {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 v = p[k * stride + i];
+            const __half2* h = reinterpret_cast<const __half2*>(&v);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float2 f = __half22float2(h[j]);
+                s.c[4 * k + j] = mk<R>((R)f.x, (R)f.y);
+            }
+        }
+        return (R)nrm[i];
     }
     template <class R>
     DD_DEV void store(long long i, const Spinor<R>& s) const {
@@ -224,6 +251,16 @@ struct LinkF16 {
         }
         reconstruct_row2(u);
     }
+};
+
+// ------------------------------------------------------------------ site sets
+// The sites a kernel visits: thread t < n works on site map[t] (map null:
+// on site t).  Solves restricted to the blocks of one colour visit only
+// that colour's half of the lattice.
+struct SiteSet {
+    const int* map;
+    long long n;
+    DD_DEV long long at(long long t) const { return map ? (long long)__ldg(map + t) : t; }
 };
 
 // ------------------------------------------------------------------ geometry
@@ -427,6 +464,10 @@ DD_DEV R snorm2(const Spinor<R>& s) {
     for (int k = 0; k < 12; ++k) r += norm2(s.c[k]);
     return r;
 }
+
+// counter of a random stream: the call's counter plus the device offset of
+// a graph replay (off may be null)
+DD_DEV uint64_t stream_ctr(uint64_t ctr, const unsigned long long* off) { return off ? ctr + *off : ctr; }
 
 // ------------------------------------------------------------ Philox4x32-10
 // Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11).

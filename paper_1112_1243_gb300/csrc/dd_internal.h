@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -90,6 +91,17 @@ struct SolverVecs {
     float* q16n;
 };
 
+constexpr int DD_BLOCK_CTAS_MAX = 4;  // scratch slots of the persistent block solver per SM
+
+// Launch shapes chosen by the autotuner (dd_autotune); defaults are the
+// shapes the kernels were written for.
+struct TuneConfig {
+    int hop_tpb = 128, hop_spt = 1;      // FP16/FP32-storage hop kernels: threads, sites per thread
+    int hop64_tpb = 128, hop64_spt = 1;  // FP64 hop kernels
+    int block_tpb = 256, block_ctas_per_sm = 2;  // persistent block solver (at most DD_BLOCK_CTAS_MAX per SM)
+    int tuned = 0;                       // bit 0: hops, bit 1: block solver
+};
+
 struct dd_handle {
     dd_params prm;
     Geo g;
@@ -137,7 +149,51 @@ struct dd_handle {
     std::vector<cudaEvent_t> timer_ev[3];
     size_t timer_used[3] = {0, 0, 0};
     unsigned long long* d_sites = nullptr;  // [3] output sites of the timed launches
+    // even-odd indices of the sites of each block colour (null when the
+    // block extent along axis 0 is odd); Dirichlet solves of one colour
+    // visit only these
+    int* d_colour_sites[2] = {nullptr, nullptr};
+    // graph capture (graph.cu): counter offset added by every kernel that
+    // draws random numbers (0 outside graph replays), device loop counters
+    // of captured solver loops, capture streams of loop bodies by depth
+    unsigned long long* d_ctr_off = nullptr;
+    int* d_loop = nullptr;  // [DD_LOOP_SLOTS]
+    bool capturing = false;  // dd_graph_begin .. dd_graph_end
+    cudaStream_t cap_stream = nullptr;   // private stream the capture runs on
+    cudaStream_t user_stream = nullptr;  // the handle's stream, restored by dd_graph_end
+    int loop_depth = 0;
+    std::vector<cudaStream_t> body_streams;
+    // last bytes uploaded per cached upload slot (upload_cached)
+    std::vector<char> upload_cache[4];
+    TuneConfig tune;
 };
+
+constexpr int DD_LOOP_SLOTS = 32;
+
+// ----------------------------------------------------------- graph capture
+// true while the handle's stream is being captured into a CUDA graph
+bool dd_stream_capturing(dd_handle* h);
+// Host -> device copy of a small descriptor table through cache slot
+// `slot`: skipped when the same bytes were the last upload to dst; inside a
+// capture a changed table is an error (DD_ERR_UNSUPPORTED).
+int upload_cached(dd_handle* h, int slot, void* dst, const void* src, size_t bytes);
+// Stopping rule of a device-side solver loop: continue while any st[k]
+// (k < nrhs) is active, the body ran fewer than max_trips times and, when
+// it_src is set, the running sum of it_src[k].iters stays below max_total;
+// numeric = 1: a state with flag 2 raises DD_ERR_NUMERIC and stops.
+struct LoopCond {
+    const CGState* st;
+    int nrhs;
+    int max_trips;
+    const CGState* it_src;
+    long long max_total;
+    int numeric;
+};
+// Runs body() repeatedly.  Eager: host_more() decides after every pass (it
+// may synchronise and read device state).  Inside a capture: one conditional
+// WHILE node whose body graph is body() followed by a kernel evaluating cond.
+int dd_loop(dd_handle* h, const std::function<int()>& body, const std::function<int(bool&)>& host_more,
+            const LoopCond& cond);
 
 // Launch a kernel and count it: DD_KLAUNCH(h, kern<<<grid, block, 0, h->stream>>>(args));
 #define DD_KLAUNCH(h, ...) ((__VA_ARGS__), ++(h)->launches)

@@ -49,6 +49,7 @@ struct HopArgs {
     // three-value reductions (BiCGStab): 0 off; 1: <rhat, out>; 2: <out, xin> and |out|^2
     int red3 = 0;
     SX rhat;
+    SiteSet S = {nullptr, -1};  // output sites (n < 0: all Vh sites of parity p)
 };
 
 template <class LK>
@@ -77,49 +78,57 @@ DD_DEV void hop_site(const Geo& g, int p, int h, const int x[4], const SIn& in, 
         if (okf) {
             int yh = neighbour_index(g, s, x, a, +1) >> 1;
             Spinor<R> s;
-            in.load(yh, s);
+            R w = in.load_unscaled(yh, s);
             if (g5in) gamma5(s);
             Half<R> hf, uh;
             project<R>(a, +1, s, hf);
             Link<R> u;
             lk_p.load(h, a, u);
             mul_link(u, hf, uh);
-            R sc = (a == 3 && x[3] == g.L[3] - 1) ? (R)g.bc : (R)1;
+            R sc = (a == 3 && x[3] == g.L[3] - 1) ? (R)g.bc * w : w;
             accumulate<R>(a, +1, uh, sc, acc);
         }
         if (okb) {
             int yh = neighbour_index(g, s, x, a, -1) >> 1;
             Spinor<R> s;
-            in.load(yh, s);
+            R w = in.load_unscaled(yh, s);
             if (g5in) gamma5(s);
             Half<R> hf, uh;
             project<R>(a, -1, s, hf);
             Link<R> u;
             lk_q.load(yh, a, u);
             mul_link_dag(u, hf, uh);
-            R sc = (a == 3 && x[3] == 0) ? (R)g.bc : (R)1;
+            R sc = (a == 3 && x[3] == 0) ? (R)g.bc * w : w;
             accumulate<R>(a, -1, uh, sc, acc);
         }
     }
 }
 
-template <class R, class SIn, class SX, class SOut, class LK, int MASK, int RED3>
-__global__ void __launch_bounds__(128) hop_eo_kernel(HopArgs<SIn, SX, SOut, LK> A) {
+// Each thread block covers SPT * blockDim.x consecutive entries of the site
+// set (SPT passes of blockDim.x threads; thread block size and SPT are
+// chosen by the autotuner, see dd_autotune).
+template <class R, class SIn, class SX, class SOut, class LK, int MASK, int RED3, int SPT>
+__global__ void __launch_bounds__(sizeof(R) == 4 ? 256 : 128, sizeof(R) == 4 ? 3 : 0)
+    hop_eo_kernel(HopArgs<SIn, SX, SOut, LK> A) {
     __shared__ double sh[34];
     const int rhs = blockIdx.y;
     if (A.st && !A.st[rhs].active) return;
-    const int h = blockIdx.x * blockDim.x + threadIdx.x;
     const long long Vh = A.g.Vh;
-    double v3[3] = {0.0, 0.0, 0.0};
+    const long long tile = (long long)blockDim.x * SPT;
     if (A.sites && threadIdx.x == 0)
-        atomicAdd(A.sites, (unsigned long long)min((long long)blockDim.x, Vh - (long long)blockIdx.x * blockDim.x));
+        atomicAdd(A.sites, (unsigned long long)min(tile, A.S.n - (long long)blockIdx.x * tile));
+    double v3[3] = {0.0, 0.0, 0.0};
     double nrm = 0.0;
-    if (h < A.g.Vh) {
-        SIn in = at_rhs(A.in, rhs);
+#pragma unroll
+    for (int pass = 0; pass < SPT; ++pass) {
+        const long long t = (long long)blockIdx.x * tile + (long long)pass * blockDim.x + threadIdx.x;
+        if (t >= A.S.n) break;
+        const int h = (int)A.S.at(t);
+        const SIn in = at_rhs(A.in, rhs);
         LK lk = A.lk;
         lk.p += (long long)rhs * A.lk_rhs_stride;
-        LK lk_p = link_parity(lk, A.p, Vh);
-        LK lk_q = link_parity(lk, 1 - A.p, Vh);
+        const LK lk_p = link_parity(lk, A.p, Vh);
+        const LK lk_q = link_parity(lk, 1 - A.p, Vh);
         int x[4];
         eo_coords(A.g, A.p, h, x);
         Spinor<R> acc;
@@ -150,8 +159,8 @@ __global__ void __launch_bounds__(128) hop_eo_kernel(HopArgs<SIn, SX, SOut, LK> 
                 d0 += rv.c[k].x * res.c[k].x + rv.c[k].y * res.c[k].y;
                 d1 += rv.c[k].x * res.c[k].y - rv.c[k].y * res.c[k].x;
             }
-            v3[0] = (double)d0;
-            v3[1] = (double)d1;
+            v3[0] += (double)d0;
+            v3[1] += (double)d1;
         } else if (RED3 == 2) {
             R d0 = 0, d1 = 0;
 #pragma unroll
@@ -159,11 +168,11 @@ __global__ void __launch_bounds__(128) hop_eo_kernel(HopArgs<SIn, SX, SOut, LK> 
                 d0 += res.c[k].x * xv.c[k].x + res.c[k].y * xv.c[k].y;
                 d1 += res.c[k].x * xv.c[k].y - res.c[k].y * xv.c[k].x;
             }
-            v3[0] = (double)d0;
-            v3[1] = (double)d1;
-            v3[2] = (double)snorm2(res);
+            v3[0] += (double)d0;
+            v3[1] += (double)d1;
+            v3[2] += (double)snorm2(res);
         } else {
-            nrm = (double)snorm2(res);
+            nrm += (double)snorm2(res);
         }
     }
     if (RED3) {
@@ -184,11 +193,20 @@ constexpr int hop_kind() {
 
 template <class R, class SIn, class SX, class SOut, class LK, int MASK>
 inline void launch_hop(const HopArgs<SIn, SX, SOut, LK>& A, int nrhs, dd_handle* h) {
-    dim3 grid(grid_for(A.g.Vh, 128), nrhs);
+    HopArgs<SIn, SX, SOut, LK> B = A;
+    if (B.S.n < 0) B.S = SiteSet{nullptr, (long long)A.g.Vh};
+    // tile shape from the handle's tuning (threads x sites per thread >= 64,
+    // which keeps the grid within the reduction partials)
+    const bool f64 = std::is_same<R, double>::value;
+    const int tpb = f64 ? h->tune.hop64_tpb : h->tune.hop_tpb;
+    // two sites per thread only for the FP32-arithmetic kernels (the FP64
+    // kernel needs 130-150 registers for one site)
+    constexpr int SPT2 = std::is_same<R, double>::value ? 1 : 2;
+    const int spt = (!f64 && h->tune.hop_spt == 2) ? 2 : 1;
+    dim3 grid(grid_for(B.S.n, (long long)tpb * spt), nrhs);
     constexpr int kind = hop_kind<SIn, SOut>();
     bool timed = false;
-    if (kind >= 0 && MASK == 0 && h->timer_on) timed = (h->timer_seen[kind]++ % h->timer_every) == 0;
-    HopArgs<SIn, SX, SOut, LK> B = A;
+    if (kind >= 0 && MASK == 0 && h->timer_on && !h->capturing && !dd_stream_capturing(h)) timed = (h->timer_seen[kind]++ % h->timer_every) == 0;
     B.sites = nullptr;
     if (timed) {
         cudaEvent_t e = dd_timer_event(h, kind);
@@ -196,11 +214,11 @@ inline void launch_hop(const HopArgs<SIn, SX, SOut, LK>& A, int nrhs, dd_handle*
         B.sites = h->d_sites + kind;
     }
     if (A.red3 == 1)
-        DD_KLAUNCH(h, hop_eo_kernel<R, SIn, SX, SOut, LK, MASK, 1><<<grid, 128, 0, h->stream>>>(B));
+        DD_KLAUNCH(h, (spt == 2 ? hop_eo_kernel<R, SIn, SX, SOut, LK, MASK, 1, SPT2> : hop_eo_kernel<R, SIn, SX, SOut, LK, MASK, 1, 1>)<<<grid, tpb, 0, h->stream>>>(B));
     else if (A.red3 == 2)
-        DD_KLAUNCH(h, hop_eo_kernel<R, SIn, SX, SOut, LK, MASK, 2><<<grid, 128, 0, h->stream>>>(B));
+        DD_KLAUNCH(h, (spt == 2 ? hop_eo_kernel<R, SIn, SX, SOut, LK, MASK, 2, SPT2> : hop_eo_kernel<R, SIn, SX, SOut, LK, MASK, 2, 1>)<<<grid, tpb, 0, h->stream>>>(B));
     else
-        DD_KLAUNCH(h, hop_eo_kernel<R, SIn, SX, SOut, LK, MASK, 0><<<grid, 128, 0, h->stream>>>(B));
+        DD_KLAUNCH(h, (spt == 2 ? hop_eo_kernel<R, SIn, SX, SOut, LK, MASK, 0, SPT2> : hop_eo_kernel<R, SIn, SX, SOut, LK, MASK, 0, 1>)<<<grid, tpb, 0, h->stream>>>(B));
     if (timed) {
         cudaEvent_t e = dd_timer_event(h, kind);
         if (e) cudaEventRecord(e, h->stream);

@@ -40,7 +40,8 @@ DD_DEV void dd_coords(const Geo& g, const BlockCtx& c, long long q, int x[4], in
 
 // eta on the black sites (purpose / sub), 0 on white; block order
 __global__ void noise_black_kernel(Geo g, BlockCtx c, double2* bank, long long vs, int purpose, uint64_t seed,
-                                   uint64_t ctr) {
+                                   uint64_t ctr0, const unsigned long long* ctr_off) {
+    const uint64_t ctr = stream_ctr(ctr0, ctr_off);
     long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int i = blockIdx.y;
     if (q >= g.V) return;
@@ -59,13 +60,14 @@ __global__ void noise_black_kernel(Geo g, BlockCtx c, double2* bank, long long v
 }
 
 // out = -kappa * (hops that cross block faces) in, on the sites of colour
-// `target` (0 elsewhere).  Links from the canonical FP64 copy of the field.
+// `target` (0 elsewhere).  Links from the canonical FP64 copy of the field
+// of slot f0 + i * fstep for right-hand side i.
 __global__ void inter_hop_kernel(Geo g, BlockCtx c, const double2* in_bank, double2* out_bank, long long vs,
-                                 const double* canon0, long long canon_fs, const int* field_of, int target) {
+                                 const double* canon0, long long canon_fs, int f0, int fstep, int target) {
     long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int i = blockIdx.y;
     if (q >= g.V) return;
-    const double* U = canon0 + (long long)field_of[i] * canon_fs;
+    const double* U = canon0 + (long long)(f0 + i * fstep) * canon_fs;
     int x[4], col;
     dd_coords(g, c, q, x, &col);
     long long pos = q / c.nb, j = q % c.nb;
@@ -109,8 +111,8 @@ __global__ void inter_hop_kernel(Geo g, BlockCtx c, const double2* in_bank, doub
 
 // out = v - D_b[field] a on black sites, 0 on white (block order)
 __global__ void schur_source_kernel(Geo g, BlockCtx c, const double2* v_bank, const double2* a_bank,
-                                    double2* out_bank, long long vs, const double2* dd64, long long fs,
-                                    const int* field_of) {
+                                    double2* out_bank, long long vs, const double2* dd64, long long fs, int f0,
+                                    int fstep) {
     long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int i = blockIdx.y;
     if (q >= g.V) return;
@@ -121,7 +123,7 @@ __global__ void schur_source_kernel(Geo g, BlockCtx c, const double2* v_bank, co
     if (pos < g.nblocks / 2) {
         SpinorF64 av{(double2*)a_bank + (long long)i * vs + pos * 12 * c.nb, c.nb};
         SpinorF64 vv{(double2*)v_bank + (long long)i * vs + pos * 12 * c.nb, c.nb};
-        LinkF64 lk{dd64 + (long long)field_of[i] * fs + pos * 4 * 9 * c.nb, c.nb};
+        LinkF64 lk{dd64 + (long long)(f0 + i * fstep) * fs + pos * 4 * 9 * c.nb, c.nb};
         Spinor<double> acc, a;
         dirichlet_hop<double>(c, j, av, lk, 0, acc);
         av.load(j, a);
@@ -174,10 +176,23 @@ __global__ void __launch_bounds__(128) estimate_kernel(Geo g, BlockCtx c, const 
     grid_reduce(red, i, acc, sh);
 }
 
-__global__ void sum_items_kernel(int nblocks, const int* item_base, int n, const double* item_out, double* ln_b) {
+// ln_b[b] = sum of the n item results of block b (0 for blocks without
+// items).  item_base: the first item of every block, or null for the
+// block-filter order (the blocks of colour_mask in block order from
+// position pos0, n consecutive items each)
+__global__ void sum_items_kernel(Geo g, const int* item_base, int colour_mask, int pos0, int n,
+                                 const double* item_out, double* ln_b) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nblocks) return;
-    int base = item_base[b];
+    if (b >= g.nblocks) return;
+    int base;
+    if (item_base) {
+        base = item_base[b];
+    } else {
+        int B[4] = {b % g.nbk[0], (b / g.nbk[0]) % g.nbk[1], (b / (g.nbk[0] * g.nbk[1])) % g.nbk[2],
+                    b / (g.nbk[0] * g.nbk[1] * g.nbk[2])};
+        int col = (B[0] + B[1] + B[2] + B[3]) & 1;
+        base = ((colour_mask >> col) & 1) ? (block_pos_of(g, b, col) - pos0) * n : -1;
+    }
     double s = 0.0;
     if (base >= 0)
         for (int i = 0; i < n; ++i) s += item_out[base + i];
@@ -185,7 +200,7 @@ __global__ void sum_items_kernel(int nblocks, const int* item_base, int n, const
 }
 
 __global__ void block_accept_kernel(Geo g, int colour_mask, const double* ln_b, uint8_t* accept, uint64_t seed,
-                                    uint64_t ctr) {
+                                    uint64_t ctr, const unsigned long long* ctr_off) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= g.nblocks) return;
     int B[4] = {b % g.nbk[0], (b / g.nbk[0]) % g.nbk[1], (b / (g.nbk[0] * g.nbk[1])) % g.nbk[2],
@@ -196,7 +211,7 @@ __global__ void block_accept_kernel(Geo g, int colour_mask, const double* ln_b, 
         return;
     }
     double u1, u2;
-    uniform_pair((uint32_t)b, DD_PURPOSE_BLOCK_ACCEPT, 0u, seed, ctr, u1, u2);
+    uniform_pair((uint32_t)b, DD_PURPOSE_BLOCK_ACCEPT, 0u, seed, stream_ctr(ctr, ctr_off), u1, u2);
     accept[b] = log(u1) < ln_b[b] ? 1 : 0;
 }
 
@@ -212,12 +227,12 @@ __global__ void restore_kernel(Geo g, int n, const int* links, const uint8_t* ac
     for (int e = 0; e < 18; ++e) U_new[(long long)l * 18 + e] = U_old[(long long)l * 18 + e];
 }
 
-__global__ void global_accept_kernel(const double* ln_r, int n, uint64_t seed, uint64_t ctr, uint8_t* accept,
-                                     double* margin) {
+__global__ void global_accept_kernel(const double* ln_r, int n, uint64_t seed, uint64_t ctr,
+                                     const unsigned long long* ctr_off, uint8_t* accept, double* margin) {
     double s = 0.0;
     for (int i = 0; i < n; ++i) s += ln_r[i];
     double u1, u2;
-    uniform_pair(0u, DD_PURPOSE_GLOBAL_ACCEPT, 0u, seed, ctr, u1, u2);
+    uniform_pair(0u, DD_PURPOSE_GLOBAL_ACCEPT, 0u, seed, stream_ctr(ctr, ctr_off), u1, u2);
     double lu = log(u1);
     accept[0] = lu < s ? 1 : 0;
     if (margin) margin[0] = s - lu;
@@ -262,20 +277,21 @@ static int prepare_fields(dd_handle* h, const double* U_old, const double* U_new
     return DD_OK;
 }
 
-static int launch_blocks(dd_handle* h, int mode, const std::vector<BlockItem>& items, const double2* in_bank,
+// block-filter items of the blocks at positions pos0 .. pos0 + nitems / n - 1,
+// n noise vectors each, in one persistent launch
+static int launch_blocks(dd_handle* h, int mode, int pos0, int n, int nitems, const double2* in_bank,
                          double2* out_bank, uint64_t seed, uint64_t ctr) {
-    if (items.empty()) return DD_OK;
-    if ((int)items.size() > h->items_cap) return dd_fail(h, DD_ERR_INVALID_ARG, "too many block items");
-    DD_CUDA(h, cudaMemcpyAsync(h->d_items, items.data(), sizeof(BlockItem) * items.size(), cudaMemcpyHostToDevice,
-                               h->stream));
+    if (nitems <= 0) return DD_OK;
     DD_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream));
     BlockArgs A;
     A.lats = nullptr;
     A.g = h->g;
     A.c = block_ctx(h);
     A.mode = mode;
-    A.items = (const BlockItem*)h->d_items;
-    A.nitems = (int)items.size();
+    A.items = nullptr;
+    A.nitems = nitems;
+    A.item_pos0 = pos0;
+    A.item_n = n;
     A.queue = h->d_queue;
     A.dd64 = h->fields[0].dd64;
     A.dd64_fs = (long long)(h->fields[1].dd64 - h->fields[0].dd64);
@@ -289,6 +305,7 @@ static int launch_blocks(dd_handle* h, int mode, const std::vector<BlockItem>& i
     A.slot_bytes = (long long)h->block_slot_bytes;
     A.seed = seed;
     A.ctr = ctr;
+    A.ctr_off = h->d_ctr_off;
     A.purpose = DD_PURPOSE_BLOCK_NOISE;
     A.tol2 = h->prm.tol_block * h->prm.tol_block;
     A.inner_f64 = h->prm.block_prec == DD_PREC_F64;
@@ -296,12 +313,42 @@ static int launch_blocks(dd_handle* h, int mode, const std::vector<BlockItem>& i
     A.maxit_inner = std::min(h->prm.maxit, 2000);
     A.max_outer = A.inner_f64 ? 3 : 12;
     A.status = h->d_status;
-    int grid = std::min((int)items.size(), h->block_slots);
+    const int grid = std::min(nitems, std::min(h->block_slots, std::max(1, h->num_sms) * h->tune.block_ctas_per_sm));
+    const int tpb = h->tune.block_tpb;
     if (A.inner_f64)
-        DD_KLAUNCH(h, block_solve_kernel<double, SpinorF64, LinkF64><<<grid, 256, 0, h->stream>>>(A));
+        DD_KLAUNCH(h, block_solve_kernel<double, SpinorF64, LinkF64><<<grid, tpb, 0, h->stream>>>(A));
     else
-        DD_KLAUNCH(h, block_solve_kernel<float, SpinorF32, LinkF32><<<grid, 256, 0, h->stream>>>(A));
+        DD_KLAUNCH(h, block_solve_kernel<float, SpinorF32, LinkF32><<<grid, tpb, 0, h->stream>>>(A));
     DD_LAUNCH_CHECK(h, "block_solve_kernel");
+    return DD_OK;
+}
+
+// autotuner probe: one block-filter pass (one noise vector per block, every
+// block) on the fields of (U_old, U_new) with the handle's current launch
+// shape; *ms = average duration of the persistent launch over reps
+int tune_block_filter(dd_handle* h, const double* U_old, const double* U_new, int reps, float* ms) {
+    int rc = prepare_fields(h, U_old, U_new, 1, true, false);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    DD_CUDA(h, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return dd_fail(h, DD_ERR_CUDA, "cudaEventCreate");
+    }
+    rc = launch_blocks(h, BLOCK_FILTER, 0, 1, h->g.nblocks, nullptr, nullptr, 1, 0);
+    cudaEventRecord(e0, h->stream);
+    for (int r = 0; r < reps && !rc; ++r) rc = launch_blocks(h, BLOCK_FILTER, 0, 1, h->g.nblocks, nullptr, nullptr, 1, 0);
+    cudaEventRecord(e1, h->stream);
+    float t = -1.f;
+    if (!rc && cudaEventSynchronize(e1) == cudaSuccess) {
+        cudaEventElapsedTime(&t, e0, e1);
+        t /= (float)reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (t < 0) return dd_fail(h, DD_ERR_CUDA, "block-filter timing failed");
+    *ms = t;
     return DD_OK;
 }
 
@@ -310,9 +357,10 @@ static void raise_status_host(dd_handle* h, int code) {
     DD_KLAUNCH(h, set_status_kernel<<<1, 1, 0, h->stream>>>(h->d_status, code));
 }
 
-// eo FP64 chunks of the global solver -> block order (FP64)
+// eo FP64 chunks of the global solver -> block order (FP64); sites of
+// blocks whose colour is not in colour_mask are written as zero
 __global__ void eo_to_dd_kernel(Geo g, BlockCtx c, const double2* xe, const double2* xo, double2* bank,
-                                long long vs) {
+                                long long vs, int colour_mask) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     int i = blockIdx.y;
     if (s >= g.V) return;
@@ -322,17 +370,22 @@ __global__ void eo_to_dd_kernel(Geo g, BlockCtx c, const double2* xe, const doub
     const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
     SpinorF64 src{(double2*)(par ? xo : xe) + (long long)i * 12 * g.Vh, g.Vh};
     Spinor<double> v;
-    src.load(s >> 1, v);
+    if ((colour_mask >> block_colour_of(g, x)) & 1)
+        src.load(s >> 1, v);
+    else
+        zero(v);
     SpinorF64 dst{bank + (long long)i * vs + (q / c.nb) * 12 * c.nb, c.nb};
     dst.store(q % c.nb, v);
 }
 
 // out_bank[i] = (D_bb + D_ww)^{-1} in_bank[i] for i < n, with the gauge field
 // of slot field0 + i * step: every Dirichlet block solve of every factor in
-// one batched even-odd CG (inner precision of the handle, FP64 defect
-// correction to tol_block relative to the whole right-hand side).
+// one batched even-odd Krylov solve (inner precision of the handle, FP64
+// defect correction to tol_block relative to the whole right-hand side).
+// The right-hand sides live on the blocks of one colour (0 black, 1 white);
+// only that colour's sites are visited, the other colour of out_bank is 0.
 static int dirichlet_solve_bank(dd_handle* h, const double2* in_bank, double2* out_bank, int n, int field0,
-                                int step) {
+                                int step, int colour) {
     const Geo& g = h->g;
     const BlockCtx c = block_ctx(h);
     const long long vs = 12LL * g.V;
@@ -341,10 +394,11 @@ static int dirichlet_solve_bank(dd_handle* h, const double2* in_bank, double2* o
     DD_KLAUNCH(h, dd_to_eo_kernel<<<gv, 128, 0, h->stream>>>(g, c, in_bank, vs, v.be, v.bo));
     DD_LAUNCH_CHECK(h, "dd_to_eo_kernel");
     int it = 0;
-    int rc = solve_packed(h, n, field0, step, h->prm.inner_prec, h->prm.tol_block, h->prm.maxit, &it, nullptr, 1);
+    int rc = solve_packed(h, n, field0, step, h->prm.inner_prec, h->prm.tol_block, h->prm.maxit, &it, nullptr, 1,
+                          colour);
     if (rc && rc != DD_ERR_NOT_CONVERGED) return dd_fail(h, rc, "Dirichlet block solves failed");
     if (rc == DD_ERR_NOT_CONVERGED) raise_status_host(h, DD_ERR_NOT_CONVERGED);
-    DD_KLAUNCH(h, eo_to_dd_kernel<<<gv, 128, 0, h->stream>>>(g, c, v.xe, v.xo, out_bank, vs));
+    DD_KLAUNCH(h, eo_to_dd_kernel<<<gv, 128, 0, h->stream>>>(g, c, v.xe, v.xo, out_bank, vs, 1 << colour));
     DD_LAUNCH_CHECK(h, "eo_to_dd_kernel");
     return DD_OK;
 }
@@ -365,37 +419,21 @@ extern "C" int dd_block_filter(dd_t h, const void* U_old, void* U_new, int colou
         rc = prepare_fields(h, (const double*)U_old, (const double*)U_new, n, true, false);
         if (rc) return rc;
         const Geo& g = h->g;
-        std::vector<BlockItem> items;
-        std::vector<int> base(g.nblocks, -1);
+        // the blocks of the selected colours are contiguous in block order
+        // (black first); n consecutive items per block
         const int half = g.nblocks / 2;
-        // items of a block are consecutive; block ids from positions
-        std::vector<int> id_at(g.nblocks);
-        {
-            // host mirror of block_id_at
-            for (int pos = 0; pos < g.nblocks; ++pos) {
-                int col = pos >= half ? 1 : 0, rank = pos - col * half, id = 2 * rank;
-                int B1 = (id / g.nbk[0]) % g.nbk[1], B2 = (id / (g.nbk[0] * g.nbk[1])) % g.nbk[2],
-                    B3 = id / (g.nbk[0] * g.nbk[1] * g.nbk[2]);
-                if (((B1 + B2 + B3) & 1) != col) id += 1;
-                id_at[pos] = id;
-            }
-        }
-        for (int pos = 0; pos < g.nblocks; ++pos) {
-            int col = pos >= half ? 1 : 0;
-            if (!((colour_mask >> col) & 1)) continue;
-            base[id_at[pos]] = (int)items.size();
-            for (int i = 0; i < n; ++i) items.push_back(BlockItem{pos, i, i + 1, i, 0});
-        }
-        rc = launch_blocks(h, BLOCK_FILTER, items, nullptr, nullptr, seed, ctr);
+        const int pos0 = colour_mask == 2 ? half : 0;
+        const int nb = colour_mask == 3 ? g.nblocks : half;
+        rc = launch_blocks(h, BLOCK_FILTER, pos0, n, nb * n, nullptr, nullptr, seed, ctr);
         if (rc) return rc;
-        int* d_base = h->d_imap;
-        DD_CUDA(h, cudaMemcpyAsync(d_base, base.data(), sizeof(int) * g.nblocks, cudaMemcpyHostToDevice, h->stream));
-        DD_KLAUNCH(h, sum_items_kernel<<<grid_for(g.nblocks, 128), 128, 0, h->stream>>>(g.nblocks, d_base, n, h->d_item_out, ln_b));
+        DD_KLAUNCH(h, sum_items_kernel<<<grid_for(g.nblocks, 128), 128, 0, h->stream>>>(g, nullptr, colour_mask, pos0, n,
+                                                                                       h->d_item_out, ln_b));
         DD_LAUNCH_CHECK(h, "sum_items_kernel");
     } else {
         return dd_fail(h, DD_ERR_INVALID_ARG, "dd_block_filter: unknown mode");
     }
-    DD_KLAUNCH(h, block_accept_kernel<<<grid_for(h->g.nblocks, 128), 128, 0, h->stream>>>(h->g, colour_mask, ln_b, accept, seed, ctr));
+    DD_KLAUNCH(h, block_accept_kernel<<<grid_for(h->g.nblocks, 128), 128, 0, h->stream>>>(h->g, colour_mask, ln_b, accept, seed,
+                                                                                         ctr, h->d_ctr_off));
     if (h->n_active > 0)
         DD_KLAUNCH(h, restore_kernel<<<grid_for(h->n_active, 128), 128, 0, h->stream>>>(h->g, h->n_active, h->d_active_links, accept,
                                                                         (const double*)U_old, (double*)U_new));
@@ -421,7 +459,7 @@ BatchPlan batch_plan(int nh, dd_handle* const* hs, int n) {
     }
     p.nitems = nitems;
     p.slot_bytes = (long long)((((size_t)nbmax * (4 * 192 + 5 * 192)) + 4096 + 255) & ~(size_t)255);
-    p.slots = std::max(1, hs[0]->num_sms) * 2;
+    p.slots = std::max(1, hs[0]->num_sms) * hs[0]->tune.block_ctas_per_sm;
     size_t off = 0;
     p.lats = off;
     off = align256(off + sizeof(LatDesc) * nh);
@@ -529,10 +567,12 @@ extern "C" int dd_block_filter_batch(int nh, const dd_t* hs_, const void* const*
         off += hs[k]->g.nblocks;
     }
     cudaStream_t s = h0->stream;
-    DD_CUDA(h0, cudaMemcpyAsync(d_lats, lats.data(), sizeof(LatDesc) * nh, cudaMemcpyHostToDevice, s));
-    if (!items.empty())
-        DD_CUDA(h0, cudaMemcpyAsync(d_items, items.data(), sizeof(BlockItem) * items.size(), cudaMemcpyHostToDevice, s));
-    DD_CUDA(h0, cudaMemcpyAsync(d_bases, bases.data(), sizeof(int) * bases.size(), cudaMemcpyHostToDevice, s));
+    // descriptor tables (skipped when the workspace already holds them, as
+    // it must inside a graph capture)
+    rc = upload_cached(h0, 0, d_lats, lats.data(), sizeof(LatDesc) * nh);
+    if (!rc && !items.empty()) rc = upload_cached(h0, 1, d_items, items.data(), sizeof(BlockItem) * items.size());
+    if (!rc) rc = upload_cached(h0, 2, d_bases, bases.data(), sizeof(int) * bases.size());
+    if (rc) return rc;
     DD_CUDA(h0, cudaMemsetAsync(d_queue, 0, sizeof(int), s));
     if (!items.empty()) {
         BlockArgs A;
@@ -542,6 +582,8 @@ extern "C" int dd_block_filter_batch(int nh, const dd_t* hs_, const void* const*
         A.mode = BLOCK_FILTER;
         A.items = d_items;
         A.nitems = (int)items.size();
+        A.item_pos0 = 0;
+        A.item_n = n;
         A.queue = d_queue;
         A.dd64 = h0->fields[0].dd64;
         A.dd64_fs = 0;
@@ -555,6 +597,7 @@ extern "C" int dd_block_filter_batch(int nh, const dd_t* hs_, const void* const*
         A.slot_bytes = P.slot_bytes;
         A.seed = seed;
         A.ctr = ctr;
+        A.ctr_off = h0->d_ctr_off;
         A.purpose = DD_PURPOSE_BLOCK_NOISE;
         A.tol2 = h0->prm.tol_block * h0->prm.tol_block;
         A.inner_f64 = h0->prm.block_prec == DD_PREC_F64;
@@ -563,18 +606,20 @@ extern "C" int dd_block_filter_batch(int nh, const dd_t* hs_, const void* const*
         A.max_outer = A.inner_f64 ? 3 : 12;
         A.status = h0->d_status;
         const int grid = std::min((int)items.size(), P.slots);
+        const int tpb = h0->tune.block_tpb;
         if (A.inner_f64)
-            DD_KLAUNCH(h0, block_solve_kernel<double, SpinorF64, LinkF64><<<grid, 256, 0, s>>>(A));
+            DD_KLAUNCH(h0, block_solve_kernel<double, SpinorF64, LinkF64><<<grid, tpb, 0, s>>>(A));
         else
-            DD_KLAUNCH(h0, block_solve_kernel<float, SpinorF32, LinkF32><<<grid, 256, 0, s>>>(A));
+            DD_KLAUNCH(h0, block_solve_kernel<float, SpinorF32, LinkF32><<<grid, tpb, 0, s>>>(A));
         DD_LAUNCH_CHECK(h0, "block_solve_kernel (batch)");
     }
     for (int k = 0; k < nh; ++k) {
         dd_handle* h = hs[k];
-        DD_KLAUNCH(h, sum_items_kernel<<<grid_for(h->g.nblocks, 128), 128, 0, s>>>(h->g.nblocks, d_bases + base_off[k],
-                                                                                 n, d_out, ln_b[k]));
+        DD_KLAUNCH(h, sum_items_kernel<<<grid_for(h->g.nblocks, 128), 128, 0, s>>>(h->g, d_bases + base_off[k],
+                                                                                 colour_mask, 0, n, d_out, ln_b[k]));
         DD_KLAUNCH(h, block_accept_kernel<<<grid_for(h->g.nblocks, 128), 128, 0, s>>>(h->g, colour_mask, ln_b[k],
-                                                                                    accept[k], seed, ctr));
+                                                                                    accept[k], seed, ctr,
+                                                                                    h0->d_ctr_off));
         if (h->n_active > 0)
             DD_KLAUNCH(h, restore_kernel<<<grid_for(h->n_active, 128), 128, 0, s>>>(
                               h->g, h->n_active, h->d_active_links, accept[k], (const double*)U_old[k],
@@ -601,46 +646,39 @@ extern "C" int dd_det_ratio_estimate(dd_t h, const void* U_old, const void* U_ne
     const long long vs = 12LL * g.V;
     double2* bank[6];
     for (int k = 0; k < 6; ++k) bank[k] = h->dd_vec + (long long)k * R * vs;
-    // field slot of the old / new operator of every factor
-    std::vector<int> f_old(n), f_new(n);
-    for (int i = 0; i < n; ++i) {
-        f_old[i] = factors ? i : 0;
-        f_new[i] = factors ? i + 1 : 1;
-    }
-    int* d_fold = h->d_imap + g.nblocks;
-    int* d_fnew = d_fold + 2 * R;
-    DD_CUDA(h, cudaMemcpyAsync(d_fold, f_old.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
-    DD_CUDA(h, cudaMemcpyAsync(d_fnew, f_new.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+    // field slot of the old / new operator of factor i: fs * i + {0, 1}
+    const int fs = factors ? 1 : 0;
     const long long canon_fs = (long long)(h->fields[1].canon - h->fields[0].canon) * 2;  // doubles
     const long long dd64_fs = (long long)(h->fields[1].dd64 - h->fields[0].dd64);
     dim3 gv(grid_for(g.V, 128), n);
     // 1. eta on black sites
-    DD_KLAUNCH(h, noise_black_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], vs, DD_PURPOSE_GLOBAL_NOISE, seed, ctr));
+    DD_KLAUNCH(h, noise_black_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], vs, DD_PURPOSE_GLOBAL_NOISE, seed, ctr,
+                                                               h->d_ctr_off));
     // 2. w = C eta, w' = C' eta (onto white sites)
-    DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], bank[1], vs, (const double*)h->fields[0].canon, canon_fs, d_fold, 1));
-    DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], bank[2], vs, (const double*)h->fields[0].canon, canon_fs, d_fnew, 1));
+    DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], bank[1], vs, (const double*)h->fields[0].canon, canon_fs, 0, fs, 1));
+    DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], bank[2], vs, (const double*)h->fields[0].canon, canon_fs, 1, fs, 1));
     DD_LAUNCH_CHECK(h, "schur stage 1-2");
     // 3. z = E^{-1} w, z' = E'^{-1} w': all white-block solves of all factors
     //    as one batched even-odd CG on the Dirichlet operator
-    rc = dirichlet_solve_bank(h, bank[1], bank[3], n, 0, factors ? 1 : 0);
+    rc = dirichlet_solve_bank(h, bank[1], bank[3], n, 0, fs, 1);
     if (rc) return rc;
-    rc = dirichlet_solve_bank(h, bank[2], bank[4], n, 1, factors ? 1 : 0);
+    rc = dirichlet_solve_bank(h, bank[2], bank[4], n, 1, fs, 1);
     if (rc) return rc;
     // 4. v = B z, v' = B' z' (onto black sites)
-    DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[3], bank[1], vs, (const double*)h->fields[0].canon, canon_fs, d_fold, 0));
-    DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[4], bank[2], vs, (const double*)h->fields[0].canon, canon_fs, d_fnew, 0));
+    DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[3], bank[1], vs, (const double*)h->fields[0].canon, canon_fs, 0, fs, 0));
+    DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[4], bank[2], vs, (const double*)h->fields[0].canon, canon_fs, 1, fs, 0));
     DD_LAUNCH_CHECK(h, "schur stage 4");
     // 5. a = A^{-1} v (black-block solves)
-    rc = dirichlet_solve_bank(h, bank[1], bank[5], n, 0, factors ? 1 : 0);
+    rc = dirichlet_solve_bank(h, bank[1], bank[5], n, 0, fs, 0);
     if (rc) return rc;
     // 6. s = v' - A' a  -> bank 3
-    DD_KLAUNCH(h, schur_source_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[2], bank[5], bank[3], vs, h->fields[0].dd64, dd64_fs, d_fnew));
+    DD_KLAUNCH(h, schur_source_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[2], bank[5], bank[3], vs, h->fields[0].dd64, dd64_fs, 1, fs));
     // 7. global solve D' y = (s, 0)
     SolverVecs& v = h->vecs[0];
     DD_KLAUNCH(h, dd_to_eo_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[3], vs, v.be, v.bo));
     DD_LAUNCH_CHECK(h, "schur stage 6-7");
     int iters = 0;
-    rc = solve_packed(h, n, f_new[0], factors ? 1 : 0, h->prm.inner_prec, h->prm.tol_global, h->prm.maxit, &iters,
+    rc = solve_packed(h, n, 1, fs, h->prm.inner_prec, h->prm.tol_global, h->prm.maxit, &iters,
                       nullptr);
     if (rc && rc != DD_ERR_NOT_CONVERGED) return dd_fail(h, rc, "dd_det_ratio_estimate: global solve failed");
     // 8. ln r_i
@@ -663,7 +701,7 @@ extern "C" int dd_global_accept(dd_t h, void* U, const void* U_old, const double
     int rc = dd_require_ws(h);
     if (rc) return rc;
     if (!U || !U_old || !ln_r || !accept || n < 1) return dd_fail(h, DD_ERR_INVALID_ARG, "dd_global_accept: bad arguments");
-    DD_KLAUNCH(h, global_accept_kernel<<<1, 1, 0, h->stream>>>(ln_r, n, seed, ctr, accept, ln_margin));
+    DD_KLAUNCH(h, global_accept_kernel<<<1, 1, 0, h->stream>>>(ln_r, n, seed, ctr, h->d_ctr_off, accept, ln_margin));
     const long long m = (long long)h->g.V * 72;
     DD_KLAUNCH(h, conditional_copy_kernel<<<grid_for(m, 256), 256, 0, h->stream>>>(m, accept, (const double*)U_old, (double*)U));
     DD_LAUNCH_CHECK(h, "global accept");

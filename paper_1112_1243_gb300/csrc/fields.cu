@@ -7,7 +7,9 @@
 #include "su3.cuh"
 
 // ------------------------------------------------------------------- noise
-__global__ void noise_kernel(long long V, double* out, int purpose, uint64_t seed, uint64_t ctr) {
+__global__ void noise_kernel(long long V, double* out, int purpose, uint64_t seed, uint64_t ctr0,
+                             const unsigned long long* ctr_off) {
+    const uint64_t ctr = stream_ctr(ctr0, ctr_off);
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // element = s*12 + k
     int r = blockIdx.y;
     if (e >= V * 12) return;
@@ -23,7 +25,7 @@ extern "C" int dd_noise(dd_t h, void* eta, int nrhs, int purpose, uint64_t seed,
     if (!eta || nrhs < 1 || purpose < 0 || purpose > 255) return dd_fail(h, DD_ERR_INVALID_ARG, "dd_noise: bad arguments");
     const long long n = (long long)h->g.V * 12;
     dim3 grid(grid_for(n, 256), nrhs);
-    DD_KLAUNCH(h, noise_kernel<<<grid, 256, 0, h->stream>>>(h->g.V, (double*)eta, purpose, seed, ctr));
+    DD_KLAUNCH(h, noise_kernel<<<grid, 256, 0, h->stream>>>(h->g.V, (double*)eta, purpose, seed, ctr, h->d_ctr_off));
     DD_LAUNCH_CHECK(h, "noise_kernel");
     return DD_OK;
 }

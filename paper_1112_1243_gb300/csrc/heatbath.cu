@@ -49,9 +49,11 @@ DD_DEV M2 dag2(const M2& a) {
 DD_DEV M3 link_at(const double* U, long long s, int a) { return load_m3(U + (s * 4 + a) * 18); }
 
 __global__ void heatbath_kernel(Geo g, double* U, const int* links, int n, double beta, int overrelax, int sweep,
-                                uint64_t seed, uint64_t ctr, unsigned long long* fails) {
+                                uint64_t seed, uint64_t ctr0, const unsigned long long* ctr_off,
+                                unsigned long long* fails) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
+    const uint64_t ctr = stream_ctr(ctr0, ctr_off);
     const int l = links[k];
     const int s = l >> 2, a = l & 3;
     int x[4];
@@ -147,7 +149,7 @@ extern "C" int dd_gauge_update(dd_t h, void* U, int colour_mask, double beta, in
                         if (cnt <= 0) continue;
                         DD_KLAUNCH(h, heatbath_kernel<<<grid_for(cnt, 64), 64, 0, h->stream>>>(
                             h->g, (double*)U, h->d_active_links + off, cnt, beta, kind > 0, sweep, seed, ctr,
-                            h->d_hb_fails));
+                            h->d_ctr_off, h->d_hb_fails));
                     }
     DD_LAUNCH_CHECK(h, "heatbath_kernel");
     return DD_OK;

@@ -380,7 +380,8 @@ void plan(dd_handle* h, char* base) {
     // block-ordered FP64 vectors: 6 banks of R vectors (estimator)
     h->dd_vec = c.take<double2>(est ? (size_t)6 * R * 12 * V : 0);
     h->d_cg = c.take<CGState>((size_t)2 * R + 2);
-    h->partials_cap = (size_t)(grid_for(std::max(Vh, V), 128) + 64) * (R + 1) * 2;
+    // partials of grid reductions with tiles of 64 sites or more (3 values per tile)
+    h->partials_cap = (size_t)(grid_for(std::max(Vh, V), 64) + 64) * (R + 1) * 2;
     h->d_partials = c.take<double>(h->partials_cap);
     h->d_counters = c.take<unsigned>((size_t)4 * (R + 1) + 64);
     h->d_scalars = c.take<double>((size_t)64 * (R + 2));
@@ -388,7 +389,7 @@ void plan(dd_handle* h, char* base) {
     const long long nb = h->g.bsites;
     // 4 FP64 vectors + 5 inner vectors (FP64 at most) of one block
     h->block_slot_bytes = ((size_t)nb * (4 * 192 + 5 * 192) + 4096 + 255) & ~(size_t)255;
-    h->block_slots = std::max(1, h->num_sms) * 2;
+    h->block_slots = std::max(1, h->num_sms) * DD_BLOCK_CTAS_MAX;
     h->block_scratch = c.take<char>(est ? h->block_slot_bytes * h->block_slots : 0);
     h->items_cap = h->g.nblocks * 2 * R + 64;
     h->d_items = c.take<int>((size_t)5 * h->items_cap);  // five ints per item
@@ -514,12 +515,39 @@ extern "C" int dd_init(dd_t* out, const dd_params* p, void* stream) {
     if (e == cudaSuccess) e = cudaMemset(h->d_hb_fails, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_sites, 3 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(h->d_sites, 0, 3 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_ctr_off, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(h->d_ctr_off, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_loop, sizeof(int) * DD_LOOP_SLOTS);
+    if (e == cudaSuccess) e = cudaMemset(h->d_loop, 0, sizeof(int) * DD_LOOP_SLOTS);
+    // sites of each block colour by even-odd index: with an even block
+    // extent along axis 0, x0 = 2 hx and 2 hx + 1 lie in one block, so the
+    // list is the same for both site parities
+    if (e == cudaSuccess && (g.b[0] & 1) == 0) {
+        std::vector<int> cs[2];
+        for (int hh = 0; hh < g.Vh; ++hh) {
+            int hx = hh % g.Lh0, r = hh / g.Lh0;
+            int x1 = r % g.L[1], x2 = (r / g.L[1]) % g.L[2], x3 = r / (g.L[1] * g.L[2]);
+            int x0 = 2 * hx + ((x1 + x2 + x3) & 1);
+            int col = (x0 / g.b[0] + x1 / g.b[1] + x2 / g.b[2] + x3 / g.b[3]) & 1;
+            cs[col].push_back(hh);
+        }
+        for (int col = 0; col < 2 && e == cudaSuccess; ++col) {
+            e = cudaMalloc(&h->d_colour_sites[col], sizeof(int) * std::max<size_t>(1, cs[col].size()));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(h->d_colour_sites[col], cs[col].data(), sizeof(int) * cs[col].size(),
+                               cudaMemcpyHostToDevice);
+        }
+    }
     if (e != cudaSuccess) {
         cudaFree(h->d_active_links);
         cudaFree(h->d_active_mask);
         cudaFree(h->d_status);
         cudaFree(h->d_hb_fails);
         cudaFree(h->d_sites);
+        cudaFree(h->d_ctr_off);
+        cudaFree(h->d_loop);
+        cudaFree(h->d_colour_sites[0]);
+        cudaFree(h->d_colour_sites[1]);
         delete h;
         return DD_ERR_CUDA;
     }
@@ -654,6 +682,12 @@ extern "C" int dd_finalize(dd_t h) {
     cudaFree(h->d_status);
     cudaFree(h->d_hb_fails);
     cudaFree(h->d_sites);
+    cudaFree(h->d_ctr_off);
+    cudaFree(h->d_loop);
+    cudaFree(h->d_colour_sites[0]);
+    cudaFree(h->d_colour_sites[1]);
+    for (cudaStream_t st : h->body_streams) cudaStreamDestroy(st);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
     return DD_OK;
 }

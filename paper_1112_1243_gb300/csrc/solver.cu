@@ -24,15 +24,16 @@ namespace {
 
 // ------------------------------------------------------------- BLAS kernels
 template <class R, class SM, class SH>
-__global__ void __launch_bounds__(128) cg_xr_kernel(long long n, SM x, SM r, SM p, SM q, SH rh, int copy,
+__global__ void __launch_bounds__(128) cg_xr_kernel(SiteSet S, SM x, SM r, SM p, SM q, SH rh, int copy,
                                                     const CGState* st, Reduce red) {
     __shared__ double sh[34];
     const int rhs = blockIdx.y;
     if (!st[rhs].active) return;
     const R alpha = (R)st[rhs].alpha;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double nrm = 0.0;
-    if (i < n) {
+    if (ti < S.n) {
+        const long long i = S.at(ti);
         SM xr = at_rhs(x, rhs), rr = at_rhs(r, rhs), pr = at_rhs(p, rhs), qr = at_rhs(q, rhs);
         Spinor<R> a, b;
         xr.load(i, a);
@@ -52,12 +53,13 @@ __global__ void __launch_bounds__(128) cg_xr_kernel(long long n, SM x, SM r, SM 
 }
 
 template <class R, class SM, class SH>
-__global__ void __launch_bounds__(128) cg_p_kernel(long long n, SM p, SM z, SH ph, int copy, const CGState* st) {
+__global__ void __launch_bounds__(128) cg_p_kernel(SiteSet S, SM p, SM z, SH ph, int copy, const CGState* st) {
     const int rhs = blockIdx.y;
     if (!st[rhs].active) return;
     const double beta = st[rhs].beta;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ti >= S.n) return;
+    const long long i = S.at(ti);
     SM pr = at_rhs(p, rhs), zr = at_rhs(z, rhs);
     Spinor<R> a, b;
     zr.load(i, a);
@@ -73,11 +75,12 @@ __global__ void __launch_bounds__(128) cg_p_kernel(long long n, SM p, SM z, SH p
 
 // start an inner solve: x = 0, r = r0 (copied into the hop copy), states armed
 template <class R, class SM, class SH>
-__global__ void cg_start_kernel(long long n, SM x, SM r, SH rh, int copy, CGState* st, const CGState* outer) {
+__global__ void cg_start_kernel(SiteSet S, SM x, SM r, SH rh, int copy, CGState* st, const CGState* outer) {
     const int rhs = blockIdx.y;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (outer && !outer[rhs].active) return;
-    if (i < n) {
+    if (ti < S.n) {
+        const long long i = S.at(ti);
         Spinor<R> z;
         zero(z);
         at_rhs(x, rhs).store(i, z);
@@ -129,11 +132,12 @@ __global__ void outer_arm_kernel(int nrhs, CGState* outer, const double* bb, dou
 // x64 += scale * e (any storage; scale = |r_outer| when the inner system was
 // normalised, rr = null: 1), r64 = b - t (with |r|^2), v = 0, copies
 template <class SE>
-__global__ void add_correction_kernel(long long n, SpinorF64 x, SE e, const double* rr, const CGState* outer) {
+__global__ void add_correction_kernel(SiteSet S, SpinorF64 x, SE e, const double* rr, const CGState* outer) {
     const int rhs = blockIdx.y;
     if (outer && !outer[rhs].active) return;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ti >= S.n) return;
+    const long long i = S.at(ti);
     const double sc = rr ? sqrt(rr[rhs]) : 1.0;
     Spinor<double> a, b;
     at_rhs(x, rhs).load(i, a);
@@ -145,11 +149,12 @@ __global__ void add_correction_kernel(long long n, SpinorF64 x, SE e, const doub
 // out = in / |in| (|in|^2 given per rhs): the inner solver always sees a
 // unit-norm right-hand side, so FP32 squares neither underflow nor overflow
 template <class SOut>
-__global__ void normalised_copy_kernel(long long n, SpinorF64 in, SOut out, const double* rr, const CGState* outer) {
+__global__ void normalised_copy_kernel(SiteSet S, SpinorF64 in, SOut out, const double* rr, const CGState* outer) {
     const int rhs = blockIdx.y;
     if (outer && !outer[rhs].active) return;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ti >= S.n) return;
+    const long long i = S.at(ti);
     const double inv = rr[rhs] > 0.0 ? 1.0 / sqrt(rr[rhs]) : 0.0;
     Spinor<double> a;
     at_rhs(in, rhs).load(i, a);
@@ -161,14 +166,15 @@ __global__ void fill_kernel(int n, double* p, double v) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
 }
-__global__ void __launch_bounds__(128) residual_kernel(long long n, SpinorF64 b, SpinorF64 t, SpinorF64 r,
+__global__ void __launch_bounds__(128) residual_kernel(SiteSet S, SpinorF64 b, SpinorF64 t, SpinorF64 r,
                                                        const CGState* outer, Reduce red) {
     __shared__ double sh[34];
     const int rhs = blockIdx.y;
     if (outer && !outer[rhs].active) return;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double nrm = 0.0;
-    if (i < n) {
+    if (ti < S.n) {
+        const long long i = S.at(ti);
         Spinor<double> a, c;
         at_rhs(b, rhs).load(i, a);
         at_rhs(t, rhs).load(i, c);
@@ -179,13 +185,14 @@ __global__ void __launch_bounds__(128) residual_kernel(long long n, SpinorF64 b,
     }
     grid_reduce(red, rhs, nrm, sh);
 }
-template <class S>
-__global__ void __launch_bounds__(128) norm2_kernel(long long n, S v, Reduce red) {
+template <class SV>
+__global__ void __launch_bounds__(128) norm2_kernel(SiteSet S, SV v, Reduce red) {
     __shared__ double sh[34];
     const int rhs = blockIdx.y;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double nrm = 0.0;
-    if (i < n) {
+    if (ti < S.n) {
+        const long long i = S.at(ti);
         Spinor<double> a;
         at_rhs(v, rhs).load(i, a);
         nrm = snorm2(a);
@@ -193,19 +200,21 @@ __global__ void __launch_bounds__(128) norm2_kernel(long long n, S v, Reduce red
     grid_reduce(red, rhs, nrm, sh);
 }
 template <class SIn, class SOut>
-__global__ void copy_kernel(long long n, SIn in, SOut out, const CGState* outer) {
+__global__ void copy_kernel(SiteSet S, SIn in, SOut out, const CGState* outer) {
     const int rhs = blockIdx.y;
     if (outer && !outer[rhs].active) return;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ti >= S.n) return;
+    const long long i = S.at(ti);
     Spinor<double> a;
     at_rhs(in, rhs).load(i, a);
     at_rhs(out, rhs).store(i, a);
 }
-__global__ void zero64_kernel(long long n, SpinorF64 v) {
+__global__ void zero64_kernel(SiteSet S, SpinorF64 v) {
     const int rhs = blockIdx.y;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ti >= S.n) return;
+    const long long i = S.at(ti);
     Spinor<double> z;
     zero(z);
     at_rhs(v, rhs).store(i, z);
@@ -223,6 +232,7 @@ struct NormalCG {
     long long lk_rs;
     CGState* st;
     const CGState* outer;
+    SiteSet S;  // the sites of the solve (all even sites, or one block colour's)
 
     Reduce red(int op) const {
         Reduce R_;
@@ -253,6 +263,7 @@ struct NormalCG {
         A.colour_mask = 3;
         A.st = st;
         A.red = red(op);
+        A.S = S;
         return A;
     }
     // z = Dtilde^dag r  (two hops), |z|^2 -> op
@@ -269,32 +280,40 @@ struct NormalCG {
     }
     // solve Dtilde x = r (r holds the right-hand side; x starts at 0)
     int run(const double* rr0, double tol, double abs_fac, int maxit, int chunk, int* iters_out) {
-        const long long n = h->g.Vh;
-        dim3 grid(grid_for(n, 128), nrhs);
+        dim3 grid(grid_for(S.n, 128), nrhs);
         if (maxit < 1) maxit = 1;
         DD_KLAUNCH(h, cg_arm_kernel<<<1, 64, 0, h->stream>>>(nrhs, st, outer, rr0, tol, abs_fac, maxit));
-        DD_KLAUNCH(h, cg_start_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(n, x, r, rh, copies, st, outer));
+        DD_KLAUNCH(h, cg_start_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(S, x, r, rh, copies, st, outer));
         apply_dag_r(FIN_ZZ_INIT);
-        DD_KLAUNCH(h, cg_p_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(n, p, z, ph, copies, st));
+        DD_KLAUNCH(h, cg_p_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(S, p, z, ph, copies, st));
         std::vector<CGState> hs(nrhs);
         int done_iters = 0;
-        for (;;) {
+        bool polled = false;
+        auto body = [&]() -> int {
             for (int it = 0; it < chunk; ++it) {
                 apply_p();
-                DD_KLAUNCH(h, cg_xr_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(n, x, r, p, q, rh, copies, st, red(FIN_RR)));
+                DD_KLAUNCH(h, cg_xr_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(S, x, r, p, q, rh, copies, st, red(FIN_RR)));
                 apply_dag_r(FIN_BETA);
-                DD_KLAUNCH(h, cg_p_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(n, p, z, ph, copies, st));
+                DD_KLAUNCH(h, cg_p_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(S, p, z, ph, copies, st));
             }
+            return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+        };
+        // eager: poll the states every chunk iterations
+        auto more = [&](bool& m) -> int {
             done_iters += chunk;
-            if (cudaGetLastError() != cudaSuccess) return DD_ERR_CUDA;
             if (cudaMemcpyAsync(hs.data(), st, sizeof(CGState) * nrhs, cudaMemcpyDeviceToHost, h->stream) !=
                 cudaSuccess)
                 return DD_ERR_CUDA;
             if (cudaStreamSynchronize(h->stream) != cudaSuccess) return DD_ERR_CUDA;
+            polled = true;
             bool any = false;
             for (int k = 0; k < nrhs; ++k) any = any || hs[k].active;
-            if (!any || done_iters >= maxit + chunk) break;
-        }
+            m = any && done_iters < maxit + chunk;
+            return DD_OK;
+        };
+        const LoopCond lc{st, nrhs, (maxit + 2 * chunk - 1) / chunk, nullptr, 0, 1};
+        int rc = dd_loop(h, body, more, lc);
+        if (rc || !polled) return rc;  // captured: breakdowns are raised on the device
         int tot = 0, flags = 0;
         for (int k = 0; k < nrhs; ++k) {
             tot += hs[k].iters;
@@ -318,11 +337,12 @@ DD_DEV cpx<R> cscal(double re, double im) {
 }
 
 template <class R, class SM>
-__global__ void bicg_start_kernel(long long n, SM x, SM r, SM rhat, SM p, SM v, const CGState* outer) {
+__global__ void bicg_start_kernel(SiteSet S, SM x, SM r, SM rhat, SM p, SM v, const CGState* outer) {
     const int rhs = blockIdx.y;
     if (outer && !outer[rhs].active) return;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ti >= S.n) return;
+    const long long i = S.at(ti);
     Spinor<R> z, a;
     zero(z);
     at_rhs(x, rhs).store(i, z);
@@ -342,13 +362,14 @@ __global__ void bicg_arm_kernel(int nrhs, CGState* st) {
 }
 
 template <class R, class SM>
-__global__ void __launch_bounds__(128) bicg_rho_kernel(long long n, SM rhat, SM r, const CGState* st, Reduce red) {
+__global__ void __launch_bounds__(128) bicg_rho_kernel(SiteSet S, SM rhat, SM r, const CGState* st, Reduce red) {
     __shared__ double sh[34];
     const int rhs = blockIdx.y;
     if (!st[rhs].active) return;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double v[3] = {0.0, 0.0, 0.0};
-    if (i < n) {
+    if (ti < S.n) {
+        const long long i = S.at(ti);
         Spinor<R> a, b;
         at_rhs(rhat, rhs).load(i, a);
         at_rhs(r, rhs).load(i, b);
@@ -367,12 +388,13 @@ __global__ void __launch_bounds__(128) bicg_rho_kernel(long long n, SM rhat, SM 
 
 // p = r + beta (p - omega v), hop copy of p
 template <class R, class SM, class SH>
-__global__ void __launch_bounds__(128) bicg_p_kernel(long long n, SM p, SM r, SM v, SH ph, int copy,
+__global__ void __launch_bounds__(128) bicg_p_kernel(SiteSet S, SM p, SM r, SM v, SH ph, int copy,
                                                      const CGState* st) {
     const int rhs = blockIdx.y;
     if (!st[rhs].active) return;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ti >= S.n) return;
+    const long long i = S.at(ti);
     const CGState& c = st[rhs];
     const cpx<R> be = cscal<R>(c.be_re, c.be_im), om = cscal<R>(c.om_re, c.om_im);
     Spinor<R> pp, rr, vv;
@@ -387,12 +409,13 @@ __global__ void __launch_bounds__(128) bicg_p_kernel(long long n, SM p, SM r, SM
 
 // s = r - alpha v, hop copy of s
 template <class R, class SM, class SH>
-__global__ void __launch_bounds__(128) bicg_s_kernel(long long n, SM s, SM r, SM v, SH shop, int copy,
+__global__ void __launch_bounds__(128) bicg_s_kernel(SiteSet S, SM s, SM r, SM v, SH shop, int copy,
                                                      const CGState* st) {
     const int rhs = blockIdx.y;
     if (!st[rhs].active) return;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ti >= S.n) return;
+    const long long i = S.at(ti);
     const CGState& c = st[rhs];
     const cpx<R> al = cscal<R>(c.al_re, c.al_im);
     Spinor<R> rr, vv;
@@ -406,14 +429,15 @@ __global__ void __launch_bounds__(128) bicg_s_kernel(long long n, SM s, SM r, SM
 
 // x += alpha p + omega s, r = s - omega t; <rh, r>, |r|^2 -> FIN_BI_RHO
 template <class R, class SM>
-__global__ void __launch_bounds__(128) bicg_xr_kernel(long long n, SM x, SM r, SM p, SM s, SM t, SM rhat,
+__global__ void __launch_bounds__(128) bicg_xr_kernel(SiteSet S, SM x, SM r, SM p, SM s, SM t, SM rhat,
                                                       const CGState* st, Reduce red) {
     __shared__ double sh[34];
     const int rhs = blockIdx.y;
     if (!st[rhs].active) return;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double v[3] = {0.0, 0.0, 0.0};
-    if (i < n) {
+    if (ti < S.n) {
+        const long long i = S.at(ti);
         const CGState& c = st[rhs];
         const cpx<R> al = cscal<R>(c.al_re, c.al_im), om = cscal<R>(c.om_re, c.om_im);
         Spinor<R> xx, pp, ss, tt, rh;
@@ -452,6 +476,7 @@ struct BiCGStab {
     long long lk_rs;
     CGState* st;
     const CGState* outer;
+    SiteSet S;  // the sites of the solve (all even sites, or one block colour's)
 
     Reduce red(int op) const {
         Reduce R_;
@@ -484,6 +509,7 @@ struct BiCGStab {
         A.red = red(op);
         A.red3 = red3;
         A.rhat = rhat;
+        A.S = S;
         return A;
     }
     // out = Dtilde in_h (in_m: the same vector in master storage for the xpay term)
@@ -494,34 +520,42 @@ struct BiCGStab {
     }
     // solve Dtilde x = r (r holds the right-hand side; x starts at 0)
     int run(const double* rr0, double tol, double abs_fac, int maxit, int chunk, int* iters_out) {
-        const long long n = h->g.Vh;
-        dim3 grid(grid_for(n, 128), nrhs);
+        dim3 grid(grid_for(S.n, 128), nrhs);
         if (maxit < 1) maxit = 1;
         DD_KLAUNCH(h, cg_arm_kernel<<<1, 64, 0, h->stream>>>(nrhs, st, outer, rr0, tol, abs_fac, maxit));
         DD_KLAUNCH(h, bicg_arm_kernel<<<1, 64, 0, h->stream>>>(nrhs, st));
-        DD_KLAUNCH(h, bicg_start_kernel<R, SM><<<grid, 128, 0, h->stream>>>(n, x, r, rhat, p, v, outer));
-        DD_KLAUNCH(h, bicg_rho_kernel<R, SM><<<grid, 128, 0, h->stream>>>(n, rhat, r, st, red(FIN_BI_RHO)));
+        DD_KLAUNCH(h, bicg_start_kernel<R, SM><<<grid, 128, 0, h->stream>>>(S, x, r, rhat, p, v, outer));
+        DD_KLAUNCH(h, bicg_rho_kernel<R, SM><<<grid, 128, 0, h->stream>>>(S, rhat, r, st, red(FIN_BI_RHO)));
         std::vector<CGState> hs(nrhs);
         int done = 0;
-        for (;;) {
+        bool polled = false;
+        auto body = [&]() -> int {
             for (int it = 0; it < chunk; ++it) {
-                DD_KLAUNCH(h, bicg_p_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(n, p, r, v, ph, copies, st));
+                DD_KLAUNCH(h, bicg_p_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(S, p, r, v, ph, copies, st));
                 apply(ph, p, v, FIN_BI_ALPHA, 1);
-                DD_KLAUNCH(h, bicg_s_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(n, s, r, v, shop, copies, st));
+                DD_KLAUNCH(h, bicg_s_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(S, s, r, v, shop, copies, st));
                 apply(shop, s, t, FIN_BI_OMEGA, 2);
-                DD_KLAUNCH(h, bicg_xr_kernel<R, SM><<<grid, 128, 0, h->stream>>>(n, x, r, p, s, t, rhat, st,
+                DD_KLAUNCH(h, bicg_xr_kernel<R, SM><<<grid, 128, 0, h->stream>>>(S, x, r, p, s, t, rhat, st,
                                                                                  red(FIN_BI_RHO)));
             }
+            return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+        };
+        auto more = [&](bool& m) -> int {
             done += chunk;
-            if (cudaGetLastError() != cudaSuccess) return DD_ERR_CUDA;
             if (cudaMemcpyAsync(hs.data(), st, sizeof(CGState) * nrhs, cudaMemcpyDeviceToHost, h->stream) !=
                 cudaSuccess)
                 return DD_ERR_CUDA;
             if (cudaStreamSynchronize(h->stream) != cudaSuccess) return DD_ERR_CUDA;
+            polled = true;
             bool any = false;
             for (int k = 0; k < nrhs; ++k) any = any || hs[k].active;
-            if (!any || done >= maxit + chunk) break;
-        }
+            m = any && done < maxit + chunk;
+            return DD_OK;
+        };
+        // a breakdown only ends this inner solve (no NUMERIC stop)
+        const LoopCond lc{st, nrhs, (maxit + 2 * chunk - 1) / chunk, nullptr, 0, 0};
+        int rc = dd_loop(h, body, more, lc);
+        if (rc || !polled) return rc;
         int tot = 0, flags = 0;
         for (int k = 0; k < nrhs; ++k) {
             tot += hs[k].iters;
@@ -568,7 +602,7 @@ Reduce store_reduce(dd_handle* h, double* out) {
 
 // FP64 hop helper on eo FP64 vectors
 template <int MASK>
-void hop64(dd_handle* h, int nrhs, int par, SpinorF64 in, SpinorF64 xin, SpinorF64 out, double a, double b,
+void hop64(dd_handle* h, SiteSet S, int nrhs, int par, SpinorF64 in, SpinorF64 xin, SpinorF64 out, double a, double b,
            int hasx, LinkF64 lk, long long lk_rs, const CGState* st, Reduce red) {
     HopArgs<SpinorF64, SpinorF64, SpinorF64, LinkF64> A;
     A.g = h->g;
@@ -586,7 +620,16 @@ void hop64(dd_handle* h, int nrhs, int par, SpinorF64 in, SpinorF64 xin, SpinorF
     A.colour_mask = 3;
     A.st = st;
     A.red = red;
+    A.S = S;
     launch_hop<double, SpinorF64, SpinorF64, SpinorF64, LinkF64, MASK>(A, nrhs, h);
+}
+
+__global__ void not_converged_kernel(int nrhs, const CGState* outer, int* status) {
+    for (int k = 0; k < nrhs; ++k)
+        if (outer[k].active) {
+            raise_status(status, DD_ERR_NOT_CONVERGED);
+            return;
+        }
 }
 
 __global__ void add_scalars_kernel(int n, double* a, const double* b) {
@@ -603,7 +646,8 @@ int defect_correction(dd_handle* h, int nrhs, int field0, int step, Inner& cg, b
     SolverVecs& v = h->vecs[0];
     const long long Vh = h->g.Vh;
     const double kappa = h->prm.kappa;
-    dim3 grid(grid_for(Vh, 128), nrhs);
+    const SiteSet S = cg.S;
+    dim3 grid(grid_for(S.n, 128), nrhs);
     SpinorF64 be{v.be, Vh}, bo{v.bo, Vh}, xe{v.xe, Vh}, xo{v.xo, Vh}, re{v.re, Vh}, t64{v.t64, Vh},
         t64b{v.t64b, Vh};
     LinkF64 lk64 = field_links<LinkF64>(h, field0);
@@ -616,24 +660,25 @@ int defect_correction(dd_handle* h, int nrhs, int field0, int step, Inner& cg, b
     Reduce none;
     none.op = FIN_NONE;
     // |b|^2 over both parities, then b~ = b_e + kappa H_eo b_o (in place)
-    DD_KLAUNCH(h, norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(Vh, be, store_reduce(h, bb)));
-    DD_KLAUNCH(h, norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(Vh, bo, store_reduce(h, tmp)));
+    DD_KLAUNCH(h, norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(S, be, store_reduce(h, bb)));
+    DD_KLAUNCH(h, norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(S, bo, store_reduce(h, tmp)));
     DD_KLAUNCH(h, add_scalars_kernel<<<1, 64, 0, h->stream>>>(nrhs, bb, tmp));
-    hop64<MASK>(h, nrhs, 0, bo, be, be, 1.0, kappa, 1, lk64, rs64, nullptr, none);
+    hop64<MASK>(h, S, nrhs, 0, bo, be, be, 1.0, kappa, 1, lk64, rs64, nullptr, none);
     DD_KLAUNCH(h, outer_arm_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, bb, tol));
-    DD_KLAUNCH(h, zero64_kernel<<<grid, 128, 0, h->stream>>>(Vh, xe));
-    DD_KLAUNCH(h, copy_kernel<SpinorF64, SpinorF64><<<grid, 128, 0, h->stream>>>(Vh, be, re, nullptr));
-    DD_KLAUNCH(h, norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(Vh, re, store_reduce(h, rr)));
+    DD_KLAUNCH(h, zero64_kernel<<<grid, 128, 0, h->stream>>>(S, xe));
+    DD_KLAUNCH(h, copy_kernel<SpinorF64, SpinorF64><<<grid, 128, 0, h->stream>>>(S, be, re, nullptr));
+    DD_KLAUNCH(h, norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(S, re, store_reduce(h, rr)));
     DD_KLAUNCH(h, outer_update_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, rr));
     if (cudaGetLastError() != cudaSuccess) return DD_ERR_CUDA;
     const double tol_inner = fp64_inner ? 0.0 : h->prm.tol_inner;
-    int total = 0;
+    int total = 0, cycles = 0;
+    bool polled = false;
     std::vector<CGState> hs(nrhs);
-    for (int cycle = 0; cycle < 200; ++cycle) {
+    auto body = [&]() -> int {
         // inner right-hand side: the current FP64 residual
         // (the mixed inner system is normalised to |r| = 1)
         if (!fp64_inner) {
-            DD_KLAUNCH(h, normalised_copy_kernel<SM><<<grid, 128, 0, h->stream>>>(Vh, re, cg.r, rr, outer));
+            DD_KLAUNCH(h, normalised_copy_kernel<SM><<<grid, 128, 0, h->stream>>>(S, re, cg.r, rr, outer));
             DD_KLAUNCH(h, fill_kernel<<<1, 64, 0, h->stream>>>(nrhs, ones, 1.0));
         }
         // inner stopping rule: FP64 inner aims at the outer target directly
@@ -642,25 +687,40 @@ int defect_correction(dd_handle* h, int nrhs, int field0, int step, Inner& cg, b
         int rc = cg.run(fp64_inner ? rr : ones, tol_inner, fp64_inner ? 0.25 : -1.0, maxit - total, 16, &it);
         total += it;
         if (rc) return rc;
-        DD_KLAUNCH(h, add_correction_kernel<SM><<<grid, 128, 0, h->stream>>>(Vh, xe, cg.x, fp64_inner ? nullptr : rr,
+        DD_KLAUNCH(h, add_correction_kernel<SM><<<grid, 128, 0, h->stream>>>(S, xe, cg.x, fp64_inner ? nullptr : rr,
                                                                           outer));
         // true residual r = b~ - Dtilde x (FP64)
-        hop64<MASK>(h, nrhs, 1, xe, xe, t64, 0.0, 1.0, 0, lk64, rs64, outer, none);
-        hop64<MASK>(h, nrhs, 0, t64, xe, t64b, 1.0, -kappa * kappa, 1, lk64, rs64, outer, none);
-        DD_KLAUNCH(h, residual_kernel<<<grid, 128, 0, h->stream>>>(Vh, be, t64b, re, outer, store_reduce(h, rr)));
+        hop64<MASK>(h, S, nrhs, 1, xe, xe, t64, 0.0, 1.0, 0, lk64, rs64, outer, none);
+        hop64<MASK>(h, S, nrhs, 0, t64, xe, t64b, 1.0, -kappa * kappa, 1, lk64, rs64, outer, none);
+        DD_KLAUNCH(h, residual_kernel<<<grid, 128, 0, h->stream>>>(S, be, t64b, re, outer, store_reduce(h, rr)));
         DD_KLAUNCH(h, outer_update_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, rr));
-        if (cudaGetLastError() != cudaSuccess) return DD_ERR_CUDA;
+        return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+    };
+    auto more = [&](bool& m) -> int {
+        ++cycles;
         if (cudaMemcpyAsync(hs.data(), outer, sizeof(CGState) * nrhs, cudaMemcpyDeviceToHost, h->stream) !=
             cudaSuccess)
             return DD_ERR_CUDA;
         if (cudaStreamSynchronize(h->stream) != cudaSuccess) return DD_ERR_CUDA;
+        polled = true;
         bool any = false;
         for (int k = 0; k < nrhs; ++k) any = any || hs[k].active;
-        if (!any || total >= maxit) break;
-    }
+        m = any && total < maxit && cycles < 200;
+        return DD_OK;
+    };
+    // captured: the inner maxit stays the full budget; the outer loop stops
+    // once the inner iterations of all cycles reach maxit
+    const LoopCond lc{outer, nrhs, 200, cg.st, (long long)maxit, 0};
+    int rc = dd_loop(h, body, more, lc);
+    if (rc) return rc;
     // x_o = b_o + kappa H_oe x_e
-    hop64<MASK>(h, nrhs, 1, xe, bo, xo, 1.0, kappa, 1, lk64, rs64, nullptr, none);
+    hop64<MASK>(h, S, nrhs, 1, xe, bo, xo, 1.0, kappa, 1, lk64, rs64, nullptr, none);
     if (cudaGetLastError() != cudaSuccess) return DD_ERR_CUDA;
+    if (!polled) {
+        // captured: a solve that missed its target is reported in the status word
+        DD_KLAUNCH(h, not_converged_kernel<<<1, 1, 0, h->stream>>>(nrhs, outer, h->d_status));
+        return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+    }
     std::vector<double> hb(nrhs);
     if (cudaMemcpyAsync(hb.data(), bb, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
         return DD_ERR_CUDA;
@@ -696,8 +756,8 @@ static void fill_bicg(dd_handle* h, B& bi, long long Vh, CGState* inner, CGState
 }
 
 template <int MASK>
-static int solve_packed_mask(dd_handle* h, int nrhs, int field0, int step, int prec, double tol, int maxit,
-                             int* iters, double* relres) {
+static int solve_packed_mask(dd_handle* h, SiteSet S, int nrhs, int field0, int step, int prec, double tol,
+                             int maxit, int* iters, double* relres) {
     SolverVecs& v = h->vecs[0];
     const long long Vh = h->g.Vh;
     CGState* inner = h->d_cg;
@@ -720,6 +780,7 @@ static int solve_packed_mask(dd_handle* h, int nrhs, int field0, int step, int p
         cg.lk_rs = field_stride<LinkF64>(h, step);
         cg.st = inner;
         cg.outer = outer;
+        cg.S = S;
         return defect_correction<MASK>(h, nrhs, field0, step, cg, true, tol, maxit, iters, relres);
     } else if (h->prm.krylov == DD_KRYLOV_BICGSTAB) {
         if (prec == DD_PREC_F32) {
@@ -731,6 +792,7 @@ static int solve_packed_mask(dd_handle* h, int nrhs, int field0, int step, int p
             bi.copies = 0;
             bi.lk = field_links<LinkF32>(h, field0);
             bi.lk_rs = field_stride<LinkF32>(h, step);
+            bi.S = S;
             return defect_correction<MASK>(h, nrhs, field0, step, bi, false, tol, maxit, iters, relres);
         }
         BiCGStab<float, SpinorF32, SpinorF16, LinkF16, MASK> bi;
@@ -741,6 +803,7 @@ static int solve_packed_mask(dd_handle* h, int nrhs, int field0, int step, int p
         bi.copies = 1;
         bi.lk = field_links<LinkF16>(h, field0);
         bi.lk_rs = field_stride<LinkF16>(h, step);
+        bi.S = S;
         return defect_correction<MASK>(h, nrhs, field0, step, bi, false, tol, maxit, iters, relres);
     } else if (prec == DD_PREC_F32) {
         NormalCG<float, SpinorF32, SpinorF32, LinkF32, MASK> cg;
@@ -759,6 +822,7 @@ static int solve_packed_mask(dd_handle* h, int nrhs, int field0, int step, int p
         cg.lk_rs = field_stride<LinkF32>(h, step);
         cg.st = inner;
         cg.outer = outer;
+        cg.S = S;
         return defect_correction<MASK>(h, nrhs, field0, step, cg, false, tol, maxit, iters, relres);
     } else {
         NormalCG<float, SpinorF32, SpinorF16, LinkF16, MASK> cg;
@@ -777,14 +841,19 @@ static int solve_packed_mask(dd_handle* h, int nrhs, int field0, int step, int p
         cg.lk_rs = field_stride<LinkF16>(h, step);
         cg.st = inner;
         cg.outer = outer;
+        cg.S = S;
         return defect_correction<MASK>(h, nrhs, field0, step, cg, false, tol, maxit, iters, relres);
     }
 }
 
 int solve_packed(dd_handle* h, int nrhs, int field0, int step, int prec, double tol, int maxit, int* iters,
-                 double* relres, int mask) {
-    if (mask == 1) return solve_packed_mask<1>(h, nrhs, field0, step, prec, tol, maxit, iters, relres);
-    return solve_packed_mask<0>(h, nrhs, field0, step, prec, tol, maxit, iters, relres);
+                 double* relres, int mask, int colour) {
+    SiteSet S{nullptr, (long long)h->g.Vh};
+    // Dirichlet solves whose right-hand sides live on the blocks of one
+    // colour: the other colour's sites stay zero and are not visited
+    if (mask == 1 && colour >= 0 && colour <= 1 && h->d_colour_sites[colour]) S = SiteSet{h->d_colour_sites[colour], (long long)h->g.Vh / 2};
+    if (mask == 1) return solve_packed_mask<1>(h, S, nrhs, field0, step, prec, tol, maxit, iters, relres);
+    return solve_packed_mask<0>(h, S, nrhs, field0, step, prec, tol, maxit, iters, relres);
 }
 
 extern "C" int dd_solve(dd_t h, void* x, const void* b, const void* U, int nrhs, int prec, int* iters,

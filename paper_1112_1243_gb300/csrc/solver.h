@@ -17,6 +17,9 @@
 // mask = 0: the whole operator D; mask = 1: the Dirichlet block operators
 // D_bb + D_ww (every hop that leaves a block dropped), i.e. all block solves
 // of the right-hand side's blocks at once, even-odd preconditioned (hops
-// inside a block still connect opposite site parities).
+// inside a block still connect opposite site parities).  colour = 0 / 1
+// (mask 1 only): the right-hand sides vanish outside the blocks of that
+// colour, so only that colour's sites are visited (the other colour of the
+// solution is left as it was).
 int solve_packed(dd_handle* h, int nrhs, int field0, int field_step, int prec, double tol, int maxit, int* iters,
-                 double* relres, int mask = 0);
+                 double* relres, int mask = 0, int colour = -1);
