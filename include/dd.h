@@ -83,6 +83,8 @@ extern "C" {
 #define DD_PURPOSE_BLOCK_ACCEPT 5
 #define DD_PURPOSE_GLOBAL_ACCEPT 6
 #define DD_PURPOSE_USER_NOISE 7
+#define DD_PURPOSE_BLOCK_SCHUR_NOISE 4  /* step 2 of Eq. 4step (dd_block_schur_filter) */
+#define DD_PURPOSE_BLOCK_SCHUR_ACCEPT 8
 
 /* estimator modes (Eq. param) */
 #define DD_EST_FACTORS 0  /* factor i uses U_i, U_{i+1} of the geodesic path, its own eta_i */
@@ -109,6 +111,13 @@ typedef struct {
     int maxit;         /* iteration cap of any single Krylov solve */
     int features;      /* workspace parts to plan: DD_FEAT_* bits, 0 = all */
     int krylov;        /* inner Krylov method of mixed-precision solves: DD_KRYLOV_* */
+    int sub_block[4];  /* one level of recursive decomposition (Eq. ddrec): sub-block
+                          extents, each block split into an even number of sub-blocks
+                          per direction; all 0 = no recursion.  With sub-blocks the
+                          active links are those of the sub-blocks (active_mode applied
+                          to the sub-blocks; dd_chain_step needs PAPER or INNER6),
+                          dd_block_filter acts on the sub-blocks (Eq. 4step step 1)
+                          and dd_block_schur_filter on the blocks (step 2). */
 } dd_params;
 
 /* inner Krylov method of the FP32/FP16 solves (the FP64 solver is always CGNR) */
@@ -212,6 +221,29 @@ int dd_det_ratio_estimate(dd_t h, const void* U_old, const void* U_new, int n, u
  * All (block, factor) solves run in one persistent launch. */
 int dd_block_filter(dd_t h, const void* U_old, void* U_new, int colour_mask, int mode, int n, uint64_t seed,
                     uint64_t ctr, double* ln_b, uint8_t* accept);
+
+/* Block Schur filter, step 2 of Eq. 4step with one level of recursion
+ * (Eq. ddrec; handles created with sub_block set): for every block b of the
+ * colours in colour_mask the stochastic estimate of
+ * ln det(Dhat_b'^dag Dhat_b' / Dhat_b^dag Dhat_b), Dhat_b = the Schur
+ * complement of the block operator D_b with respect to its sub-blocks,
+ * summed over n interpolation factors (Eq. param, one eta per factor):
+ *   ln_b[b] = -sum_i sum_{x in b} (2 Re<eta_i, delta_i>_x + |delta_i|_x^2),
+ *   delta_i = [D1[U_{i+1}]^{-1} (s_i, 0)]_black,
+ *   s_i = B'E'^{-1}C' eta_i - A'A^{-1}BE^{-1}C eta_i,
+ * with D1 the Dirichlet operator of the blocks, A/E the sub-block operators
+ * of the black/white sub-blocks and B/C the hops across sub-block faces
+ * inside a block (unprimed: U_i, primed: U_{i+1}); eta_i on the black
+ * sub-blocks (purpose DD_PURPOSE_BLOCK_SCHUR_NOISE, element 12 s + 3 spin
+ * + colour, sub = i).  Solves: sub-block Dirichlet solves to tol_block, the
+ * block Dirichlet solve to tol_global (mixed precision as dd_solve).
+ * accept[b] = ln u_b < ln_b[b] (purpose DD_PURPOSE_BLOCK_SCHUR_ACCEPT,
+ * element b; 1 for unselected colours); the active links of rejected blocks
+ * are restored from U_old in U_new.  ln_b (nblocks doubles) and accept
+ * (nblocks bytes) are device arrays over the blocks (not the sub-blocks).
+ * DD_ERR_UNSUPPORTED without sub-blocks. */
+int dd_block_schur_filter(dd_t h, const void* U_old, void* U_new, int colour_mask, int n, uint64_t seed,
+                          uint64_t ctr, double* ln_b, uint8_t* accept);
 
 /* The block filter of several lattices at once (Eq. 4step step 1): every
  * (block, factor) solve of all nh handles runs in ONE persistent launch, the
@@ -320,6 +352,9 @@ int dd_block_ratios_noalloc(const int dims[4], const int block[4], double kappa,
  *   of (U, Up) with n_block factors (rejected blocks restored), U <- Up;
  *   then the n_global-factor estimate for (U0, U) and the global accept
  *   (U <- U0 on rejection).
+ * With sub-blocks (one level of recursion) every iteration runs step 0,
+ * step 1 on the sub-blocks and, when n_schur > 0, step 2 on the blocks
+ * (dd_block_schur_filter, same counter), before U <- Up.
  * Counters: step << 20 | iteration << 4 | pass for the proposal and filter,
  * step << 20 | n_inner << 4 for the global step (step < 2^40).
  * U: device gauge field, updated in place.  All buffers are caller-owned
@@ -336,17 +371,19 @@ typedef struct dd_chain_params {
     int n_or;
     int filter_mode;   /* DD_FILTER_STOCHASTIC or DD_FILTER_EXACT */
     int colour_passes; /* 1 or 2 */
-    int reserved;
+    int n_schur;       /* factors of the block Schur filter (step 2; handles with sub-blocks; 0 = skip) */
     uint64_t seed;
 } dd_chain_params;
 typedef struct dd_chain_buffers {
     void* U0;
     void* Up;
-    double* ln_b;
+    double* ln_b;      /* step 1: per smallest block (sub-blocks when the handle has them) */
     uint8_t* acc_b;
     double* ln_g;
     uint8_t* acc_g;
     double* margin;
+    double* ln_bs;     /* step 2: per block (n_schur > 0 only; else may be NULL) */
+    uint8_t* acc_bs;
 } dd_chain_buffers;
 int dd_chain_step(dd_t h, void* U, const dd_chain_params* p, const dd_chain_buffers* b, unsigned long long step);
 
@@ -378,9 +415,12 @@ int dd_graph_destroy(dd_graph_t graph);
 
 /* Autotuner of the launch shapes (no counterpart in the paper).
  * what: DD_TUNE_HOP (thread-block size x sites per thread of the even-odd
- * hop kernels, FP16/FP32 storage and FP64 separately), DD_TUNE_BLOCK (thread-block size and thread
- * blocks per SM of the persistent block solver, at most 4 per SM), optionally
- * with DD_TUNE_NO_CACHE.  Each candidate is timed with CUDA events on the
+ * hop kernels, FP16/FP32 storage and FP64 separately), DD_TUNE_BLOCK
+ * (thread-block size and thread blocks per SM of the persistent block
+ * solver, at most 4 per SM, and whether the stochastic block filter runs
+ * faster as that persistent launch or as batched whole-lattice Dirichlet
+ * solves of all blocks, one right-hand side per factor), optionally with
+ * DD_TUNE_NO_CACHE.  Each candidate is timed with CUDA events on the
  * handle's stream on this handle's lattice: the hop on zeroed solver
  * vectors (max_rhs right-hand sides), the block solver on one block-filter
  * pass over the fields (U_old, U_new) (device gauge fields; required for
@@ -395,7 +435,8 @@ int dd_graph_destroy(dd_graph_t graph);
  * dd_set_tuning sets the shapes directly (threads 64, 128 or 256 and 1 or 2
  * sites per thread for the FP16/FP32 hops; 64 or 128 threads and 1 site per
  * thread for the FP64 hops; 64, 128 or 256 threads and 1..4 blocks per SM
- * for the block solver).
+ * for the block solver; filter_masked 0 = persistent block-filter launch,
+ * 1 = whole-lattice Dirichlet solves).
  * Changing the block-solver shape changes dd_block_filter_batch_workspace. */
 #define DD_TUNE_HOP 1
 #define DD_TUNE_BLOCK 2
@@ -404,10 +445,12 @@ typedef struct dd_tune_report {
     int hop_tpb, hop_spt, hop64_tpb, hop64_spt, block_tpb, block_ctas_per_sm;
     int from_cache;
     float hop_ms, hop_default_ms, hop64_ms, hop64_default_ms, block_ms, block_default_ms;
+    int filter_masked;      /* 1: the stochastic block filter runs as whole-lattice solves */
+    float filter_masked_ms; /* time of that form (one factor) */
 } dd_tune_report;
 int dd_autotune(dd_t h, int what, const void* U_old, const void* U_new, int reps, dd_tune_report* report);
 int dd_set_tuning(dd_t h, int hop_tpb, int hop_spt, int hop64_tpb, int hop64_spt, int block_tpb,
-                  int block_ctas_per_sm);
+                  int block_ctas_per_sm, int filter_masked);
 
 /* Release the handle's own tables; the workspace stays with the caller. */
 int dd_finalize(dd_t h);

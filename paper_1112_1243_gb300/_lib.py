@@ -28,6 +28,8 @@ DD_PURPOSE_HEATBATH = 3
 DD_PURPOSE_BLOCK_ACCEPT = 5
 DD_PURPOSE_GLOBAL_ACCEPT = 6
 DD_PURPOSE_USER_NOISE = 7
+DD_PURPOSE_BLOCK_SCHUR_NOISE = 4
+DD_PURPOSE_BLOCK_SCHUR_ACCEPT = 8
 DD_EST_FACTORS, DD_EST_REPLICAS = 0, 1
 DD_FILTER_STOCHASTIC, DD_FILTER_EXACT = 0, 1
 
@@ -58,6 +60,7 @@ class dd_params(ctypes.Structure):
         ("maxit", ctypes.c_int),
         ("features", ctypes.c_int),
         ("krylov", ctypes.c_int),
+        ("sub_block", ctypes.c_int * 4),
     ]
 
 
@@ -71,20 +74,22 @@ class dd_chain_params(ctypes.Structure):
         ("n_or", ctypes.c_int),
         ("filter_mode", ctypes.c_int),
         ("colour_passes", ctypes.c_int),
-        ("reserved", ctypes.c_int),
+        ("n_schur", ctypes.c_int),
         ("seed", ctypes.c_uint64),
     ]
 
 
 class dd_chain_buffers(ctypes.Structure):
-    _fields_ = [(name, ctypes.c_void_p) for name in ("U0", "Up", "ln_b", "acc_b", "ln_g", "acc_g", "margin")]
+    _fields_ = [(name, ctypes.c_void_p) for name in ("U0", "Up", "ln_b", "acc_b", "ln_g", "acc_g", "margin",
+                                                     "ln_bs", "acc_bs")]
 
 
 class dd_tune_report(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in ("hop_tpb", "hop_spt", "hop64_tpb", "hop64_spt", "block_tpb",
                                               "block_ctas_per_sm", "from_cache")] + \
                [(n, ctypes.c_float) for n in ("hop_ms", "hop_default_ms", "hop64_ms", "hop64_default_ms", "block_ms",
-                                              "block_default_ms")]
+                                              "block_default_ms")] + \
+               [("filter_masked", ctypes.c_int), ("filter_masked_ms", ctypes.c_float)]
 
 
 DD_TUNE_HOP, DD_TUNE_BLOCK, DD_TUNE_NO_CACHE = 1, 2, 4
@@ -111,6 +116,7 @@ SIGNATURES = {
     "dd_interpolate": [_P, _P, _P, _P, _I, _I],
     "dd_det_ratio_estimate": [_P, _P, _P, _I, _U64, _U64, _I, _P],
     "dd_block_filter": [_P, _P, _P, _I, _I, _I, _U64, _U64, _P, _P],
+    "dd_block_schur_filter": [_P, _P, _P, _I, _I, _U64, _U64, _P, _P],
     "dd_block_filter_batch_workspace": [_I, _P, _I, ctypes.POINTER(ctypes.c_size_t)],
     "dd_block_filter_batch": [_I, _P, _P, _P, _I, _I, _U64, _U64, _P, _P, _P, ctypes.c_size_t],
     "dd_gauge_update": [_P, _P, _I, _D, _I, _I, _U64, _U64],
@@ -132,7 +138,7 @@ SIGNATURES = {
     "dd_graph_nodes": [_P, ctypes.POINTER(ctypes.c_size_t)],
     "dd_graph_destroy": [_P],
     "dd_autotune": [_P, _I, _P, _P, _I, ctypes.POINTER(dd_tune_report)],
-    "dd_set_tuning": [_P, _I, _I, _I, _I, _I, _I],
+    "dd_set_tuning": [_P, _I, _I, _I, _I, _I, _I, _I],
     "dd_finalize": [_P],
 }
 

@@ -34,6 +34,11 @@ class Handle:
         self.nblocks = 1
         for L, b in zip(self.dims, self.block):
             self.nblocks *= L // b
+        self.sub_block = tuple(params.sub_block) if any(params.sub_block) else None
+        # blocks of the smallest level (the block filter's blocks)
+        self.nfine = 1
+        for L, b in zip(self.dims, self.sub_block or self.block):
+            self.nfine *= L // b
 
     def __del__(self):
         if getattr(self, "ptr", None):
@@ -71,8 +76,10 @@ def dd_default_params():
 def dd_init(dims, block, kappa, bc_time=-1, active_mode=_lib.DD_ACTIVE_AUTO, max_rhs=1,
             inner_prec=_lib.DD_PREC_F16, block_prec=_lib.DD_PREC_F32, tol_global=1e-10,
             tol_block=1e-12, tol_inner=1e-3, maxit=20000, stream=None, device=None, features=0,
-            krylov=_lib.DD_KRYLOV_CGNR):
-    """Create a handle and give it a torch-allocated workspace on `device`."""
+            krylov=_lib.DD_KRYLOV_CGNR, sub_block=None):
+    """Create a handle and give it a torch-allocated workspace on `device`.
+    sub_block: extents of the sub-blocks of one level of recursion (None: no
+    recursion)."""
     lib = _lib.load()
     p = dd_default_params()
     for a in range(4):
@@ -90,6 +97,8 @@ def dd_init(dims, block, kappa, bc_time=-1, active_mode=_lib.DD_ACTIVE_AUTO, max
     p.maxit = int(maxit)
     p.features = int(features)
     p.krylov = int(krylov)
+    for a in range(4):
+        p.sub_block[a] = int(sub_block[a]) if sub_block is not None else 0
     device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
     if stream is None:
         stream = torch.cuda.current_stream(device)
@@ -160,11 +169,24 @@ def dd_det_ratio_estimate(h, U_old, U_new, n, seed, ctr, mode=_lib.DD_EST_FACTOR
 def dd_block_filter(h, U_old, U_new, colour_mask, mode, n, seed, ctr, ln_b=None, accept=None):
     dev = h.workspace.device
     if ln_b is None:
+        ln_b = torch.zeros(h.nfine, dtype=torch.float64, device=dev)
+    if accept is None:
+        accept = torch.zeros(h.nfine, dtype=torch.uint8, device=dev)
+    _check(h, _lib.load().dd_block_filter(h.ptr, _ptr(U_old), _ptr(U_new), int(colour_mask), int(mode), int(n),
+                                          int(seed), int(ctr), _ptr(ln_b), _ptr(accept)))
+    return ln_b, accept
+
+
+def dd_block_schur_filter(h, U_old, U_new, colour_mask, n, seed, ctr, ln_b=None, accept=None):
+    """Step 2 of the hierarchy (handles with sub-blocks): per-block Schur
+    log-ratios over the blocks, decisions, restore."""
+    dev = h.workspace.device
+    if ln_b is None:
         ln_b = torch.zeros(h.nblocks, dtype=torch.float64, device=dev)
     if accept is None:
         accept = torch.zeros(h.nblocks, dtype=torch.uint8, device=dev)
-    _check(h, _lib.load().dd_block_filter(h.ptr, _ptr(U_old), _ptr(U_new), int(colour_mask), int(mode), int(n),
-                                          int(seed), int(ctr), _ptr(ln_b), _ptr(accept)))
+    _check(h, _lib.load().dd_block_schur_filter(h.ptr, _ptr(U_old), _ptr(U_new), int(colour_mask), int(n),
+                                                int(seed), int(ctr), _ptr(ln_b), _ptr(accept)))
     return ln_b, accept
 
 
@@ -275,8 +297,8 @@ def dd_chain_step(h, U, params, buffers, step):
     """One hierarchical step on the device (U updated in place).  params: a
     _lib.dd_chain_params; buffers: dict of the device tensors U0, Up, ln_b,
     acc_b, ln_g, acc_g, margin."""
-    bufs = _lib.dd_chain_buffers(*[_ptr(buffers[k]) for k in ("U0", "Up", "ln_b", "acc_b", "ln_g", "acc_g",
-                                                                 "margin")])
+    bufs = _lib.dd_chain_buffers(*[_ptr(buffers.get(k)) for k in ("U0", "Up", "ln_b", "acc_b", "ln_g", "acc_g",
+                                                                     "margin", "ln_bs", "acc_bs")])
     return _check(h, _lib.load().dd_chain_step(h.ptr, _ptr(U), ctypes.byref(params), ctypes.byref(bufs),
                                                int(step)))
 
@@ -333,9 +355,10 @@ def dd_autotune(h, what=_lib.DD_TUNE_HOP, U_old=None, U_new=None, reps=20):
     return {name: getattr(r, name) for name, _ in r._fields_}
 
 
-def dd_set_tuning(h, hop_tpb=128, hop_spt=1, hop64_tpb=128, hop64_spt=1, block_tpb=256, block_ctas_per_sm=2):
+def dd_set_tuning(h, hop_tpb=128, hop_spt=1, hop64_tpb=128, hop64_spt=1, block_tpb=256, block_ctas_per_sm=2,
+                  filter_masked=0):
     return _check(h, _lib.load().dd_set_tuning(h.ptr, int(hop_tpb), int(hop_spt), int(hop64_tpb), int(hop64_spt),
-                                               int(block_tpb), int(block_ctas_per_sm)))
+                                               int(block_tpb), int(block_ctas_per_sm), int(filter_masked)))
 
 
 def dd_finalize(h):

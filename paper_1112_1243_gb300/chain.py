@@ -24,10 +24,12 @@ class HierarchicalStep:
     n_inner proposal/filter iterations per global step; n_block interpolation
     factors in the block filter, n_global in the global step; colour passes
     1 and 2 (black, white) when the active set is "intra", one pass otherwise.
+    On a handle with sub-blocks, n_schur > 0 adds the blocks' Schur filter
+    (Eq. 4step step 2) after the sub-block filter of every iteration.
     """
 
     def __init__(self, h, beta, n_inner=1, n_block=4, n_global=12, n_or=0, seed=1,
-                 filter_mode=api.DD_FILTER_STOCHASTIC, intra=False):
+                 filter_mode=api.DD_FILTER_STOCHASTIC, intra=False, n_schur=0):
         self.h = h
         self.beta = float(beta)
         self.n_inner = int(n_inner)
@@ -41,8 +43,12 @@ class HierarchicalStep:
         shape = (h.V, 4, 3, 3)
         self.U0 = torch.empty(shape, dtype=torch.complex128, device=dev)
         self.Up = torch.empty(shape, dtype=torch.complex128, device=dev)
-        self.ln_b = torch.zeros(h.nblocks, dtype=torch.float64, device=dev)
-        self.acc_b = torch.zeros(h.nblocks, dtype=torch.uint8, device=dev)
+        # step 1 per smallest block; step 2 (handles with sub-blocks) per block
+        self.ln_b = torch.zeros(h.nfine, dtype=torch.float64, device=dev)
+        self.acc_b = torch.zeros(h.nfine, dtype=torch.uint8, device=dev)
+        self.n_schur = int(n_schur)
+        self.ln_bs = torch.zeros(h.nblocks, dtype=torch.float64, device=dev)
+        self.acc_bs = torch.zeros(h.nblocks, dtype=torch.uint8, device=dev)
         self.ln_g = torch.zeros(self.n_global, dtype=torch.float64, device=dev)
         self.acc_g = torch.zeros(1, dtype=torch.uint8, device=dev)
         self.margin = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -55,9 +61,10 @@ class HierarchicalStep:
         self.params.n_or = self.n_or
         self.params.filter_mode = self.filter_mode
         self.params.colour_passes = len(self.passes)
+        self.params.n_schur = self.n_schur
         self.params.seed = self.seed
         self.buffers = {"U0": self.U0, "Up": self.Up, "ln_b": self.ln_b, "acc_b": self.acc_b, "ln_g": self.ln_g,
-                        "acc_g": self.acc_g, "margin": self.margin}
+                        "acc_g": self.acc_g, "margin": self.margin, "ln_bs": self.ln_bs, "acc_bs": self.acc_bs}
         self.graph = None
         self.graph_U = None
 

@@ -99,6 +99,7 @@ struct TuneConfig {
     int hop_tpb = 128, hop_spt = 1;      // FP16/FP32-storage hop kernels: threads, sites per thread
     int hop64_tpb = 128, hop64_spt = 1;  // FP64 hop kernels
     int block_tpb = 256, block_ctas_per_sm = 2;  // persistent block solver (at most DD_BLOCK_CTAS_MAX per SM)
+    int filter_masked = 0;  // stochastic block filter: 0 persistent per-block kernel, 1 whole-lattice Dirichlet solves
     int tuned = 0;                       // bit 0: hops, bit 1: block solver
 };
 
@@ -153,6 +154,12 @@ struct dd_handle {
     // block extent along axis 0 is odd); Dirichlet solves of one colour
     // visit only these
     int* d_colour_sites[2] = {nullptr, nullptr};
+    // one level of recursion (dd_params.sub_block): geometry and colour
+    // tables of the sub-blocks; LevelScope swaps them in for sub-block work
+    bool has_sub = false;
+    int active_mode = 0;  // resolved DD_ACTIVE_* of the smallest blocks
+    Geo g2;
+    int* d_colour_sites2[2] = {nullptr, nullptr};
     // graph capture (graph.cu): counter offset added by every kernel that
     // draws random numbers (0 outside graph replays), device loop counters
     // of captured solver loops, capture streams of loop bodies by depth
@@ -169,6 +176,33 @@ struct dd_handle {
 };
 
 constexpr int DD_LOOP_SLOTS = 32;
+
+// Makes the sub-block level the handle's block decomposition for the
+// lifetime of the scope (kernels and solvers read h->g and the colour
+// tables); a no-op when `sub` is false.
+struct LevelScope {
+    dd_handle* h;
+    bool on;
+    Geo saved;
+    int* saved_cs[2];
+    LevelScope(dd_handle* h_, bool sub) : h(h_), on(sub && h_->has_sub) {
+        if (!on) return;
+        saved = h->g;
+        saved_cs[0] = h->d_colour_sites[0];
+        saved_cs[1] = h->d_colour_sites[1];
+        h->g = h->g2;
+        h->d_colour_sites[0] = h->d_colour_sites2[0];
+        h->d_colour_sites[1] = h->d_colour_sites2[1];
+    }
+    ~LevelScope() {
+        if (!on) return;
+        h->g = saved;
+        h->d_colour_sites[0] = saved_cs[0];
+        h->d_colour_sites[1] = saved_cs[1];
+    }
+    LevelScope(const LevelScope&) = delete;
+    LevelScope& operator=(const LevelScope&) = delete;
+};
 
 // ----------------------------------------------------------- graph capture
 // true while the handle's stream is being captured into a CUDA graph

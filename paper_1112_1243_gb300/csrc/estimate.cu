@@ -38,9 +38,18 @@ DD_DEV void dd_coords(const Geo& g, const BlockCtx& c, long long q, int x[4], in
     for (int a = 0; a < 4; ++a) x[a] = o[a] + l[a];
 }
 
-// eta on the black sites (purpose / sub), 0 on white; block order
+// extents of the enclosing blocks of a two-level decomposition (x = 0: none)
+DD_DEV bool same_outer_block(int4 ob, const int x[4], const int y[4]) {
+    return ob.x == 0 || (x[0] / ob.x == y[0] / ob.x && x[1] / ob.y == y[1] / ob.y && x[2] / ob.z == y[2] / ob.z &&
+                         x[3] / ob.w == y[3] / ob.w);
+}
+DD_DEV int outer_colour(int4 ob, const int x[4]) { return (x[0] / ob.x + x[1] / ob.y + x[2] / ob.z + x[3] / ob.w) & 1; }
+
+// eta on the black sites (purpose / sub), 0 on white; block order.  With
+// enclosing blocks (ob.x > 0) only inside the enclosing blocks whose colour
+// is in outer_mask.
 __global__ void noise_black_kernel(Geo g, BlockCtx c, double2* bank, long long vs, int purpose, uint64_t seed,
-                                   uint64_t ctr0, const unsigned long long* ctr_off) {
+                                   uint64_t ctr0, const unsigned long long* ctr_off, int4 ob, int outer_mask) {
     const uint64_t ctr = stream_ctr(ctr0, ctr_off);
     long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int i = blockIdx.y;
@@ -51,7 +60,7 @@ __global__ void noise_black_kernel(Geo g, BlockCtx c, double2* bank, long long v
     SpinorF64 out{bank + (long long)i * vs + pos * 12 * c.nb, c.nb};
     Spinor<double> e;
     uint32_t s = (uint32_t)canon_index(g, x);
-    if (col == 0) {
+    if (col == 0 && (ob.x == 0 || ((outer_mask >> outer_colour(ob, x)) & 1))) {
         for (int k = 0; k < 12; ++k) e.c[k] = gaussian(s * 12u + k, (uint32_t)purpose, (uint32_t)i, seed, ctr);
     } else {
         zero(e);
@@ -61,9 +70,11 @@ __global__ void noise_black_kernel(Geo g, BlockCtx c, double2* bank, long long v
 
 // out = -kappa * (hops that cross block faces) in, on the sites of colour
 // `target` (0 elsewhere).  Links from the canonical FP64 copy of the field
-// of slot f0 + i * fstep for right-hand side i.
+// of slot f0 + i * fstep for right-hand side i.  With enclosing blocks
+// (ob.x > 0), hops that leave the enclosing block are dropped as well.
 __global__ void inter_hop_kernel(Geo g, BlockCtx c, const double2* in_bank, double2* out_bank, long long vs,
-                                 const double* canon0, long long canon_fs, int f0, int fstep, int target) {
+                                 const double* canon0, long long canon_fs, int f0, int fstep, int target,
+                                 int4 ob) {
     long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int i = blockIdx.y;
     if (q >= g.V) return;
@@ -82,7 +93,7 @@ __global__ void inter_hop_kernel(Geo g, BlockCtx c, const double2* in_bank, doub
                 y[a] += dir;
                 if (y[a] == g.L[a]) y[a] = 0;
                 if (y[a] < 0) y[a] = g.L[a] - 1;
-                if (block_id_of(g, y) == bid) continue;
+                if (block_id_of(g, y) == bid || !same_outer_block(ob, x, y)) continue;
                 long long qy = dd_position(g, y);
                 SpinorF64 src{(double2*)in_bank + (long long)i * vs + (qy / c.nb) * 12 * c.nb, c.nb};
                 Spinor<double> sp;
@@ -200,7 +211,8 @@ __global__ void sum_items_kernel(Geo g, const int* item_base, int colour_mask, i
 }
 
 __global__ void block_accept_kernel(Geo g, int colour_mask, const double* ln_b, uint8_t* accept, uint64_t seed,
-                                    uint64_t ctr, const unsigned long long* ctr_off) {
+                                    uint64_t ctr, const unsigned long long* ctr_off,
+                                    int purpose = DD_PURPOSE_BLOCK_ACCEPT) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= g.nblocks) return;
     int B[4] = {b % g.nbk[0], (b / g.nbk[0]) % g.nbk[1], (b / (g.nbk[0] * g.nbk[1])) % g.nbk[2],
@@ -211,7 +223,7 @@ __global__ void block_accept_kernel(Geo g, int colour_mask, const double* ln_b, 
         return;
     }
     double u1, u2;
-    uniform_pair((uint32_t)b, DD_PURPOSE_BLOCK_ACCEPT, 0u, seed, stream_ctr(ctr, ctr_off), u1, u2);
+    uniform_pair((uint32_t)b, (uint32_t)purpose, 0u, seed, stream_ctr(ctr, ctr_off), u1, u2);
     accept[b] = log(u1) < ln_b[b] ? 1 : 0;
 }
 
@@ -403,6 +415,165 @@ static int dirichlet_solve_bank(dd_handle* h, const double2* in_bank, double2* o
     return DD_OK;
 }
 
+// ------------------------------------ block filter as whole-lattice solves
+// The stochastic block filter computed with the batched Dirichlet solver
+// instead of the persistent per-block kernel: every block's noise, source
+// and solution live in whole-lattice even-odd vectors (the Dirichlet
+// operator is block-diagonal, so the blocks do not mix), one right-hand side
+// per factor.  eta_i(x) = block noise (purpose DD_PURPOSE_BLOCK_NOISE,
+// element 12 s + k, sub i) on the blocks of colour_mask;
+// b_i = (D_b[U_i] - D_b[U_{i+1}]) eta_i = -kappa (H_b[U_i] - H_b[U_{i+1}]) eta_i,
+// where only the active links differ.
+__global__ void filter_source_kernel(Geo g, int colour_mask, uint64_t seed, uint64_t ctr0,
+                                     const unsigned long long* ctr_off, const double* canon0, long long canon_fs,
+                                     const uint8_t* active, double2* eta_e, double2* eta_o, double2* be,
+                                     double2* bo, double kappa) {
+    const uint64_t ctr = stream_ctr(ctr0, ctr_off);
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (s >= g.V) return;
+    int x[4];
+    canon_coords(g, s, x);
+    const bool in = (colour_mask >> block_colour_of(g, x)) & 1;
+    Spinor<double> e, acc;
+    zero(e);
+    zero(acc);
+    if (in) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k)
+            e.c[k] = gaussian((uint32_t)s * 12u + k, DD_PURPOSE_BLOCK_NOISE, (uint32_t)i, seed, ctr);
+        const double* U1 = canon0 + (long long)i * canon_fs;
+        const double* U2 = canon0 + (long long)(i + 1) * canon_fs;
+        const int bid = block_id_of(g, x);
+        for (int a = 0; a < 4; ++a) {
+            for (int dir = +1; dir >= -1; dir -= 2) {
+                const int y = shift_index(g, x, a, dir);
+                const int l = (dir > 0 ? s : y) * 4 + a;
+                if (!active[l]) continue;
+                int xy[4];
+                canon_coords(g, y, xy);
+                if (block_id_of(g, xy) != bid) continue;  // Dirichlet: hops stay in the block
+                Link<double> u;
+                bool same = true;
+                for (int k = 0; k < 9; ++k) {
+                    const double* p1 = U1 + (long long)l * 18 + 2 * k;
+                    const double* p2 = U2 + (long long)l * 18 + 2 * k;
+                    u.m[k / 3][k % 3] = mk<double>(p1[0] - p2[0], p1[1] - p2[1]);
+                    same = same && p1[0] == p2[0] && p1[1] == p2[1];
+                }
+                if (same) continue;
+                Spinor<double> ey;
+#pragma unroll
+                for (int k = 0; k < 12; ++k)
+                    ey.c[k] = gaussian((uint32_t)y * 12u + k, DD_PURPOSE_BLOCK_NOISE, (uint32_t)i, seed, ctr);
+                Half<double> hf, uh;
+                project<double>(a, dir, ey, hf);
+                if (dir > 0)
+                    mul_link(u, hf, uh);
+                else
+                    mul_link_dag(u, hf, uh);
+                accumulate<double>(a, dir, uh, 1.0, acc);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc.c[k] = (-kappa) * acc.c[k];
+    }
+    const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+    SpinorF64 eo{(par ? eta_o : eta_e) + (long long)i * 12 * g.Vh, g.Vh};
+    SpinorF64 bo_{(par ? bo : be) + (long long)i * 12 * g.Vh, g.Vh};
+    eo.store(s >> 1, e);
+    bo_.store(s >> 1, acc);
+}
+
+// ln_b[b] = -sum_i sum_{x in b} (2 Re<eta_i, d_i>_x + |d_i|_x^2), one thread
+// block per block (fixed order); 0 for blocks outside colour_mask
+__global__ void __launch_bounds__(256) filter_estimate_kernel(Geo g, int colour_mask, const double2* eta_e,
+                                                              const double2* eta_o, const double2* xe,
+                                                              const double2* xo, int n, double* ln_b) {
+    __shared__ double sh[34];
+    const int b = blockIdx.x;
+    int o[4];
+    block_origin(g, b, o);
+    const int col = (o[0] / g.b[0] + o[1] / g.b[1] + o[2] / g.b[2] + o[3] / g.b[3]) & 1;
+    if (!((colour_mask >> col) & 1)) {
+        if (threadIdx.x == 0) ln_b[b] = 0.0;
+        return;
+    }
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) {
+        for (int j = threadIdx.x; j < g.bsites; j += blockDim.x) {
+            int x[4] = {o[0] + j % g.b[0], o[1] + (j / g.b[0]) % g.b[1], o[2] + (j / (g.b[0] * g.b[1])) % g.b[2],
+                        o[3] + j / (g.b[0] * g.b[1] * g.b[2])};
+            const int s = canon_index(g, x);
+            const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+            SpinorF64 es{(double2*)(par ? eta_o : eta_e) + (long long)i * 12 * g.Vh, g.Vh};
+            SpinorF64 ds{(double2*)(par ? xo : xe) + (long long)i * 12 * g.Vh, g.Vh};
+            Spinor<double> e, d;
+            es.load(s >> 1, e);
+            ds.load(s >> 1, d);
+            double t = 0.0;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) t += 2.0 * (e.c[k].x * d.c[k].x + e.c[k].y * d.c[k].y) + norm2(d.c[k]);
+            acc -= t;
+        }
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) ln_b[b] = acc;
+}
+
+// fields of slots 0..n are prepared (canonical and even-odd formats)
+static int block_filter_masked(dd_handle* h, int colour_mask, int n, uint64_t seed, uint64_t ctr, double* ln_b) {
+    const Geo& g = h->g;
+    SolverVecs& v = h->vecs[0];
+    const long long Vh = g.Vh;
+    double2* eta_e = h->dd_vec;
+    double2* eta_o = h->dd_vec + (long long)h->prm.max_rhs * 12 * Vh;
+    const long long canon_fs = (long long)(h->fields[1].canon - h->fields[0].canon) * 2;
+    dim3 gv(grid_for(g.V, 128), n);
+    DD_KLAUNCH(h, filter_source_kernel<<<gv, 128, 0, h->stream>>>(g, colour_mask, seed, ctr, h->d_ctr_off,
+                                                                 (const double*)h->fields[0].canon, canon_fs,
+                                                                 h->d_active_mask, eta_e, eta_o, v.be, v.bo,
+                                                                 h->prm.kappa));
+    DD_LAUNCH_CHECK(h, "filter_source_kernel");
+    const int colour = colour_mask == 1 ? 0 : colour_mask == 2 ? 1 : -1;
+    int it = 0;
+    int rc = solve_packed(h, n, 1, 1, h->prm.inner_prec, h->prm.tol_block, h->prm.maxit, &it, nullptr, 1, colour);
+    if (rc && rc != DD_ERR_NOT_CONVERGED) return dd_fail(h, rc, "block filter: Dirichlet solves failed");
+    if (rc == DD_ERR_NOT_CONVERGED) raise_status_host(h, DD_ERR_NOT_CONVERGED);
+    DD_KLAUNCH(h, filter_estimate_kernel<<<g.nblocks, 256, 0, h->stream>>>(g, colour_mask, eta_e, eta_o, v.xe, v.xo, n,
+                                                                         ln_b));
+    DD_LAUNCH_CHECK(h, "filter_estimate_kernel");
+    return DD_OK;
+}
+
+// autotuner probe: one masked block-filter pass (n = 1, every block)
+int tune_block_filter_masked(dd_handle* h, const double* U_old, const double* U_new, int reps, float* ms) {
+    int rc = prepare_fields(h, U_old, U_new, 1, true, true);
+    if (rc) return rc;
+    double* ln = h->d_item_out;  // only timed; the values are discarded (nblocks <= items_cap)
+    cudaEvent_t e0, e1;
+    DD_CUDA(h, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return dd_fail(h, DD_ERR_CUDA, "cudaEventCreate");
+    }
+    rc = block_filter_masked(h, 3, 1, 1, 0, ln);
+    cudaEventRecord(e0, h->stream);
+    for (int r = 0; r < reps && !rc; ++r) rc = block_filter_masked(h, 3, 1, 1, 0, ln);
+    cudaEventRecord(e1, h->stream);
+    float t = -1.f;
+    if (!rc && cudaEventSynchronize(e1) == cudaSuccess) {
+        cudaEventElapsedTime(&t, e0, e1);
+        t /= (float)reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (t < 0) return dd_fail(h, DD_ERR_CUDA, "masked block-filter timing failed");
+    *ms = t;
+    return DD_OK;
+}
+
 // ------------------------------------------------------------- entry points
 extern "C" int dd_block_filter(dd_t h, const void* U_old, void* U_new, int colour_mask, int mode, int n,
                                uint64_t seed, uint64_t ctr, double* ln_b, uint8_t* accept) {
@@ -412,8 +583,16 @@ extern "C" int dd_block_filter(dd_t h, const void* U_old, void* U_new, int colou
     if (rc) return rc;
     if (!U_old || !U_new || !ln_b || !accept || n < 1 || n > h->prm.max_rhs || colour_mask < 1 || colour_mask > 3)
         return dd_fail(h, DD_ERR_INVALID_ARG, "dd_block_filter: bad arguments");
+    // with one level of recursion this filter is step 1 of Eq. 4step: the
+    // smallest blocks (sub-blocks)
+    LevelScope level(h, true);
     if (mode == DD_FILTER_EXACT) {
         rc = block_filter_exact(h, (const double*)U_old, (const double*)U_new, colour_mask, ln_b);
+        if (rc) return rc;
+    } else if (mode == DD_FILTER_STOCHASTIC && h->tune.filter_masked) {
+        rc = prepare_fields(h, (const double*)U_old, (const double*)U_new, n, true, true);
+        if (rc) return rc;
+        rc = block_filter_masked(h, colour_mask, n, seed, ctr, ln_b);
         if (rc) return rc;
     } else if (mode == DD_FILTER_STOCHASTIC) {
         rc = prepare_fields(h, (const double*)U_old, (const double*)U_new, n, true, false);
@@ -479,7 +658,7 @@ BatchPlan batch_plan(int nh, dd_handle* const* hs, int n) {
 int batch_check(int nh, dd_handle* const* hs, int n) {
     if (nh < 1 || !hs) return DD_ERR_INVALID_ARG;
     for (int k = 0; k < nh; ++k) {
-        if (!hs[k] || !hs[k]->ws || !hs[k]->feat_estimate) return DD_ERR_INVALID_ARG;
+        if (!hs[k] || !hs[k]->ws || !hs[k]->feat_estimate || hs[k]->has_sub) return DD_ERR_INVALID_ARG;
         if (n < 1 || n > hs[k]->prm.max_rhs) return DD_ERR_INVALID_ARG;
         if (hs[k]->stream != hs[0]->stream || hs[k]->prm.block_prec != hs[0]->prm.block_prec)
             return DD_ERR_INVALID_ARG;
@@ -652,11 +831,12 @@ extern "C" int dd_det_ratio_estimate(dd_t h, const void* U_old, const void* U_ne
     const long long dd64_fs = (long long)(h->fields[1].dd64 - h->fields[0].dd64);
     dim3 gv(grid_for(g.V, 128), n);
     // 1. eta on black sites
+    const int4 no_outer = make_int4(0, 0, 0, 0);
     DD_KLAUNCH(h, noise_black_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], vs, DD_PURPOSE_GLOBAL_NOISE, seed, ctr,
-                                                               h->d_ctr_off));
+                                                               h->d_ctr_off, no_outer, 3));
     // 2. w = C eta, w' = C' eta (onto white sites)
-    DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], bank[1], vs, (const double*)h->fields[0].canon, canon_fs, 0, fs, 1));
-    DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], bank[2], vs, (const double*)h->fields[0].canon, canon_fs, 1, fs, 1));
+    DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], bank[1], vs, (const double*)h->fields[0].canon, canon_fs, 0, fs, 1, no_outer));
+    DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[0], bank[2], vs, (const double*)h->fields[0].canon, canon_fs, 1, fs, 1, no_outer));
     DD_LAUNCH_CHECK(h, "schur stage 1-2");
     // 3. z = E^{-1} w, z' = E'^{-1} w': all white-block solves of all factors
     //    as one batched even-odd CG on the Dirichlet operator
@@ -665,8 +845,8 @@ extern "C" int dd_det_ratio_estimate(dd_t h, const void* U_old, const void* U_ne
     rc = dirichlet_solve_bank(h, bank[2], bank[4], n, 1, fs, 1);
     if (rc) return rc;
     // 4. v = B z, v' = B' z' (onto black sites)
-    DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[3], bank[1], vs, (const double*)h->fields[0].canon, canon_fs, 0, fs, 0));
-    DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[4], bank[2], vs, (const double*)h->fields[0].canon, canon_fs, 1, fs, 0));
+    DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[3], bank[1], vs, (const double*)h->fields[0].canon, canon_fs, 0, fs, 0, no_outer));
+    DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g, c, bank[4], bank[2], vs, (const double*)h->fields[0].canon, canon_fs, 1, fs, 0, no_outer));
     DD_LAUNCH_CHECK(h, "schur stage 4");
     // 5. a = A^{-1} v (black-block solves)
     rc = dirichlet_solve_bank(h, bank[1], bank[5], n, 0, fs, 0);
@@ -693,6 +873,120 @@ extern "C" int dd_det_ratio_estimate(dd_t h, const void* U_old, const void* U_ne
     DD_KLAUNCH(h, estimate_kernel<<<gb, 128, 0, h->stream>>>(g, c, bank[0], vs, v.xe, v.xo, red));
     DD_LAUNCH_CHECK(h, "estimate_kernel");
     if (rc == DD_ERR_NOT_CONVERGED) return dd_fail(h, rc, "dd_det_ratio_estimate: global solve hit maxit");
+    return DD_OK;
+}
+
+// ------------------------------------------- block Schur filter (step 2)
+// ln_b[b] = -sum_i sum_{x in b, black sub-block} (2 Re<eta_i, d_i>_x + |d_i|_x^2)
+// for every block b of g1 with colour in colour_mask (0 for the others): one
+// thread block per block b, a fixed summation order (deterministic).  eta in
+// the block order of the sub-blocks (g2, c2), d in even-odd FP64 chunks.
+__global__ void __launch_bounds__(256) estimate_blocks_kernel(Geo g1, Geo g2, BlockCtx c2, const double2* eta_bank,
+                                                              long long vs, const double2* xe, const double2* xo,
+                                                              int n, int colour_mask, double* ln_b) {
+    __shared__ double sh[34];
+    const int b = blockIdx.x;
+    int o[4];
+    block_origin(g1, b, o);
+    const int col = (o[0] / g1.b[0] + o[1] / g1.b[1] + o[2] / g1.b[2] + o[3] / g1.b[3]) & 1;
+    if (!((colour_mask >> col) & 1)) {
+        if (threadIdx.x == 0) ln_b[b] = 0.0;
+        return;
+    }
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) {
+        for (int j = threadIdx.x; j < g1.bsites; j += blockDim.x) {
+            int l[4] = {j % g1.b[0], (j / g1.b[0]) % g1.b[1], (j / (g1.b[0] * g1.b[1])) % g1.b[2],
+                        j / (g1.b[0] * g1.b[1] * g1.b[2])};
+            int x[4] = {o[0] + l[0], o[1] + l[1], o[2] + l[2], o[3] + l[3]};
+            if (block_colour_of(g2, x)) continue;  // white sub-block: eta = 0
+            const long long q = dd_position(g2, x);
+            SpinorF64 es{(double2*)eta_bank + (long long)i * vs + (q / c2.nb) * 12 * c2.nb, c2.nb};
+            Spinor<double> e, d;
+            es.load(q % c2.nb, e);
+            const int s = canon_index(g1, x);
+            const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+            SpinorF64 ds{(double2*)(par ? xo : xe) + (long long)i * 12 * g1.Vh, g1.Vh};
+            ds.load(s >> 1, d);
+            double t = 0.0;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) t += 2.0 * (e.c[k].x * d.c[k].x + e.c[k].y * d.c[k].y) + norm2(d.c[k]);
+            acc -= t;
+        }
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) ln_b[b] = acc;
+}
+
+extern "C" int dd_block_schur_filter(dd_t h, const void* U_old, void* U_new, int colour_mask, int n, uint64_t seed,
+                                     uint64_t ctr, double* ln_b, uint8_t* accept) {
+    int rc = dd_require_ws(h);
+    if (rc) return rc;
+    rc = dd_require_feature(h, h->feat_estimate, "dd_block_schur_filter");
+    if (rc) return rc;
+    if (!h->has_sub) return dd_fail(h, DD_ERR_UNSUPPORTED, "dd_block_schur_filter: the handle has no sub-blocks");
+    if (!U_old || !U_new || !ln_b || !accept || n < 1 || n > h->prm.max_rhs || colour_mask < 1 || colour_mask > 3)
+        return dd_fail(h, DD_ERR_INVALID_ARG, "dd_block_schur_filter: bad arguments");
+    const Geo g1 = h->g;
+    const int R = h->prm.max_rhs;
+    const long long vs = 12LL * g1.V;
+    double2* bank[6];
+    for (int k = 0; k < 6; ++k) bank[k] = h->dd_vec + (long long)k * R * vs;
+    const int4 ob = make_int4(g1.b[0], g1.b[1], g1.b[2], g1.b[3]);
+    SolverVecs& v = h->vecs[0];
+    Geo g2;
+    BlockCtx c2;
+    {
+        // Schur pieces of the sub-block decomposition inside every block:
+        // block order, Dirichlet solves and colour tables of the sub-blocks
+        LevelScope level(h, true);
+        g2 = h->g;
+        c2 = block_ctx(h);
+        rc = prepare_fields(h, (const double*)U_old, (const double*)U_new, n, true, true);
+        if (rc) return rc;
+        const long long canon_fs = (long long)(h->fields[1].canon - h->fields[0].canon) * 2;
+        const long long dd64_fs = (long long)(h->fields[1].dd64 - h->fields[0].dd64);
+        dim3 gv(grid_for(g2.V, 128), n);
+        // 1. eta on the black sub-blocks of the selected blocks
+        DD_KLAUNCH(h, noise_black_kernel<<<gv, 128, 0, h->stream>>>(g2, c2, bank[0], vs, DD_PURPOSE_BLOCK_SCHUR_NOISE, seed,
+                                                                   ctr, h->d_ctr_off, ob, colour_mask));
+        // 2. w = C eta, w' = C' eta (hops across sub-block faces inside a block)
+        DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g2, c2, bank[0], bank[1], vs, (const double*)h->fields[0].canon, canon_fs, 0, 1, 1, ob));
+        DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g2, c2, bank[0], bank[2], vs, (const double*)h->fields[0].canon, canon_fs, 1, 1, 1, ob));
+        DD_LAUNCH_CHECK(h, "block schur stage 1-2");
+        // 3. z = E^{-1} w, z' = E'^{-1} w' (white sub-blocks)
+        rc = dirichlet_solve_bank(h, bank[1], bank[3], n, 0, 1, 1);
+        if (rc) return rc;
+        rc = dirichlet_solve_bank(h, bank[2], bank[4], n, 1, 1, 1);
+        if (rc) return rc;
+        // 4. v = B z, v' = B' z'
+        DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g2, c2, bank[3], bank[1], vs, (const double*)h->fields[0].canon, canon_fs, 0, 1, 0, ob));
+        DD_KLAUNCH(h, inter_hop_kernel<<<gv, 128, 0, h->stream>>>(g2, c2, bank[4], bank[2], vs, (const double*)h->fields[0].canon, canon_fs, 1, 1, 0, ob));
+        DD_LAUNCH_CHECK(h, "block schur stage 4");
+        // 5. a = A^{-1} v (black sub-blocks)
+        rc = dirichlet_solve_bank(h, bank[1], bank[5], n, 0, 1, 0);
+        if (rc) return rc;
+        // 6. s = v' - A' a
+        DD_KLAUNCH(h, schur_source_kernel<<<gv, 128, 0, h->stream>>>(g2, c2, bank[2], bank[5], bank[3], vs, h->fields[0].dd64, dd64_fs, 1, 1));
+        DD_KLAUNCH(h, dd_to_eo_kernel<<<gv, 128, 0, h->stream>>>(g2, c2, bank[3], vs, v.be, v.bo));
+        DD_LAUNCH_CHECK(h, "block schur stage 5-6");
+    }
+    // 7. D1' y = (s, 0): the Dirichlet operator of the blocks plays the part
+    //    of D in the global step (even-odd formats do not depend on blocks)
+    int iters = 0;
+    rc = solve_packed(h, n, 1, 1, h->prm.inner_prec, h->prm.tol_global, h->prm.maxit, &iters, nullptr, 1);
+    if (rc && rc != DD_ERR_NOT_CONVERGED) return dd_fail(h, rc, "dd_block_schur_filter: block solve failed");
+    if (rc == DD_ERR_NOT_CONVERGED) raise_status_host(h, DD_ERR_NOT_CONVERGED);
+    // 8. per-block log-ratios, decisions, restore
+    DD_KLAUNCH(h, estimate_blocks_kernel<<<g1.nblocks, 256, 0, h->stream>>>(g1, g2, c2, bank[0], vs, v.xe, v.xo, n,
+                                                                          colour_mask, ln_b));
+    DD_KLAUNCH(h, block_accept_kernel<<<grid_for(g1.nblocks, 128), 128, 0, h->stream>>>(
+                      g1, colour_mask, ln_b, accept, seed, ctr, h->d_ctr_off, DD_PURPOSE_BLOCK_SCHUR_ACCEPT));
+    if (h->n_active > 0)
+        DD_KLAUNCH(h, restore_kernel<<<grid_for(h->n_active, 128), 128, 0, h->stream>>>(g1, h->n_active, h->d_active_links,
+                                                                                      accept, (const double*)U_old,
+                                                                                      (double*)U_new));
+    DD_LAUNCH_CHECK(h, "block schur accept");
     return DD_OK;
 }
 

@@ -391,7 +391,7 @@ void plan(dd_handle* h, char* base) {
     h->block_slot_bytes = ((size_t)nb * (4 * 192 + 5 * 192) + 4096 + 255) & ~(size_t)255;
     h->block_slots = std::max(1, h->num_sms) * DD_BLOCK_CTAS_MAX;
     h->block_scratch = c.take<char>(est ? h->block_slot_bytes * h->block_slots : 0);
-    h->items_cap = h->g.nblocks * 2 * R + 64;
+    h->items_cap = std::max(h->g.nblocks, h->has_sub ? h->g2.nblocks : 0) * 2 * R + 64;
     h->d_items = c.take<int>((size_t)5 * h->items_cap);  // five ints per item
     h->d_item_out = c.take<double>((size_t)h->items_cap);
     h->d_queue = c.take<int>(64);
@@ -468,6 +468,25 @@ extern "C" int dd_init(dd_t* out, const dd_params* p, void* stream) {
     }
     g.bc = p->bc_time;
     geo_finish(g);
+    // one level of recursion: sub-blocks tile every block with an even
+    // number of sub-blocks per direction (the sub-block checkerboard inside a
+    // block is then the global one)
+    const bool any_sub = p->sub_block[0] || p->sub_block[1] || p->sub_block[2] || p->sub_block[3];
+    if (any_sub) {
+        Geo& g2 = h->g2;
+        g2 = g;
+        for (int a = 0; a < 4; ++a) {
+            int b2 = p->sub_block[a];
+            if (b2 < 1 || g.b[a] % b2 || ((g.b[a] / b2) & 1)) {
+                delete h;
+                return DD_ERR_INVALID_ARG;
+            }
+            g2.b[a] = b2;
+            g2.nbk[a] = g.L[a] / b2;
+        }
+        geo_finish(g2);
+        h->has_sub = true;
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -475,19 +494,24 @@ extern "C" int dd_init(dd_t* out, const dd_params* p, void* stream) {
         delete h;
         return DD_ERR_CUDA;
     }
-    // active links, grouped by (colour, direction, site parity) for the heat-bath
+    // active links of the smallest blocks, grouped by (colour, direction,
+    // site parity) for the heat-bath
+    const Geo& gf = h->has_sub ? h->g2 : g;
     HostGeo G;
     for (int a = 0; a < 4; ++a) {
-        G.L[a] = g.L[a];
-        G.b[a] = g.b[a];
-        G.nbk[a] = g.nbk[a];
+        G.L[a] = gf.L[a];
+        G.b[a] = gf.b[a];
+        G.nbk[a] = gf.nbk[a];
     }
-    G.V = g.V;
-    const int mode = resolve_mode(*p);
-    if (mode == DD_ACTIVE_INNER6 && std::min(std::min(g.b[0], g.b[1]), std::min(g.b[2], g.b[3])) < 4) {
+    G.V = gf.V;
+    dd_params pf = *p;
+    for (int a = 0; a < 4; ++a) pf.block[a] = gf.b[a];
+    const int mode = resolve_mode(pf);
+    if (mode == DD_ACTIVE_INNER6 && std::min(std::min(gf.b[0], gf.b[1]), std::min(gf.b[2], gf.b[3])) < 4) {
         delete h;
         return DD_ERR_INVALID_ARG;
     }
+    h->active_mode = mode;
     std::vector<uint8_t> act = active_links(G, mode);
     std::vector<int> links;
     h->h_group_off.assign(17, 0);
@@ -521,21 +545,23 @@ extern "C" int dd_init(dd_t* out, const dd_params* p, void* stream) {
     if (e == cudaSuccess) e = cudaMemset(h->d_loop, 0, sizeof(int) * DD_LOOP_SLOTS);
     // sites of each block colour by even-odd index: with an even block
     // extent along axis 0, x0 = 2 hx and 2 hx + 1 lie in one block, so the
-    // list is the same for both site parities
-    if (e == cudaSuccess && (g.b[0] & 1) == 0) {
+    // list is the same for both site parities (blocks, then sub-blocks)
+    for (int lev = 0; lev < (h->has_sub ? 2 : 1); ++lev) {
+        const Geo& gl = lev ? h->g2 : g;
+        int** dst = lev ? h->d_colour_sites2 : h->d_colour_sites;
+        if (e != cudaSuccess || (gl.b[0] & 1)) continue;
         std::vector<int> cs[2];
-        for (int hh = 0; hh < g.Vh; ++hh) {
-            int hx = hh % g.Lh0, r = hh / g.Lh0;
-            int x1 = r % g.L[1], x2 = (r / g.L[1]) % g.L[2], x3 = r / (g.L[1] * g.L[2]);
+        for (int hh = 0; hh < gl.Vh; ++hh) {
+            int hx = hh % gl.Lh0, r = hh / gl.Lh0;
+            int x1 = r % gl.L[1], x2 = (r / gl.L[1]) % gl.L[2], x3 = r / (gl.L[1] * gl.L[2]);
             int x0 = 2 * hx + ((x1 + x2 + x3) & 1);
-            int col = (x0 / g.b[0] + x1 / g.b[1] + x2 / g.b[2] + x3 / g.b[3]) & 1;
+            int col = (x0 / gl.b[0] + x1 / gl.b[1] + x2 / gl.b[2] + x3 / gl.b[3]) & 1;
             cs[col].push_back(hh);
         }
         for (int col = 0; col < 2 && e == cudaSuccess; ++col) {
-            e = cudaMalloc(&h->d_colour_sites[col], sizeof(int) * std::max<size_t>(1, cs[col].size()));
+            e = cudaMalloc(&dst[col], sizeof(int) * std::max<size_t>(1, cs[col].size()));
             if (e == cudaSuccess)
-                e = cudaMemcpy(h->d_colour_sites[col], cs[col].data(), sizeof(int) * cs[col].size(),
-                               cudaMemcpyHostToDevice);
+                e = cudaMemcpy(dst[col], cs[col].data(), sizeof(int) * cs[col].size(), cudaMemcpyHostToDevice);
         }
     }
     if (e != cudaSuccess) {
@@ -548,6 +574,8 @@ extern "C" int dd_init(dd_t* out, const dd_params* p, void* stream) {
         cudaFree(h->d_loop);
         cudaFree(h->d_colour_sites[0]);
         cudaFree(h->d_colour_sites[1]);
+        cudaFree(h->d_colour_sites2[0]);
+        cudaFree(h->d_colour_sites2[1]);
         delete h;
         return DD_ERR_CUDA;
     }
@@ -686,6 +714,8 @@ extern "C" int dd_finalize(dd_t h) {
     cudaFree(h->d_loop);
     cudaFree(h->d_colour_sites[0]);
     cudaFree(h->d_colour_sites[1]);
+    cudaFree(h->d_colour_sites2[0]);
+    cudaFree(h->d_colour_sites2[1]);
     for (cudaStream_t st : h->body_streams) cudaStreamDestroy(st);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;

@@ -16,6 +16,7 @@
 #include "dslash.cuh"
 
 int tune_block_filter(dd_handle* h, const double* U_old, const double* U_new, int reps, float* ms);
+int tune_block_filter_masked(dd_handle* h, const double* U_old, const double* U_new, int reps, float* ms);
 
 namespace {
 
@@ -48,8 +49,8 @@ bool file_lookup(const std::string& key, TuneConfig& t) {
     while (std::fgets(line, sizeof(line), f)) {
         char k[512];
         TuneConfig c;
-        if (std::sscanf(line, "%511s %d %d %d %d %d %d", k, &c.hop_tpb, &c.hop_spt, &c.hop64_tpb, &c.hop64_spt,
-                        &c.block_tpb, &c.block_ctas_per_sm) == 7 &&
+        if (std::sscanf(line, "%511s %d %d %d %d %d %d %d", k, &c.hop_tpb, &c.hop_spt, &c.hop64_tpb, &c.hop64_spt,
+                        &c.block_tpb, &c.block_ctas_per_sm, &c.filter_masked) == 8 &&
             key == k) {
             c.tuned = 3;
             t = c;
@@ -65,8 +66,8 @@ void file_store(const std::string& key, const TuneConfig& t) {
     if (!path || !*path) return;
     FILE* f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s %d %d %d %d %d %d\n", key.c_str(), t.hop_tpb, t.hop_spt, t.hop64_tpb, t.hop64_spt,
-                 t.block_tpb, t.block_ctas_per_sm);
+    std::fprintf(f, "%s %d %d %d %d %d %d %d\n", key.c_str(), t.hop_tpb, t.hop_spt, t.hop64_tpb, t.hop64_spt,
+                 t.block_tpb, t.block_ctas_per_sm, t.filter_masked);
     std::fclose(f);
 }
 
@@ -232,6 +233,15 @@ extern "C" int dd_autotune(dd_t h, int what, const void* U_old, const void* U_ne
                     keep.block_ctas_per_sm = s.spt;
                 }
             }
+            // the same filter as batched whole-lattice Dirichlet solves
+            float msm = -1.f;
+            rc = tune_block_filter_masked(h, (const double*)U_old, (const double*)U_new, std::max(1, reps / 10), &msm);
+            if (rc) {
+                h->tune = keep;
+                return rc;
+            }
+            r.filter_masked_ms = msm;
+            keep.filter_masked = msm < best ? 1 : 0;
             r.block_ms = best;
             keep.tuned |= 2;
             h->tune = keep;
@@ -248,19 +258,20 @@ extern "C" int dd_autotune(dd_t h, int what, const void* U_old, const void* U_ne
     r.hop64_spt = h->tune.hop64_spt;
     r.block_tpb = h->tune.block_tpb;
     r.block_ctas_per_sm = h->tune.block_ctas_per_sm;
+    r.filter_masked = h->tune.filter_masked;
     if (rep) *rep = r;
     return DD_OK;
 }
 
 extern "C" int dd_set_tuning(dd_t h, int hop_tpb, int hop_spt, int hop64_tpb, int hop64_spt, int block_tpb,
-                             int block_ctas_per_sm) {
+                             int block_ctas_per_sm, int filter_masked) {
     if (!h) return DD_ERR_INVALID_ARG;
     auto ok_shape = [](int tpb, int spt, int max_tpb) {
         return (tpb == 64 || tpb == 128 || tpb == 256) && tpb <= max_tpb && (spt == 1 || spt == 2);
     };
     if (!ok_shape(hop_tpb, hop_spt, 256) || !ok_shape(hop64_tpb, hop64_spt, 128) || hop64_spt != 1 ||
         !(block_tpb == 64 || block_tpb == 128 || block_tpb == 256) || block_ctas_per_sm < 1 ||
-        block_ctas_per_sm > DD_BLOCK_CTAS_MAX)
+        block_ctas_per_sm > DD_BLOCK_CTAS_MAX || (filter_masked != 0 && filter_masked != 1))
         return dd_fail(h, DD_ERR_INVALID_ARG, "dd_set_tuning: shape out of range");
     h->tune.hop_tpb = hop_tpb;
     h->tune.hop_spt = hop_spt;
@@ -268,5 +279,6 @@ extern "C" int dd_set_tuning(dd_t h, int hop_tpb, int hop_spt, int hop64_tpb, in
     h->tune.hop64_spt = hop64_spt;
     h->tune.block_tpb = block_tpb;
     h->tune.block_ctas_per_sm = block_ctas_per_sm;
+    h->tune.filter_masked = filter_masked;
     return DD_OK;
 }

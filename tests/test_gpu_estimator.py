@@ -54,8 +54,12 @@ def _block_case(api, dims, block, mode, cm, n, eps=0.3, kappa=0.13):
 @pytest.mark.parametrize("dims,block,mode,cm,n", [((4, 4, 4, 4), (2, 2, 2, 2), "intra", 1, 1),
                                                  ((4, 4, 4, 4), (2, 2, 2, 2), "intra", 2, 3),
                                                  ((8, 8, 8, 8), (4, 4, 4, 4), "paper", 3, 2)])
-def test_block_filter_stochastic(api, dims, block, mode, cm, n):
+@pytest.mark.parametrize("masked", [0, 1])
+def test_block_filter_stochastic(api, dims, block, mode, cm, n, masked):
+    """Both forms of the filter: the persistent per-block launch and the
+    batched whole-lattice Dirichlet solves."""
     lat, h, U, Up = _block_case(api, dims, block, mode, cm, n)
+    api.dd_set_tuning(h, filter_masked=masked)
     kappa = 0.13
     Upd = dev(Up)
     ln_b, acc = api.dd_block_filter(h, dev(U), Upd, cm, api.DD_FILTER_STOCHASTIC, n, 99, 5)

@@ -57,6 +57,7 @@ def test_autotune_picks_candidate_and_stays_correct(api):
     assert (rep["block_tpb"], rep["block_ctas_per_sm"]) in [(256, 2), (256, 1), (128, 2), (128, 4), (64, 4)]
     assert 0 < rep["hop_ms"] <= rep["hop_default_ms"]
     assert 0 < rep["block_ms"] <= rep["block_default_ms"]
+    assert rep["filter_masked_ms"] > 0 and rep["filter_masked"] == int(rep["filter_masked_ms"] < rep["block_ms"])
     assert not rep["from_cache"]
     # mixed solve with the tuned shapes
     b = synthetic.random_spinor(dims, 12, nrhs=2)
@@ -68,15 +69,17 @@ def test_autotune_picks_candidate_and_stays_correct(api):
         assert true <= 1e-10 * 1.01
     # block filter: per-block log-ratios agree across block-solver shapes
     ln_ref = None
-    for tpb, ctas in [(256, 2), (128, 4), (64, 4)]:
-        api.dd_set_tuning(h, rep["hop_tpb"], rep["hop_spt"], rep["hop64_tpb"], 1, tpb, ctas)
+    for tpb, ctas, masked in [(256, 2, 0), (128, 4, 0), (64, 4, 0), (256, 2, 1)]:
+        api.dd_set_tuning(h, rep["hop_tpb"], rep["hop_spt"], rep["hop64_tpb"], 1, tpb, ctas, masked)
         Un = Up.clone()
         ln_b, acc = api.dd_block_filter(h, Ud, Un, 3, api.DD_FILTER_STOCHASTIC, 2, 11, 3)
         got = host(ln_b)
         if ln_ref is None:
             ln_ref = got
         else:
-            assert np.max(np.abs(got - ln_ref)) <= 1e-9 * max(1.0, np.max(np.abs(ln_ref)))
+            # the whole-lattice form meets tol_block relative to all blocks together
+            tol = 1e-7 if masked else 1e-9
+            assert np.max(np.abs(got - ln_ref)) <= tol * max(1.0, np.max(np.abs(ln_ref))), (tpb, ctas, masked)
     assert api.dd_status(h)[0] == 0
     # the process cache answers a second request without timing
     rep2 = api.dd_autotune(h, api.DD_TUNE_HOP | api.DD_TUNE_BLOCK, Ud, Up, reps=4)
