@@ -59,6 +59,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay measurement")
     p.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
+    p.add_argument("--no-recursive", action="store_true", help="skip the step with one level of recursion")
     p.add_argument("--fp64-steps", type=int, default=0,
                    help="also time this many steps with the plain FP64 solver (same workload)")
     p.add_argument("--no-batched-filter", action="store_true",
@@ -374,6 +375,8 @@ def run_gpu(args, cfg):
         line["mixed_vs_fp64"] = compare_precisions(args, CONFIGS[args.compare_config], dev, stream, rank)
     if not args.no_batched_filter:
         line["batched_filter"] = measure_batched_filter(dev, stream)
+    if not args.no_recursive:
+        line["recursive"] = measure_recursive(cfg, dev, stream)
     if rank == 0 and not args.no_cpu_baseline:
         per_app, n, t = oracle_sample(cfg, seconds=15.0)
         line["cpu_baseline"] = {
@@ -464,6 +467,44 @@ def measure_batched_filter(dev, stream, reps=3):
            "block_estimates_per_s": items / t}
     for h in hs:
         del h
+    return out
+
+
+def measure_recursive(cfg, dev, stream, n_schur=4, steps=1):
+    """The benchmark step with one level of recursion (Eq. 4step steps 0-3):
+    the blocks of the workload split into 4^4 sub-blocks, step 1 on the
+    sub-blocks, step 2 (the blocks' Schur complements, n_schur factors) on
+    the blocks, then the global step; global estimates per second."""
+    import torch
+    from paper_1112_1243_gb300 import api, synthetic
+    from paper_1112_1243_gb300.chain import HierarchicalStep
+    sub = tuple(b // 2 for b in cfg["block"])
+    nmax = max(cfg["n_global"], cfg["n_block"], n_schur)
+    h = api.dd_init(cfg["dims"], cfg["block"], cfg["kappa"], max_rhs=nmax, inner_prec=api.DD_PREC_F16,
+                    tol_global=1e-10, tol_block=1e-12, tol_inner=1e-3, maxit=40000, stream=stream, device=dev,
+                    krylov=api.DD_KRYLOV_BICGSTAB, sub_block=sub)
+    U = torch.from_numpy(synthetic.random_gauge(cfg["dims"], cfg["eps"], cfg["seed"])).to(dev)
+    chain = HierarchicalStep(h, BETA, n_inner=1, n_block=cfg["n_block"], n_global=cfg["n_global"],
+                             seed=cfg["seed"] * 7919, n_schur=n_schur)
+    chain.step(U, 0)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        chain.step(U, 1 + k)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t = e0.elapsed_time(e1) / 1e3 / steps
+    out = {"workload": f"{'x'.join(map(str, cfg['dims']))} lattice, {'x'.join(map(str, cfg['block']))} blocks "
+                       f"split into {'x'.join(map(str, sub))} sub-blocks (active links of the sub-blocks), "
+                       f"{cfg['n_block']} sub-block, {n_schur} block-Schur and {cfg['n_global']} global factors",
+           "value": cfg["n_global"] / t, "unit": "estimates/s", "ms_per_step": 1e3 * t,
+           "block_schur_accept_rate_last_step": float(chain.acc_bs.float().mean().item()),
+           "sub_block_accept_rate_last_step": float(chain.acc_b.float().mean().item()),
+           "device_status": api.dd_status(h)[0]}
+    del chain
+    del h
+    torch.cuda.empty_cache()
     return out
 
 

@@ -67,6 +67,8 @@ extern "C" {
 #define DD_ACTIVE_PAPER 1  /* the rule applied to the block itself */
 #define DD_ACTIVE_INNER6 2 /* the rule applied to the block shrunk by one site per side */
 #define DD_ACTIVE_INTRA 3  /* every link with both ends in one block (updated colour by colour) */
+#define DD_ACTIVE_ALL 4    /* every link: pure-gauge updates of the whole lattice (thermalisation);
+                              not a decoupled set for the block filter */
 
 /* operators of dd_apply_D */
 #define DD_OP_D 0          /* D psi on the whole lattice */

@@ -21,7 +21,7 @@ Readings where the paper is silent:
 """
 import numpy as np
 
-ACTIVE_MODES = ("paper", "inner6", "intra")
+ACTIVE_MODES = ("paper", "inner6", "intra", "all")
 
 
 def resolve_active_mode(block, mode="auto"):
@@ -118,6 +118,9 @@ class Lattice:
     def _active_links(self, mode):
         """Boolean mask of shape (V, 4): link (s, a) is updated in the proposal."""
         act = np.zeros((self.V, 4), dtype=bool)
+        if mode == "all":  # every link (pure-gauge updates of the whole lattice)
+            act[:] = True
+            return act
         if mode == "intra":
             for a in range(4):
                 act[:, a] = self.block_id[self.fwd[:, a]] == self.block_id

@@ -61,3 +61,17 @@ def test_workspace_size_query_without_gpu():
     assert names == ["dims", "block", "kappa", "bc_time", "active_mode", "max_rhs", "inner_prec", "block_prec",
                      "tol_global", "tol_block", "tol_inner", "maxit", "features", "krylov", "sub_block"]
     assert ctypes.sizeof(_lib.dd_params) % 8 == 0
+
+
+def test_variance_fits_and_acceptance():
+    """Host-side analysis of the 1/N extrapolation: exact data are fitted
+    exactly, and the acceptance formula agrees with the oracle's statement of
+    the Gaussian law."""
+    from oracle import accept
+    from paper_1112_1243_gb300 import variance
+    Ns = [1, 2, 4, 8, 16]
+    a, b = variance.fit_inverse_n(Ns, [0.7 + 2.5 / n for n in Ns])
+    assert abs(a - 0.7) < 1e-12 and abs(b - 2.5) < 1e-12
+    assert abs(variance.fit_through_zero([1, 2, 3], [2.0, 4.0, 6.0]) - 2.0) < 1e-12
+    for s2 in (0.0, 0.3, 1.0, 4.0, 25.0):
+        assert abs(variance.exact_acceptance(s2) - accept.gaussian_acceptance(s2)) < 1e-15
