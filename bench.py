@@ -44,7 +44,6 @@ BETA = 5.3
 # links with two stored rows + output; FP16 spinor = 48 B + 4 B scale,
 # FP16 link rows = 24 B, FP32 spinor = 96 B, FP64 spinor 192 B, FP64 link 144 B)
 HOP_BYTES = {0: 52 + 8 * 24 + 52, 1: 52 + 8 * 24 + 96 + 96, 2: 192 + 8 * 144 + 192}
-HOP_FLOPS = 1320
 
 
 def parse():

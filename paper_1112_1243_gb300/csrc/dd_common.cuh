@@ -202,8 +202,8 @@ struct LinkF64 {
     long long stride;
     static constexpr int chunks = 9;
     template <class R>
-    DD_DEV void load(long long i, int a, Link<R>& u, long long off = 0) const {
-        const double2* q = p + off + (long long)a * 9 * stride + i;
+    DD_DEV void load(long long i, int a, Link<R>& u) const {
+        const double2* q = p + (long long)a * 9 * stride + i;
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             double2 v = q[k * stride];
@@ -218,8 +218,8 @@ struct LinkF32 {
     long long stride;
     static constexpr int chunks = 3;
     template <class R>
-    DD_DEV void load(long long i, int a, Link<R>& u, long long off = 0) const {
-        const float4* q = p + off + (long long)a * 3 * stride + i;
+    DD_DEV void load(long long i, int a, Link<R>& u) const {
+        const float4* q = p + (long long)a * 3 * stride + i;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             float4 v = q[k * stride];
@@ -237,8 +237,8 @@ struct LinkF16 {
     long long stride;
     static constexpr int chunks = 3;
     template <class R>
-    DD_DEV void load(long long i, int a, Link<R>& u, long long off = 0) const {
-        const uint2* q = p + off + (long long)a * 3 * stride + i;
+    DD_DEV void load(long long i, int a, Link<R>& u) const {
+        const uint2* q = p + (long long)a * 3 * stride + i;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             uint2 v = q[k * stride];

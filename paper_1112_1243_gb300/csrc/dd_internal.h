@@ -112,7 +112,6 @@ struct dd_handle {
     int* d_active_links = nullptr;   // canonical link indices 4*s + a of the active set, grouped
     std::vector<int> h_group_off;    // offsets of (colour, dir, parity) groups in d_active_links (17 entries)
     uint8_t* d_active_mask = nullptr;  // [V*4]
-    uint8_t* d_amask_eo = nullptr;     // [2][Vh]: bit a = link (site, a) active, per site parity
     int* d_status = nullptr;           // device status word
     unsigned long long* d_hb_fails = nullptr;
     // workspace

@@ -50,12 +50,6 @@ struct HopArgs {
     int red3 = 0;
     SX rhat;
     SiteSet S = {nullptr, -1};  // output sites (n < 0: all Vh sites of parity p)
-    // per-rhs fields that differ from a base field only on the active links:
-    // links whose active bit (amask[parity][Vh], bit a = link (site, a)) is
-    // clear are read from lk_base, shared by every rhs (amask null: off)
-    LK lk_base;
-    const uint8_t* amask = nullptr;
-    int rhs_fast = 0;  // set by the launcher
 };
 
 template <class LK>
@@ -64,15 +58,11 @@ DD_DEV LK link_parity(LK lk, int par, long long Vh) {
     return lk;
 }
 
-// lk_p / lk_q: links of parity p / 1 - p; with an active-bit table am
-// ([2][Vh]) they are the base field and the links whose bit is set are read
-// at element offset roff (this rhs's field) instead.
 template <class R, class SIn, class LK, int MASK>
 DD_DEV void hop_site(const Geo& g, int p, int h, const int x[4], const SIn& in, const LK& lk_p, const LK& lk_q,
-                     const uint8_t* am, long long roff, int g5in, Spinor<R>& acc) {
+                     int g5in, Spinor<R>& acc) {
     zero(acc);
     const int s = canon_index(g, x);
-    const unsigned mown = am ? (unsigned)am[(long long)p * g.Vh + h] : 0u;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         int loc = x[a] % g.b[a];
@@ -93,7 +83,7 @@ DD_DEV void hop_site(const Geo& g, int p, int h, const int x[4], const SIn& in, 
             Half<R> hf, uh;
             project<R>(a, +1, s, hf);
             Link<R> u;
-            lk_p.load(h, a, u, ((mown >> a) & 1u) ? roff : 0);
+            lk_p.load(h, a, u);
             mul_link(u, hf, uh);
             R sc = (a == 3 && x[3] == g.L[3] - 1) ? (R)g.bc * w : w;
             accumulate<R>(a, +1, uh, sc, acc);
@@ -106,8 +96,7 @@ DD_DEV void hop_site(const Geo& g, int p, int h, const int x[4], const SIn& in, 
             Half<R> hf, uh;
             project<R>(a, -1, s, hf);
             Link<R> u;
-            const unsigned mn = am ? (unsigned)am[(long long)(1 - p) * g.Vh + yh] : 0u;
-            lk_q.load(yh, a, u, ((mn >> a) & 1u) ? roff : 0);
+            lk_q.load(yh, a, u);
             mul_link_dag(u, hf, uh);
             R sc = (a == 3 && x[3] == 0) ? (R)g.bc * w : w;
             accumulate<R>(a, -1, uh, sc, acc);
@@ -122,38 +111,28 @@ template <class R, class SIn, class SX, class SOut, class LK, int MASK, int RED3
 __global__ void __launch_bounds__(sizeof(R) == 4 ? 256 : 128, sizeof(R) == 4 ? 3 : 0)
     hop_eo_kernel(HopArgs<SIn, SX, SOut, LK> A) {
     __shared__ double sh[34];
-    // right-hand sides along x when the launcher puts them fastest (the
-    // thread blocks of one site tile then run together and share the base
-    // links in L2), else along y
-    const bool rf = A.rhs_fast;
-    const int rhs = rf ? blockIdx.x : blockIdx.y;
-    const int part = rf ? blockIdx.y : blockIdx.x;
-    const int nparts = rf ? gridDim.y : gridDim.x;
+    const int rhs = blockIdx.y;
     if (A.st && !A.st[rhs].active) return;
     const long long Vh = A.g.Vh;
     const long long tile = (long long)blockDim.x * SPT;
     if (A.sites && threadIdx.x == 0)
-        atomicAdd(A.sites, (unsigned long long)min(tile, A.S.n - (long long)part * tile));
+        atomicAdd(A.sites, (unsigned long long)min(tile, A.S.n - (long long)blockIdx.x * tile));
     double v3[3] = {0.0, 0.0, 0.0};
     double nrm = 0.0;
 #pragma unroll
     for (int pass = 0; pass < SPT; ++pass) {
-        const long long t = (long long)part * tile + (long long)pass * blockDim.x + threadIdx.x;
+        const long long t = (long long)blockIdx.x * tile + (long long)pass * blockDim.x + threadIdx.x;
         if (t >= A.S.n) break;
         const int h = (int)A.S.at(t);
         const SIn in = at_rhs(A.in, rhs);
-        // with an active-bit table: base field + offset of this rhs's field
-        // (the base is A.lk_base, this rhs's field A.lk + rhs * stride)
-        LK lk = A.amask ? A.lk_base : A.lk;
-        const long long roff =
-            A.amask ? (long long)(A.lk.p - A.lk_base.p) + (long long)rhs * A.lk_rhs_stride : 0;
-        if (!A.amask) lk.p += (long long)rhs * A.lk_rhs_stride;
+        LK lk = A.lk;
+        lk.p += (long long)rhs * A.lk_rhs_stride;
         const LK lk_p = link_parity(lk, A.p, Vh);
         const LK lk_q = link_parity(lk, 1 - A.p, Vh);
         int x[4];
         eo_coords(A.g, A.p, h, x);
         Spinor<R> acc;
-        hop_site<R, SIn, LK, MASK>(A.g, A.p, h, x, in, lk_p, lk_q, A.amask, roff, A.g5in, acc);
+        hop_site<R, SIn, LK, MASK>(A.g, A.p, h, x, in, lk_p, lk_q, A.g5in, acc);
         if (A.g5out) gamma5(acc);
         Spinor<R> res, xv;
         const R bb = (R)A.b;
@@ -197,9 +176,9 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 256 : 128, sizeof(R) == 4 ? 3
         }
     }
     if (RED3) {
-        grid_reduce3(A.red, rhs, v3, sh, part, nparts);
+        grid_reduce3(A.red, rhs, v3, sh);
     } else if (A.red.op != FIN_NONE) {
-        grid_reduce(A.red, rhs, nrm, sh, part, nparts);
+        grid_reduce(A.red, rhs, nrm, sh);
     }
 }
 
@@ -224,9 +203,7 @@ inline void launch_hop(const HopArgs<SIn, SX, SOut, LK>& A, int nrhs, dd_handle*
     // kernel needs 130-150 registers for one site)
     constexpr int SPT2 = std::is_same<R, double>::value ? 1 : 2;
     const int spt = (!f64 && h->tune.hop_spt == 2) ? 2 : 1;
-    const int tiles = grid_for(B.S.n, (long long)tpb * spt);
-    B.rhs_fast = nrhs > 1 && tiles <= 65535;
-    dim3 grid = B.rhs_fast ? dim3(nrhs, tiles) : dim3(tiles, nrhs);
+    dim3 grid(grid_for(B.S.n, (long long)tpb * spt), nrhs);
     constexpr int kind = hop_kind<SIn, SOut>();
     bool timed = false;
     if (kind >= 0 && MASK == 0 && h->timer_on && !h->capturing && !dd_stream_capturing(h)) timed = (h->timer_seen[kind]++ % h->timer_every) == 0;

@@ -537,21 +537,6 @@ extern "C" int dd_init(dd_t* out, const dd_params* p, void* stream) {
         e = cudaMemcpy(h->d_active_links, links.data(), sizeof(int) * links.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_active_mask, act.size());
     if (e == cudaSuccess) e = cudaMemcpy(h->d_active_mask, act.data(), act.size(), cudaMemcpyHostToDevice);
-    {
-        // active bits per even-odd site: the hop kernels read the links of
-        // per-factor fields only where they can differ from the base field
-        std::vector<uint8_t> am((size_t)2 * g.Vh, 0);
-        for (int s = 0; s < g.V; ++s) {
-            int x[4];
-            G.coords(s, x);
-            const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
-            uint8_t m = 0;
-            for (int a = 0; a < 4; ++a) m |= (uint8_t)((act[4 * s + a] ? 1 : 0) << a);
-            am[(size_t)par * g.Vh + (s >> 1)] = m;
-        }
-        if (e == cudaSuccess) e = cudaMalloc(&h->d_amask_eo, am.size());
-        if (e == cudaSuccess) e = cudaMemcpy(h->d_amask_eo, am.data(), am.size(), cudaMemcpyHostToDevice);
-    }
     if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_hb_fails, sizeof(unsigned long long));
@@ -586,7 +571,6 @@ extern "C" int dd_init(dd_t* out, const dd_params* p, void* stream) {
     if (e != cudaSuccess) {
         cudaFree(h->d_active_links);
         cudaFree(h->d_active_mask);
-        cudaFree(h->d_amask_eo);
         cudaFree(h->d_status);
         cudaFree(h->d_hb_fails);
         cudaFree(h->d_sites);
@@ -727,7 +711,6 @@ extern "C" int dd_finalize(dd_t h) {
         for (cudaEvent_t e : h->timer_ev[k]) cudaEventDestroy(e);
     cudaFree(h->d_active_links);
     cudaFree(h->d_active_mask);
-    cudaFree(h->d_amask_eo);
     cudaFree(h->d_status);
     cudaFree(h->d_hb_fails);
     cudaFree(h->d_sites);

@@ -141,26 +141,20 @@ DD_DEV void finish3(const Reduce& R, int rhs, const double* s) {
     }
 }
 
-// Three-value variant: partials [rhs][nparts][3].  `sh` needs 34 doubles.
-// part / nparts: this thread block's index among the blocks of its rhs
-// (defaults: blockIdx.x of gridDim.x).
-DD_DEV void grid_reduce3(const Reduce& R, int rhs, const double* v, double* sh, int part = -1, int nparts = -1) {
-    if (part < 0) {
-        part = blockIdx.x;
-        nparts = gridDim.x;
-    }
+// Three-value variant: partials [rhs][gridDim.x][3].  `sh` needs 34 doubles.
+DD_DEV void grid_reduce3(const Reduce& R, int rhs, const double* v, double* sh) {
     double b[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) b[k] = block_sum(v[k], sh);
     int* last = reinterpret_cast<int*>(&sh[33]);
     if (threadIdx.x == 0) {
-        double* p = R.partials + ((long long)rhs * nparts + part) * 3;
+        double* p = R.partials + ((long long)rhs * gridDim.x + blockIdx.x) * 3;
         p[0] = b[0];
         p[1] = b[1];
         p[2] = b[2];
         __threadfence();
         unsigned t = atomicAdd(&R.counters[rhs], 1u);
-        *last = (t == (unsigned)nparts - 1);
+        *last = (t == gridDim.x - 1);
     }
     __syncthreads();
     if (*last) {
@@ -169,8 +163,8 @@ DD_DEV void grid_reduce3(const Reduce& R, int rhs, const double* v, double* sh, 
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             double a = 0.0;
-            for (int i = threadIdx.x; i < nparts; i += blockDim.x)
-                a += __ldcg(&R.partials[((long long)rhs * nparts + i) * 3 + k]);
+            for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x)
+                a += __ldcg(&R.partials[((long long)rhs * gridDim.x + i) * 3 + k]);
             s[k] = block_sum(a, sh);
         }
         if (threadIdx.x == 0) {
@@ -181,25 +175,21 @@ DD_DEV void grid_reduce3(const Reduce& R, int rhs, const double* v, double* sh, 
 }
 
 // Every thread of the block calls this with its contribution.  `sh` needs 34 doubles.
-DD_DEV void grid_reduce(const Reduce& R, int rhs, double v, double* sh, int part = -1, int nparts = -1) {
-    if (part < 0) {
-        part = blockIdx.x;
-        nparts = gridDim.x;
-    }
+DD_DEV void grid_reduce(const Reduce& R, int rhs, double v, double* sh) {
     double bsum = block_sum(v, sh);
     int* last = reinterpret_cast<int*>(&sh[33]);
     if (threadIdx.x == 0) {
-        R.partials[(long long)rhs * nparts + part] = bsum;
+        R.partials[(long long)rhs * gridDim.x + blockIdx.x] = bsum;
         __threadfence();
         unsigned t = atomicAdd(&R.counters[rhs], 1u);
-        *last = (t == (unsigned)nparts - 1);
+        *last = (t == gridDim.x - 1);
     }
     __syncthreads();
     if (*last) {
         __threadfence();
         double s = 0.0;
-        for (int i = threadIdx.x; i < nparts; i += blockDim.x)
-            s += __ldcg(&R.partials[(long long)rhs * nparts + i]);
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x)
+            s += __ldcg(&R.partials[(long long)rhs * gridDim.x + i]);
         s = block_sum(s, sh);
         if (threadIdx.x == 0) {
             finish(R, rhs, s);

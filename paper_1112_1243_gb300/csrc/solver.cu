@@ -233,8 +233,6 @@ struct NormalCG {
     CGState* st;
     const CGState* outer;
     SiteSet S;  // the sites of the solve (all even sites, or one block colour's)
-    LK lk_base;                       // shared base field of per-rhs fields (amask set)
-    const uint8_t* amask = nullptr;   // active bits: per-rhs links read only there
 
     Reduce red(int op) const {
         Reduce R_;
@@ -266,8 +264,6 @@ struct NormalCG {
         A.st = st;
         A.red = red(op);
         A.S = S;
-        A.lk_base = lk_base;
-        A.amask = amask;
         return A;
     }
     // z = Dtilde^dag r  (two hops), |z|^2 -> op
@@ -481,8 +477,6 @@ struct BiCGStab {
     CGState* st;
     const CGState* outer;
     SiteSet S;  // the sites of the solve (all even sites, or one block colour's)
-    LK lk_base;                       // shared base field of per-rhs fields (amask set)
-    const uint8_t* amask = nullptr;   // active bits: per-rhs links read only there
 
     Reduce red(int op) const {
         Reduce R_;
@@ -516,8 +510,6 @@ struct BiCGStab {
         A.red3 = red3;
         A.rhat = rhat;
         A.S = S;
-        A.lk_base = lk_base;
-        A.amask = amask;
         return A;
     }
     // out = Dtilde in_h (in_m: the same vector in master storage for the xpay term)
@@ -611,8 +603,7 @@ Reduce store_reduce(dd_handle* h, double* out) {
 // FP64 hop helper on eo FP64 vectors
 template <int MASK>
 void hop64(dd_handle* h, SiteSet S, int nrhs, int par, SpinorF64 in, SpinorF64 xin, SpinorF64 out, double a, double b,
-           int hasx, LinkF64 lk, long long lk_rs, const CGState* st, Reduce red, LinkF64 lk_base = LinkF64{},
-           const uint8_t* amask = nullptr) {
+           int hasx, LinkF64 lk, long long lk_rs, const CGState* st, Reduce red) {
     HopArgs<SpinorF64, SpinorF64, SpinorF64, LinkF64> A;
     A.g = h->g;
     A.p = par;
@@ -630,8 +621,6 @@ void hop64(dd_handle* h, SiteSet S, int nrhs, int par, SpinorF64 in, SpinorF64 x
     A.st = st;
     A.red = red;
     A.S = S;
-    A.lk_base = lk_base;
-    A.amask = amask;
     launch_hop<double, SpinorF64, SpinorF64, SpinorF64, LinkF64, MASK>(A, nrhs, h);
 }
 
@@ -663,9 +652,6 @@ int defect_correction(dd_handle* h, int nrhs, int field0, int step, Inner& cg, b
         t64b{v.t64b, Vh};
     LinkF64 lk64 = field_links<LinkF64>(h, field0);
     const long long rs64 = field_stride<LinkF64>(h, step);
-    // per-rhs fields share slot 0 outside the active links
-    const uint8_t* am = rs64 ? h->d_amask_eo : nullptr;
-    const LinkF64 base64 = field_links<LinkF64>(h, 0);
     CGState* outer = h->d_cg + h->prm.max_rhs;
     double* bb = h->d_scalars;
     double* tmp = h->d_scalars + nrhs;
@@ -677,7 +663,7 @@ int defect_correction(dd_handle* h, int nrhs, int field0, int step, Inner& cg, b
     DD_KLAUNCH(h, norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(S, be, store_reduce(h, bb)));
     DD_KLAUNCH(h, norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(S, bo, store_reduce(h, tmp)));
     DD_KLAUNCH(h, add_scalars_kernel<<<1, 64, 0, h->stream>>>(nrhs, bb, tmp));
-    hop64<MASK>(h, S, nrhs, 0, bo, be, be, 1.0, kappa, 1, lk64, rs64, nullptr, none, base64, am);
+    hop64<MASK>(h, S, nrhs, 0, bo, be, be, 1.0, kappa, 1, lk64, rs64, nullptr, none);
     DD_KLAUNCH(h, outer_arm_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, bb, tol));
     DD_KLAUNCH(h, zero64_kernel<<<grid, 128, 0, h->stream>>>(S, xe));
     DD_KLAUNCH(h, copy_kernel<SpinorF64, SpinorF64><<<grid, 128, 0, h->stream>>>(S, be, re, nullptr));
@@ -704,8 +690,8 @@ int defect_correction(dd_handle* h, int nrhs, int field0, int step, Inner& cg, b
         DD_KLAUNCH(h, add_correction_kernel<SM><<<grid, 128, 0, h->stream>>>(S, xe, cg.x, fp64_inner ? nullptr : rr,
                                                                           outer));
         // true residual r = b~ - Dtilde x (FP64)
-        hop64<MASK>(h, S, nrhs, 1, xe, xe, t64, 0.0, 1.0, 0, lk64, rs64, outer, none, base64, am);
-        hop64<MASK>(h, S, nrhs, 0, t64, xe, t64b, 1.0, -kappa * kappa, 1, lk64, rs64, outer, none, base64, am);
+        hop64<MASK>(h, S, nrhs, 1, xe, xe, t64, 0.0, 1.0, 0, lk64, rs64, outer, none);
+        hop64<MASK>(h, S, nrhs, 0, t64, xe, t64b, 1.0, -kappa * kappa, 1, lk64, rs64, outer, none);
         DD_KLAUNCH(h, residual_kernel<<<grid, 128, 0, h->stream>>>(S, be, t64b, re, outer, store_reduce(h, rr)));
         DD_KLAUNCH(h, outer_update_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, rr));
         return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
@@ -728,7 +714,7 @@ int defect_correction(dd_handle* h, int nrhs, int field0, int step, Inner& cg, b
     int rc = dd_loop(h, body, more, lc);
     if (rc) return rc;
     // x_o = b_o + kappa H_oe x_e
-    hop64<MASK>(h, S, nrhs, 1, xe, bo, xo, 1.0, kappa, 1, lk64, rs64, nullptr, none, base64, am);
+    hop64<MASK>(h, S, nrhs, 1, xe, bo, xo, 1.0, kappa, 1, lk64, rs64, nullptr, none);
     if (cudaGetLastError() != cudaSuccess) return DD_ERR_CUDA;
     if (!polled) {
         // captured: a solve that missed its target is reported in the status word
@@ -792,8 +778,6 @@ static int solve_packed_mask(dd_handle* h, SiteSet S, int nrhs, int field0, int 
         cg.copies = 0;
         cg.lk = field_links<LinkF64>(h, field0);
         cg.lk_rs = field_stride<LinkF64>(h, step);
-        cg.lk_base = field_links<LinkF64>(h, 0);
-        cg.amask = cg.lk_rs ? h->d_amask_eo : nullptr;
         cg.st = inner;
         cg.outer = outer;
         cg.S = S;
@@ -808,8 +792,6 @@ static int solve_packed_mask(dd_handle* h, SiteSet S, int nrhs, int field0, int 
             bi.copies = 0;
             bi.lk = field_links<LinkF32>(h, field0);
             bi.lk_rs = field_stride<LinkF32>(h, step);
-        bi.lk_base = field_links<LinkF32>(h, 0);
-        bi.amask = bi.lk_rs ? h->d_amask_eo : nullptr;
             bi.S = S;
             return defect_correction<MASK>(h, nrhs, field0, step, bi, false, tol, maxit, iters, relres);
         }
@@ -821,8 +803,6 @@ static int solve_packed_mask(dd_handle* h, SiteSet S, int nrhs, int field0, int 
         bi.copies = 1;
         bi.lk = field_links<LinkF16>(h, field0);
         bi.lk_rs = field_stride<LinkF16>(h, step);
-        bi.lk_base = field_links<LinkF16>(h, 0);
-        bi.amask = bi.lk_rs ? h->d_amask_eo : nullptr;
         bi.S = S;
         return defect_correction<MASK>(h, nrhs, field0, step, bi, false, tol, maxit, iters, relres);
     } else if (prec == DD_PREC_F32) {
@@ -840,8 +820,6 @@ static int solve_packed_mask(dd_handle* h, SiteSet S, int nrhs, int field0, int 
         cg.copies = 0;
         cg.lk = field_links<LinkF32>(h, field0);
         cg.lk_rs = field_stride<LinkF32>(h, step);
-        cg.lk_base = field_links<LinkF32>(h, 0);
-        cg.amask = cg.lk_rs ? h->d_amask_eo : nullptr;
         cg.st = inner;
         cg.outer = outer;
         cg.S = S;
@@ -861,8 +839,6 @@ static int solve_packed_mask(dd_handle* h, SiteSet S, int nrhs, int field0, int 
         cg.copies = 1;
         cg.lk = field_links<LinkF16>(h, field0);
         cg.lk_rs = field_stride<LinkF16>(h, step);
-        cg.lk_base = field_links<LinkF16>(h, 0);
-        cg.amask = cg.lk_rs ? h->d_amask_eo : nullptr;
         cg.st = inner;
         cg.outer = outer;
         cg.S = S;
