@@ -91,6 +91,8 @@ extern "C" {
 /* estimator modes (Eq. param) */
 #define DD_EST_FACTORS 0  /* factor i uses U_i, U_{i+1} of the geodesic path, its own eta_i */
 #define DD_EST_REPLICAS 1 /* every factor uses (U, U'), its own eta_i (variance measurement) */
+#define DD_EST_INTERP_ALL 4 /* flag: interpolate every link that differs between U and U' (after a
+                               relative gauge fixing), not only the active links */
 
 /* block filter modes (Eq. 4step, step 1) */
 #define DD_FILTER_STOCHASTIC 0
@@ -247,6 +249,19 @@ int dd_block_filter(dd_t h, const void* U_old, void* U_new, int colour_mask, int
 int dd_block_schur_filter(dd_t h, const void* U_old, void* U_new, int colour_mask, int n, uint64_t seed,
                           uint64_t ctr, double* ln_b, uint8_t* accept);
 
+/* Relative gauge fixing (Sec. 4: reduces the variance of the eigenvalue
+ * distribution of M^dag M; the paper does not state the method): U_new is
+ * replaced in place by U_new^g, g(x) in SU(3), g_a(x) U_new_a(x) g(x+a)^dag,
+ * with g raising F[g] = sum_{x,a} Re tr(U_a(x)^dag g(x) U_new_a(x) g(x+a)^dag)
+ * from g = 1 by `sweeps` sweeps (sites of even, then odd parity; at each site
+ * one Cabibbo-Marinari pass over the SU(2) subgroups (0,1), (1,2), (0,2)
+ * maximising Re tr(g W) with W the sum of the eight link products through
+ * the site).  Determinant ratios are unchanged (gauge invariance); the fixed
+ * field differs from U on more than the active links, so its estimate needs
+ * DD_EST_INTERP_ALL.  functional (device, 1 double, may be NULL) receives
+ * F at the final g.  U, U_new: device gauge fields. */
+int dd_relative_gauge_fix(dd_t h, const void* U, void* U_new, int sweeps, double* functional);
+
 /* The block filter of several lattices at once (Eq. 4step step 1): every
  * (block, factor) solve of all nh handles runs in ONE persistent launch, the
  * items of the largest blocks first; blocks may differ in shape between the
@@ -357,6 +372,9 @@ int dd_block_ratios_noalloc(const int dims[4], const int block[4], double kappa,
  * With sub-blocks (one level of recursion) every iteration runs step 0,
  * step 1 on the sub-blocks and, when n_schur > 0, step 2 on the blocks
  * (dd_block_schur_filter, same counter), before U <- Up.
+ * With gauge_fix_sweeps > 0 the global step estimates the ratio for the
+ * proposal fixed to U0 (dd_relative_gauge_fix into Up, DD_EST_INTERP_ALL);
+ * U itself keeps the unfixed proposal (the ratio is the same).
  * Counters: step << 20 | iteration << 4 | pass for the proposal and filter,
  * step << 20 | n_inner << 4 for the global step (step < 2^40).
  * U: device gauge field, updated in place.  All buffers are caller-owned
@@ -375,6 +393,8 @@ typedef struct dd_chain_params {
     int colour_passes; /* 1 or 2 */
     int n_schur;       /* factors of the block Schur filter (step 2; handles with sub-blocks; 0 = skip) */
     uint64_t seed;
+    int gauge_fix_sweeps; /* > 0: relative gauge fixing of the proposal before the global estimate */
+    int reserved;
 } dd_chain_params;
 typedef struct dd_chain_buffers {
     void* U0;

@@ -16,7 +16,7 @@ ctr = step << 20 | n_inner << 4 for the global step.
 """
 import numpy as np
 
-from . import accept, estimator, heatbath
+from . import accept, estimator, gaugefix, heatbath
 
 
 def counter(step, iteration, colour_pass):
@@ -28,7 +28,7 @@ def colour_passes(lat):
 
 
 def hierarchical_step(U, lat, kappa, beta, n_inner, n_block, n_global, seed, step, filter_mode="stochastic",
-                      n_or=0, tol=1e-14):
+                      n_or=0, tol=1e-14, gauge_fix_sweeps=0):
     """One global step.  Returns (U_next, record) with the block decisions, the
     per-factor global log-ratios and the global decision."""
     U0 = np.array(U, copy=True)
@@ -46,7 +46,14 @@ def hierarchical_step(U, lat, kappa, beta, n_inner, n_block, n_global, seed, ste
             rec["block"].append((ln_b, acc, lu))
             Ucur = accept.restore_rejected_blocks(Up, Ucur, lat, acc)
     ctr = counter(step, n_inner, 0)
-    ln = estimator.det_ratio_estimate(U0, Ucur, lat, kappa, n_global, seed, ctr, tol=tol)
+    if gauge_fix_sweeps > 0:
+        # the ratio of the proposal fixed relative to U0 (gauge invariant);
+        # the interpolation then runs over every link that differs
+        _, Ug, _ = gaugefix.relative_gauge_fix(U0, Ucur, lat, gauge_fix_sweeps)
+        ln = estimator.det_ratio_estimate(U0, Ug, lat, kappa, n_global, seed, ctr, tol=tol,
+                                          interp_mask=gaugefix.differing_links(U0, Ug))
+    else:
+        ln = estimator.det_ratio_estimate(U0, Ucur, lat, kappa, n_global, seed, ctr, tol=tol)
     ok, lu = accept.global_accept(float(np.sum(ln)), seed, ctr)
     rec.update(ln_global=ln, accept=ok, ln_u=lu)
     return (Ucur if ok else U0), rec

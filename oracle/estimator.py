@@ -112,18 +112,21 @@ def global_noise(lat, factor, seed, ctr):
     return eta
 
 
-def det_ratio_estimate(U, Up, lat, kappa, n, seed, ctr, mode="factors", tol=1e-14, dense=False):
+def det_ratio_estimate(U, Up, lat, kappa, n, seed, ctr, mode="factors", tol=1e-14, dense=False, interp_mask=None):
     """Per-factor ln r_i of the global (Schur complement) step, length n.
 
     mode "factors": factor i uses U_i, U_{i+1} of the n-step interpolation and
     its own eta_i.  mode "replicas": every factor uses the pair (U, U') with
-    its own eta_i (the variance measurement of Sec. 5).
+    its own eta_i (the variance measurement of Sec. 5).  interp_mask: the
+    links the interpolation runs over (default: the active links; after a
+    relative gauge fixing: every link that differs).
     """
+    mask = lat.active if interp_mask is None else interp_mask
     out = np.empty(n)
     for i in range(n):
         if mode == "factors":
-            Ui = interpolate(U, Up, i / n, lat.active)
-            Uj = interpolate(U, Up, (i + 1) / n, lat.active)
+            Ui = interpolate(U, Up, i / n, mask)
+            Uj = interpolate(U, Up, (i + 1) / n, mask)
         else:
             Ui, Uj = U, Up
         eta = global_noise(lat, i, seed, ctr)

@@ -30,7 +30,7 @@ DD_PURPOSE_GLOBAL_ACCEPT = 6
 DD_PURPOSE_USER_NOISE = 7
 DD_PURPOSE_BLOCK_SCHUR_NOISE = 4
 DD_PURPOSE_BLOCK_SCHUR_ACCEPT = 8
-DD_EST_FACTORS, DD_EST_REPLICAS = 0, 1
+DD_EST_FACTORS, DD_EST_REPLICAS, DD_EST_INTERP_ALL = 0, 1, 4
 DD_FILTER_STOCHASTIC, DD_FILTER_EXACT = 0, 1
 
 ERROR_NAMES = {
@@ -76,6 +76,8 @@ class dd_chain_params(ctypes.Structure):
         ("colour_passes", ctypes.c_int),
         ("n_schur", ctypes.c_int),
         ("seed", ctypes.c_uint64),
+        ("gauge_fix_sweeps", ctypes.c_int),
+        ("reserved", ctypes.c_int),
     ]
 
 
@@ -117,6 +119,7 @@ SIGNATURES = {
     "dd_det_ratio_estimate": [_P, _P, _P, _I, _U64, _U64, _I, _P],
     "dd_block_filter": [_P, _P, _P, _I, _I, _I, _U64, _U64, _P, _P],
     "dd_block_schur_filter": [_P, _P, _P, _I, _I, _U64, _U64, _P, _P],
+    "dd_relative_gauge_fix": [_P, _P, _P, _I, _P],
     "dd_block_filter_batch_workspace": [_I, _P, _I, ctypes.POINTER(ctypes.c_size_t)],
     "dd_block_filter_batch": [_I, _P, _P, _P, _I, _I, _U64, _U64, _P, _P, _P, ctypes.c_size_t],
     "dd_gauge_update": [_P, _P, _I, _D, _I, _I, _U64, _U64],

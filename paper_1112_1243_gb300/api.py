@@ -190,6 +190,11 @@ def dd_block_schur_filter(h, U_old, U_new, colour_mask, n, seed, ctr, ln_b=None,
     return ln_b, accept
 
 
+def dd_relative_gauge_fix(h, U, U_new, sweeps, functional=None):
+    """U_new <- U_new^g with g raising sum Re tr(U^dag g U_new g^dag) (in place)."""
+    return _check(h, _lib.load().dd_relative_gauge_fix(h.ptr, _ptr(U), _ptr(U_new), int(sweeps), _ptr(functional)))
+
+
 def dd_block_filter_batch(hs, U_olds, U_news, colour_mask, n, seed, ctr, ln_bs=None, accepts=None):
     """Block filters of several handles (lattices, block shapes) in one persistent launch."""
     lib = _lib.load()

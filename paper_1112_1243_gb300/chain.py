@@ -26,10 +26,12 @@ class HierarchicalStep:
     1 and 2 (black, white) when the active set is "intra", one pass otherwise.
     On a handle with sub-blocks, n_schur > 0 adds the blocks' Schur filter
     (Eq. 4step step 2) after the sub-block filter of every iteration.
+    gauge_fix_sweeps > 0 fixes the proposal relative to the old field before
+    the global estimate (Sec. 4).
     """
 
     def __init__(self, h, beta, n_inner=1, n_block=4, n_global=12, n_or=0, seed=1,
-                 filter_mode=api.DD_FILTER_STOCHASTIC, intra=False, n_schur=0):
+                 filter_mode=api.DD_FILTER_STOCHASTIC, intra=False, n_schur=0, gauge_fix_sweeps=0):
         self.h = h
         self.beta = float(beta)
         self.n_inner = int(n_inner)
@@ -62,6 +64,7 @@ class HierarchicalStep:
         self.params.filter_mode = self.filter_mode
         self.params.colour_passes = len(self.passes)
         self.params.n_schur = self.n_schur
+        self.params.gauge_fix_sweeps = int(gauge_fix_sweeps)
         self.params.seed = self.seed
         self.buffers = {"U0": self.U0, "Up": self.Up, "ln_b": self.ln_b, "acc_b": self.acc_b, "ln_g": self.ln_g,
                         "acc_g": self.acc_g, "margin": self.margin, "ln_bs": self.ln_bs, "acc_bs": self.acc_bs}

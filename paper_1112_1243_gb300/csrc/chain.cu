@@ -21,6 +21,7 @@ extern "C" int dd_chain_step(dd_t h, void* U, const dd_chain_params* p, const dd
     if (!U || !p || !b || !b->U0 || !b->Up || !b->ln_b || !b->acc_b || !b->ln_g || !b->acc_g || !b->margin)
         return dd_fail(h, DD_ERR_INVALID_ARG, "dd_chain_step: null argument");
     if (p->n_inner < 0 || p->n_block < 1 || p->n_global < 1 || p->n_hb < 0 || p->n_or < 0 || p->n_schur < 0 ||
+        p->gauge_fix_sweeps < 0 ||
         (p->colour_passes != 1 && p->colour_passes != 2) || step >= (1ull << 40))
         return dd_fail(h, DD_ERR_INVALID_ARG, "dd_chain_step: bad parameters");
     if (h->has_sub && p->n_schur > 0 && (!b->ln_bs || !b->acc_bs))
@@ -50,7 +51,16 @@ extern "C" int dd_chain_step(dd_t h, void* U, const dd_chain_params* p, const dd
         }
     }
     const uint64_t ctr = (step << 20) | ((uint64_t)p->n_inner << 4);
-    rc = dd_det_ratio_estimate(h, b->U0, U, p->n_global, p->seed, ctr, DD_EST_FACTORS, b->ln_g);
+    if (p->gauge_fix_sweeps > 0) {
+        // the same ratio for the proposal fixed relative to U0 (Sec. 4)
+        DD_CUDA(h, cudaMemcpyAsync(b->Up, U, bytes, cudaMemcpyDeviceToDevice, h->stream));
+        rc = dd_relative_gauge_fix(h, b->U0, b->Up, p->gauge_fix_sweeps, nullptr);
+        if (rc) return rc;
+        rc = dd_det_ratio_estimate(h, b->U0, b->Up, p->n_global, p->seed, ctr, DD_EST_FACTORS | DD_EST_INTERP_ALL,
+                                   b->ln_g);
+    } else {
+        rc = dd_det_ratio_estimate(h, b->U0, U, p->n_global, p->seed, ctr, DD_EST_FACTORS, b->ln_g);
+    }
     if (rc) return rc;
     return dd_global_accept(h, U, b->U0, b->ln_g, p->n_global, p->seed, ctr, b->acc_g, b->margin);
 }

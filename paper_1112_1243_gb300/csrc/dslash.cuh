@@ -108,7 +108,7 @@ DD_DEV void hop_site(const Geo& g, int p, int h, const int x[4], const SIn& in, 
 // set (SPT passes of blockDim.x threads; thread block size and SPT are
 // chosen by the autotuner, see dd_autotune).
 template <class R, class SIn, class SX, class SOut, class LK, int MASK, int RED3, int SPT>
-__global__ void __launch_bounds__(sizeof(R) == 4 ? 256 : 128, sizeof(R) == 4 ? 3 : 0)
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 7 : 0)
     hop_eo_kernel(HopArgs<SIn, SX, SOut, LK> A) {
     __shared__ double sh[34];
     const int rhs = blockIdx.y;

@@ -24,7 +24,8 @@
 #include "dslash.cuh"
 #include "solver.h"
 
-int launch_interpolate(dd_handle* h, const double* U, const double* Up, double* out, int num, int den);
+int launch_interpolate(dd_handle* h, const double* U, const double* Up, double* out, int num, int den,
+                       bool all_links);
 
 namespace {
 
@@ -272,14 +273,15 @@ static BlockCtx block_ctx(dd_handle* h) {
 }
 
 // format slots 0..nslots-1 from interpolated (or copied) fields
-static int prepare_fields(dd_handle* h, const double* U_old, const double* U_new, int n, bool factors, bool eo) {
+static int prepare_fields(dd_handle* h, const double* U_old, const double* U_new, int n, bool factors, bool eo,
+                          bool all_links = false) {
     const int nslots = factors ? n + 1 : 2;
     const int ip = h->prm.inner_prec;
     for (int k = 0; k < nslots; ++k) {
         FieldSlot& f = h->fields[k];
         int num = factors ? k : (k == 0 ? 0 : 1);
         int den = factors ? n : 1;
-        int rc = launch_interpolate(h, U_old, U_new, (double*)f.canon, num, den);
+        int rc = launch_interpolate(h, U_old, U_new, (double*)f.canon, num, den, all_links);
         if (rc) return rc;
         bool need_eo = eo;  // old and new fields both enter even-odd solves
         rc = format_field(h, (const double*)f.canon, f, need_eo, need_eo && ip == DD_PREC_F32,
@@ -814,10 +816,12 @@ extern "C" int dd_det_ratio_estimate(dd_t h, const void* U_old, const void* U_ne
     if (rc) return rc;
     rc = dd_require_feature(h, h->feat_estimate, "dd_det_ratio_estimate");
     if (rc) return rc;
+    const bool all_links = (mode & DD_EST_INTERP_ALL) != 0;
+    mode &= ~DD_EST_INTERP_ALL;
     if (!U_old || !U_new || !ln_out || n < 1 || n > h->prm.max_rhs || (mode != DD_EST_FACTORS && mode != DD_EST_REPLICAS))
         return dd_fail(h, DD_ERR_INVALID_ARG, "dd_det_ratio_estimate: bad arguments");
     const bool factors = mode == DD_EST_FACTORS;
-    rc = prepare_fields(h, (const double*)U_old, (const double*)U_new, n, factors, true);
+    rc = prepare_fields(h, (const double*)U_old, (const double*)U_new, n, factors, true, all_links);
     if (rc) return rc;
     const Geo& g = h->g;
     const BlockCtx c = block_ctx(h);

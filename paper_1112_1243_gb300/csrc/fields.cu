@@ -39,7 +39,7 @@ __global__ void interpolate_kernel(long long nlinks, const double* __restrict__ 
     const double* a = U + l * 18;
     const double* b = Up + l * 18;
     double* o = out + l * 18;
-    if (!active[l] || num == 0) {
+    if ((active && !active[l]) || num == 0) {
         for (int k = 0; k < 18; ++k) o[k] = a[k];
         return;
     }
@@ -60,9 +60,13 @@ __global__ void interpolate_kernel(long long nlinks, const double* __restrict__ 
     store_m3(o, mul(u, wt));
 }
 
-int launch_interpolate(dd_handle* h, const double* U, const double* Up, double* out, int num, int den) {
+// all_links: interpolate every link that differs (after a relative gauge
+// fixing), else the active links only (the rest is taken from U)
+int launch_interpolate(dd_handle* h, const double* U, const double* Up, double* out, int num, int den,
+                       bool all_links) {
     const long long n = (long long)h->g.V * 4;
-    DD_KLAUNCH(h, interpolate_kernel<<<grid_for(n, 128), 128, 0, h->stream>>>(n, U, Up, h->d_active_mask, out, num, den));
+    DD_KLAUNCH(h, interpolate_kernel<<<grid_for(n, 128), 128, 0, h->stream>>>(n, U, Up, all_links ? nullptr : h->d_active_mask,
+                                                                              out, num, den));
     DD_LAUNCH_CHECK(h, "interpolate_kernel");
     return DD_OK;
 }
@@ -71,7 +75,7 @@ extern "C" int dd_interpolate(dd_t h, void* U_t, const void* U, const void* U_ne
     int rc = dd_require_ws(h);
     if (rc) return rc;
     if (!U_t || !U || !U_new || n < 1 || i < 0 || i > n) return dd_fail(h, DD_ERR_INVALID_ARG, "dd_interpolate: bad arguments");
-    return launch_interpolate(h, (const double*)U, (const double*)U_new, (double*)U_t, i, n);
+    return launch_interpolate(h, (const double*)U, (const double*)U_new, (double*)U_t, i, n, false);
 }
 
 // ---------------------------------------------------------------- plaquette

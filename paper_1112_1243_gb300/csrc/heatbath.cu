@@ -14,6 +14,7 @@
 #include <cmath>
 
 #include "dd_internal.h"
+#include "reduce.cuh"
 #include "su3.cuh"
 
 namespace {
@@ -130,7 +131,108 @@ __global__ void heatbath_kernel(Geo g, double* U, const int* links, int n, doubl
     if (nf) atomicAdd(fails, nf);
 }
 
+// ------------------------------------------------ relative gauge fixing
+// Sec. 4 (relative gauge fixing of the proposal to the current field; the
+// method is not stated there): maximise F[g] = sum Re tr(U_a(x)^dag g(x)
+// U'_a(x) g(x+a)^dag) by sweeps over the sites of one parity at a time; at
+// site x, F = Re tr(g(x) W(x)) + const with
+//   W(x) = sum_a [U'_a(x) g(x+a)^dag U_a(x)^dag + (U_a(x-a)^dag g(x-a) U'_a(x-a))^dag],
+// raised by one Cabibbo-Marinari pass: for subgroup (i,j) the 2x2 block of
+// g W is k V (V in SU(2)) plus a part that does not contribute, and
+// g <- V^dag_emb g.  G: one SU(3) matrix per site (18 doubles).
+__global__ void gauge_identity_kernel(long long V, double* G) {
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < V) store_m3(G + s * 18, identity3());
+}
+
+__global__ void __launch_bounds__(128) gauge_fix_kernel(Geo g, const double* __restrict__ U,
+                                                        const double* __restrict__ Up, double* G, int par) {
+    const int hh = blockIdx.x * blockDim.x + threadIdx.x;
+    if (hh >= g.Vh) return;
+    int x[4];
+    eo_coords(g, par, hh, x);
+    const int s = canon_index(g, x);
+    M3 W;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) W.m[i][j] = mk<double>(0, 0);
+    for (int a = 0; a < 4; ++a) {
+        const int y = shift_index(g, x, a, +1);
+        const int z = shift_index(g, x, a, -1);
+        // U'_a(x) g(x+a)^dag U_a(x)^dag
+        W = add(W, mul_dag_right(mul_dag_right(link_at(Up, s, a), load_m3(G + (long long)y * 18)), link_at(U, s, a)));
+        // (U_a(z)^dag g(z) U'_a(z))^dag = U'_a(z)^dag g(z)^dag U_a(z)
+        W = add(W, mul(mul_dag_left(link_at(Up, z, a), dagger(load_m3(G + (long long)z * 18))), link_at(U, z, a)));
+    }
+    M3 gx = load_m3(G + (long long)s * 18);
+    const int SG[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+    for (int sg = 0; sg < 3; ++sg) {
+        const int i = SG[sg][0], j = SG[sg][1];
+        M3 M = mul(gx, W);
+        double a0 = 0.5 * (M.m[i][i].x + M.m[j][j].x);
+        double a3 = 0.5 * (M.m[i][i].y - M.m[j][j].y);
+        double a2 = 0.5 * (M.m[i][j].x - M.m[j][i].x);
+        double a1 = 0.5 * (M.m[i][j].y + M.m[j][i].y);
+        double k = sqrt(a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3);
+        if (!(k > 1e-300)) continue;
+        M2 R = dag2(su2(a0 / k, a1 / k, a2 / k, a3 / k));
+        for (int c = 0; c < 3; ++c) {
+            cpx<double> gi = gx.m[i][c], gj = gx.m[j][c];
+            gx.m[i][c] = cmul(R.m[0][0], gi) + cmul(R.m[0][1], gj);
+            gx.m[j][c] = cmul(R.m[1][0], gi) + cmul(R.m[1][1], gj);
+        }
+    }
+    store_m3(G + (long long)s * 18, gx);
+}
+
+// U'_a(x) <- g(x) U'_a(x) g(x+a)^dag (every link), and the functional
+// sum Re tr(U^dag U'^g) accumulated into *F (may be null)
+__global__ void __launch_bounds__(128) gauge_apply_kernel(Geo g, const double* __restrict__ U, const double* G,
+                                                          double* Up, Reduce red) {
+    __shared__ double sh[34];
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double f = 0.0;
+    if (s < g.V) {
+        int x[4];
+        canon_coords(g, s, x);
+        const M3 gs = load_m3(G + (long long)s * 18);
+        for (int a = 0; a < 4; ++a) {
+            const int y = shift_index(g, x, a, +1);
+            M3 v = mul_dag_right(mul(gs, link_at(Up, s, a)), load_m3(G + (long long)y * 18));
+            store_m3(Up + ((long long)s * 4 + a) * 18, v);
+            M3 t = mul_dag_left(link_at(U, s, a), v);
+            f += t.m[0][0].x + t.m[1][1].x + t.m[2][2].x;
+        }
+    }
+    if (red.op != FIN_NONE) grid_reduce(red, 0, f, sh);
+}
+
 }  // namespace
+
+extern "C" int dd_relative_gauge_fix(dd_t h, const void* U, void* U_new, int sweeps, double* functional) {
+    int rc = dd_require_ws(h);
+    if (rc) return rc;
+    rc = dd_require_feature(h, h->feat_estimate, "dd_relative_gauge_fix");
+    if (rc) return rc;
+    if (!U || !U_new || sweeps < 0 || sweeps > 10000) return dd_fail(h, DD_ERR_INVALID_ARG, "dd_relative_gauge_fix: bad arguments");
+    const Geo& g = h->g;
+    double* G = h->d_gauge_g;
+    DD_KLAUNCH(h, gauge_identity_kernel<<<grid_for(g.V, 128), 128, 0, h->stream>>>(g.V, G));
+    for (int k = 0; k < sweeps; ++k)
+        for (int par = 0; par < 2; ++par)
+            DD_KLAUNCH(h, gauge_fix_kernel<<<grid_for(g.Vh, 128), 128, 0, h->stream>>>(g, (const double*)U,
+                                                                                   (const double*)U_new, G, par));
+    Reduce red;
+    red.partials = h->d_partials;
+    red.counters = h->d_counters;
+    red.st = nullptr;
+    red.out = functional;
+    red.op = functional ? FIN_STORE : FIN_NONE;
+    red.status = h->d_status;
+    DD_KLAUNCH(h, gauge_apply_kernel<<<grid_for(g.V, 128), 128, 0, h->stream>>>(g, (const double*)U, G,
+                                                                              (double*)U_new, red));
+    DD_LAUNCH_CHECK(h, "dd_relative_gauge_fix");
+    return DD_OK;
+}
 
 extern "C" int dd_gauge_update(dd_t h, void* U, int colour_mask, double beta, int n_hb, int n_or, uint64_t seed,
                                uint64_t ctr) {

@@ -400,6 +400,7 @@ void plan(dd_handle* h, char* base) {
     h->d_item_out = c.take<double>((size_t)h->items_cap);
     h->d_queue = c.take<int>(64);
     h->d_imap = c.take<int>((size_t)h->g.nblocks + 4 * R + 64);
+    h->d_gauge_g = c.take<double>(est ? (size_t)V * 18 : 0);
     // dense LU matrices of the exact check path: D, the augmented block
     // systems and Dhat of lattices up to 512 sites (at most 3 (12V)^2
     // complex), or the batch of block operators of small blocks

@@ -52,26 +52,29 @@ def thermalise(api, dims, block, beta, sweeps, n_or, seed, U, device=None):
     return float(plaq.item())
 
 
-def sample_ln_ratios(api, h, U, beta, N, samples, seed, offset=0):
-    """Sum over N factors of ln r_i for `samples` proposals (one heat-bath
-    sweep on the active links of U, a fresh proposal and fresh noise per
-    sample); U is not changed."""
+def sample_ln_ratios(api, h, U, beta, N, samples, seed, offset=0, n_block=4):
+    """Sum over N factors of ln r_i of the global step for `samples`
+    proposals: one heat-bath sweep on the active links of U followed by the
+    block filter (n_block factors; rejected blocks restored), as the global
+    step sees them (Sec. 5); a fresh proposal and fresh noise per sample.
+    U is not changed."""
     out = []
     for s in range(samples):
         ctr = ((offset + s) << 20) | N
         Up = U.clone()
         api.dd_gauge_update(h, Up, 3, beta, 1, 0, seed, ctr)
+        api.dd_block_filter(h, U, Up, 3, api.DD_FILTER_STOCHASTIC, n_block, seed, ctr)
         ln = api.dd_det_ratio_estimate(h, U, Up, N, seed, ctr, api.DD_EST_FACTORS)
         out.append(float(ln.sum().item()))
     return np.array(out)
 
 
-def variance_scan(api, h, U, beta, Ns, samples, seed):
+def variance_scan(api, h, U, beta, Ns, samples, seed, n_block=4):
     """sigma^2(N) of the global step for every N, the 1/N extrapolation and
     the acceptance rates (estimated and exact)."""
     rows = []
     for N in Ns:
-        x = sample_ln_ratios(api, h, U, beta, N, samples, seed, offset=1000 * N)
+        x = sample_ln_ratios(api, h, U, beta, N, samples, seed, offset=1000 * N, n_block=n_block)
         rows.append({"N": int(N), "var": float(np.var(x, ddof=1)), "mean": float(np.mean(x)),
                      "acceptance_mc": float(np.mean(np.minimum(1.0, np.exp(x))))})
     a, b = fit_inverse_n([r["N"] for r in rows], [r["var"] for r in rows])
@@ -95,7 +98,7 @@ def main():
     dev = torch.device("cuda", 0)
     U = torch.from_numpy(synthetic.unit_gauge(args.dims)).to(dev)
     plaq = thermalise(api, args.dims, args.block, args.beta, args.therm, 2, args.seed, U, device=dev)
-    h = api.dd_init(args.dims, args.block, args.kappa, max_rhs=max(args.Ns), inner_prec=api.DD_PREC_F16,
+    h = api.dd_init(args.dims, args.block, args.kappa, max_rhs=max(max(args.Ns), 4), inner_prec=api.DD_PREC_F16,
                     krylov=api.DD_KRYLOV_BICGSTAB, maxit=100000, device=dev)
     res = variance_scan(api, h, U, args.beta, args.Ns, args.samples, args.seed)
     res.update(dims=args.dims, block=args.block, beta=args.beta, kappa=args.kappa, plaquette=plaq,

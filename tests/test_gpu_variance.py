@@ -36,7 +36,7 @@ def test_variance_scan_small(api):
     plaq = variance.thermalise(api, dims, block, 5.8, 20, 1, 5, U)
     assert 0.3 < plaq < 1.0
     h = api.dd_init(dims, block, 0.13, max_rhs=2, inner_prec=api.DD_PREC_F16, krylov=api.DD_KRYLOV_BICGSTAB)
-    res = variance.variance_scan(api, h, U, 5.8, [1, 2], 4, 7)
+    res = variance.variance_scan(api, h, U, 5.8, [1, 2], 4, 7, n_block=2)
     assert len(res["rows"]) == 2
     for r in res["rows"]:
         assert np.isfinite(r["var"]) and r["var"] >= 0
