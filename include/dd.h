@@ -454,7 +454,7 @@ int dd_graph_destroy(dd_graph_t graph);
  * NULL) receives the chosen shapes and the average launch times (ms) of the
  * chosen and of the default shapes (0 when taken from the cache).  Runs
  * kernels and synchronises the stream; not allowed inside a capture.
- * dd_set_tuning sets the shapes directly (threads 64, 128 or 256 and 1 or 2
+ * dd_set_tuning sets the shapes directly (threads 64 or 128 and 1 or 2
  * sites per thread for the FP16/FP32 hops; 64 or 128 threads and 1 site per
  * thread for the FP64 hops; 64, 128 or 256 threads and 1..4 blocks per SM
  * for the block solver; filter_masked 0 = persistent block-filter launch,

@@ -10,6 +10,7 @@
 // U_a(x - a) stored at the neighbour (parity 1 - p).
 #pragma once
 
+#include <algorithm>
 #include <type_traits>
 
 #include "dd_internal.h"
@@ -198,7 +199,7 @@ inline void launch_hop(const HopArgs<SIn, SX, SOut, LK>& A, int nrhs, dd_handle*
     // tile shape from the handle's tuning (threads x sites per thread >= 64,
     // which keeps the grid within the reduction partials)
     const bool f64 = std::is_same<R, double>::value;
-    const int tpb = f64 ? h->tune.hop64_tpb : h->tune.hop_tpb;
+    const int tpb = std::min(f64 ? h->tune.hop64_tpb : h->tune.hop_tpb, 128);  // the kernels' launch bound
     // two sites per thread only for the FP32-arithmetic kernels (the FP64
     // kernel needs 130-150 registers for one site)
     constexpr int SPT2 = std::is_same<R, double>::value ? 1 : 2;

@@ -100,7 +100,7 @@ struct Shape {
 };
 // thread-block size x sites per thread >= 64 keeps every grid within the
 // reduction partials planned for 64-site tiles
-const Shape kHopShapes[] = {{128, 1}, {256, 1}, {64, 1}, {128, 2}, {256, 2}, {64, 2}};
+const Shape kHopShapes[] = {{128, 1}, {64, 1}, {128, 2}, {64, 2}};
 const Shape kHop64Shapes[] = {{128, 1}, {64, 1}};
 const Shape kBlockShapes[] = {{256, 2}, {256, 1}, {128, 2}, {128, 4}, {64, 4}};
 
@@ -269,7 +269,7 @@ extern "C" int dd_set_tuning(dd_t h, int hop_tpb, int hop_spt, int hop64_tpb, in
     auto ok_shape = [](int tpb, int spt, int max_tpb) {
         return (tpb == 64 || tpb == 128 || tpb == 256) && tpb <= max_tpb && (spt == 1 || spt == 2);
     };
-    if (!ok_shape(hop_tpb, hop_spt, 256) || !ok_shape(hop64_tpb, hop64_spt, 128) || hop64_spt != 1 ||
+    if (!ok_shape(hop_tpb, hop_spt, 128) || !ok_shape(hop64_tpb, hop64_spt, 128) || hop64_spt != 1 ||
         !(block_tpb == 64 || block_tpb == 128 || block_tpb == 256) || block_ctas_per_sm < 1 ||
         block_ctas_per_sm > DD_BLOCK_CTAS_MAX || (filter_masked != 0 && filter_masked != 1))
         return dd_fail(h, DD_ERR_INVALID_ARG, "dd_set_tuning: shape out of range");
