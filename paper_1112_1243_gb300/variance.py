@@ -56,14 +56,15 @@ def sample_ln_ratios(api, h, U, beta, N, samples, seed, offset=0, n_block=4):
     """Sum over N factors of ln r_i of the global step for `samples`
     proposals: one heat-bath sweep on the active links of U followed by the
     block filter (n_block factors; rejected blocks restored), as the global
-    step sees them (Sec. 5); a fresh proposal and fresh noise per sample.
-    U is not changed."""
+    step sees them (Sec. 5), or the raw proposal for n_block = 0; a fresh
+    proposal and fresh noise per sample.  U is not changed."""
     out = []
     for s in range(samples):
         ctr = ((offset + s) << 20) | N
         Up = U.clone()
         api.dd_gauge_update(h, Up, 3, beta, 1, 0, seed, ctr)
-        api.dd_block_filter(h, U, Up, 3, api.DD_FILTER_STOCHASTIC, n_block, seed, ctr)
+        if n_block > 0:
+            api.dd_block_filter(h, U, Up, 3, api.DD_FILTER_STOCHASTIC, n_block, seed, ctr)
         ln = api.dd_det_ratio_estimate(h, U, Up, N, seed, ctr, api.DD_EST_FACTORS)
         out.append(float(ln.sum().item()))
     return np.array(out)
@@ -94,15 +95,16 @@ def main():
     p.add_argument("--Ns", type=int, nargs="+", default=[1, 2, 4, 8])
     p.add_argument("--samples", type=int, default=16)
     p.add_argument("--seed", type=int, default=11)
+    p.add_argument("--n-block", type=int, default=4, help="block-filter factors (0: unfiltered proposals)")
     args = p.parse_args()
     dev = torch.device("cuda", 0)
     U = torch.from_numpy(synthetic.unit_gauge(args.dims)).to(dev)
     plaq = thermalise(api, args.dims, args.block, args.beta, args.therm, 2, args.seed, U, device=dev)
     h = api.dd_init(args.dims, args.block, args.kappa, max_rhs=max(max(args.Ns), 4), inner_prec=api.DD_PREC_F16,
                     krylov=api.DD_KRYLOV_BICGSTAB, maxit=100000, device=dev)
-    res = variance_scan(api, h, U, args.beta, args.Ns, args.samples, args.seed)
+    res = variance_scan(api, h, U, args.beta, args.Ns, args.samples, args.seed, n_block=args.n_block)
     res.update(dims=args.dims, block=args.block, beta=args.beta, kappa=args.kappa, plaquette=plaq,
-               thermalisation_sweeps=args.therm, samples=args.samples)
+               thermalisation_sweeps=args.therm, samples=args.samples, n_block=args.n_block)
     print(json.dumps(res))
 
 
