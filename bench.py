@@ -197,6 +197,29 @@ def run_reference(args, cfg):
     return 0
 
 
+def replica_seeds(cfg, rank):
+    """Seeds of the independent chain of one rank (replicas: no data-path
+    exchange between ranks): gauge-field seed and random-stream seed."""
+    return cfg["seed"] + 1000 * rank, cfg["seed"] * 7919 + rank
+
+
+def max_over_ranks(t_ms, world, device=None):
+    """The slowest rank's time (every rank gets it): the whole job is done
+    when the last replica is."""
+    if world <= 1:
+        return float(t_ms)
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_rate(units_per_rank, world, t_max_ms):
+    """Whole-job throughput: the units all ranks processed over the slowest time."""
+    return units_per_rank * world / (t_max_ms / 1e3)
+
+
 def config_dict(args, cfg, world):
     """The workload description shared by both arms of the benchmark."""
     return {"workload": f"{args.config}: {'x'.join(map(str, cfg['dims']))} lattice, "
@@ -233,7 +256,7 @@ def run_gpu(args, cfg):
     h = api.dd_init(cfg["dims"], cfg["block"], cfg["kappa"], max_rhs=nmax, inner_prec=prec,
                     block_prec=api.DD_PREC_F32, tol_global=1e-10, tol_block=1e-12, tol_inner=args.tol_inner,
                     maxit=40000, stream=stream, device=dev, krylov=krylov)
-    U_np = synthetic.random_gauge(cfg["dims"], cfg["eps"], cfg["seed"] + 1000 * rank)
+    U_np = synthetic.random_gauge(cfg["dims"], cfg["eps"], replica_seeds(cfg, rank)[0])
     U = torch.from_numpy(U_np).to(dev)
     tune = None
     if not args.no_tune:
@@ -244,7 +267,7 @@ def run_gpu(args, cfg):
         tune = api.dd_autotune(h, api.DD_TUNE_HOP | api.DD_TUNE_BLOCK, U, Up_t, reps=10)
         del Up_t
     chain = HierarchicalStep(h, BETA, n_inner=1, n_block=cfg["n_block"], n_global=cfg["n_global"],
-                             seed=cfg["seed"] * 7919 + rank)
+                             seed=replica_seeds(cfg, rank)[1])
 
     def barrier():
         if world > 1:
@@ -268,13 +291,9 @@ def run_gpu(args, cfg):
     launches = api.dd_launch_count(h) - l0
     timing = {kind: api.dd_kernel_timer(h, 2, kind) for kind in (0, 1, 2)}
     api.dd_kernel_timer(h, 0, 0)
-    t_max = t_ms
-    if world > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(t_ms, world, dev)
     est = cfg["n_global"] * args.steps * world
-    value = est / (t_max / 1e3)
+    value = job_rate(cfg["n_global"] * args.steps, world, t_max)
     # dominant hop kernel: the kind with most time
     kind = max(timing, key=lambda k: timing[k][0])
     ms_k, cnt_k, sites_k = timing[kind]
@@ -326,11 +345,7 @@ def run_gpu(args, cfg):
             chain.step_host(U_host, U_dev, 1000 + k, ln_host, acc_host)
         f1.record(stream)
         barrier()
-        te = f0.elapsed_time(f1)
-        if world > 1:
-            tt = torch.tensor([te], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
+        te = max_over_ranks(f0.elapsed_time(f1), world, dev)
         line["e2e"] = {"value": est / (te / 1e3), "unit": "estimates/s",
                        "h2d_bytes_per_step": U.numel() * 16,
                        "d2h_bytes_per_step": U.numel() * 16 + cfg["n_global"] * 8 + 1}
@@ -347,11 +362,7 @@ def run_gpu(args, cfg):
             chain.step_graph(3000 + k)
         q1.record(stream)
         barrier()
-        tg = q0.elapsed_time(q1)
-        if world > 1:
-            tt = torch.tensor([tg], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            tg = float(tt.item())
+        tg = max_over_ranks(q0.elapsed_time(q1), world, dev)
         st_code = api.dd_status(h)[0]
         line["graph"] = {"value": est / (tg / 1e3), "unit": "estimates/s", "ms_per_step": tg / args.steps,
                          "top_level_nodes": api.dd_graph_nodes(g), "device_status": st_code}
@@ -361,7 +372,7 @@ def run_gpu(args, cfg):
                           block_prec=api.DD_PREC_F32, tol_global=1e-10, tol_block=1e-12, maxit=40000,
                           stream=stream, device=dev)
         c64 = HierarchicalStep(h64, BETA, n_inner=1, n_block=cfg["n_block"], n_global=cfg["n_global"],
-                               seed=cfg["seed"] * 7919 + rank)
+                               seed=replica_seeds(cfg, rank)[1])
         U64 = torch.from_numpy(U_np).to(dev)
         c64.step(U64, 0)
         barrier()
@@ -407,7 +418,7 @@ def compare_precisions(args, cfg, dev, stream, rank):
     from paper_1112_1243_gb300.chain import HierarchicalStep
     out = {"workload": f"{'x'.join(map(str, cfg['dims']))} lattice, {'x'.join(map(str, cfg['block']))} blocks, "
                        f"kappa {cfg['kappa']}, eps {cfg['eps']}, {cfg['n_global']} global factors"}
-    U_np = synthetic.random_gauge(cfg["dims"], cfg["eps"], cfg["seed"] + 1000 * rank)
+    U_np = synthetic.random_gauge(cfg["dims"], cfg["eps"], replica_seeds(cfg, rank)[0])
     nmax = max(cfg["n_global"], cfg["n_block"])
     for name, prec, kry in (("mixed", api.DD_PREC_F16, api.DD_KRYLOV_BICGSTAB if args.krylov == "bicgstab"
                               else api.DD_KRYLOV_CGNR), ("fp64", api.DD_PREC_F64, api.DD_KRYLOV_CGNR)):
@@ -415,7 +426,7 @@ def compare_precisions(args, cfg, dev, stream, rank):
                         block_prec=api.DD_PREC_F32 if prec != api.DD_PREC_F64 else api.DD_PREC_F64,
                         tol_global=1e-10, tol_block=1e-12, maxit=40000, stream=stream, device=dev, krylov=kry)
         st = HierarchicalStep(h, BETA, n_inner=1, n_block=cfg["n_block"], n_global=cfg["n_global"],
-                              seed=cfg["seed"] * 7919 + rank)
+                              seed=replica_seeds(cfg, rank)[1])
         U = torch.from_numpy(U_np).to(dev)
         for k in range(3):
             st.step(U, k)
