@@ -465,6 +465,10 @@ def measure_batched_filter(dev, stream, reps=3):
         Us.append(U)
         Ups.append(Up)
     items = sum(h.nblocks for h in hs) * n
+    # launch shape of the persistent block solver, timed on the first lattice
+    tune = api.dd_autotune(hs[0], api.DD_TUNE_BLOCK, Us[0], Ups[0], reps=10)
+    for h in hs[1:]:
+        api.dd_set_tuning(h, block_tpb=tune["block_tpb"], block_ctas_per_sm=tune["block_ctas_per_sm"])
     work = [u.clone() for u in Ups]
     for _ in range(2):
         for w, u in zip(work, Ups):
@@ -482,7 +486,8 @@ def measure_batched_filter(dev, stream, reps=3):
     t = e0.elapsed_time(e1) / 1e3 / reps
     out = {"workload": "256 x 4^4 (16^4), 16 x 6^4 (12^4), 16 x 8^4 (16^4) blocks, 4 noise vectors each, "
                        "one persistent launch", "items_per_launch": items, "seconds_per_call": t,
-           "block_estimates_per_s": items / t}
+           "block_estimates_per_s": items / t,
+           "launch_shape": {"threads": tune["block_tpb"], "blocks_per_sm": tune["block_ctas_per_sm"]}}
     for h in hs:
         del h
     return out

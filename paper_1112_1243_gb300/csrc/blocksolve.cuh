@@ -15,6 +15,8 @@
 // position q = block_pos * bsites + local index, local index lexicographic.
 #pragma once
 
+#include <type_traits>
+
 #include "dd_internal.h"
 #include "reduce.cuh"
 
@@ -185,6 +187,172 @@ DD_DEV int block_cgnr(const BlockCtx& c, const S& x, const S& r, const S& p, con
             p.store(j, a);
         }
         __syncthreads();
+    }
+    return it;
+}
+
+// N block-wide sums at once (two barriers for all of them); every thread
+// gets the sums.  shn: at least 32 * N doubles of shared memory.
+template <int N>
+DD_DEV void block_sum_n(double* v, double* shn) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = warp_sum(v[k]);
+    __syncthreads();  // earlier readers of shn are done
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < N; ++k) shn[wid * N + k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += shn[w * N + k];
+        v[k] = t;
+    }
+}
+
+// Inner BiCGStab (van der Vorst) on D_b itself: x = 0, r holds r0 on entry;
+// rhat = r0 is the shadow residual; block-local complex scalars.  Stops when
+// |r|^2 <= tol2rel |r0|^2, after maxit iterations or at a breakdown (the
+// FP64 refinement around it restarts from the true residual).
+template <class R, class S, class LK>
+DD_DEV int block_bicgstab(const BlockCtx& c, const S& x, const S& r, const S& rhat, const S& p, const S& v,
+                          const S& s, const S& t, const LK& lk, double tol2rel, int maxit, double* sh) {
+    double rr0 = 0.0;
+    for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+        Spinor<R> z, a;
+        zero(z);
+        x.store(j, z);
+        p.store(j, z);
+        v.store(j, z);
+        r.load(j, a);
+        rhat.store(j, a);
+        rr0 += (double)snorm2(a);
+    }
+    rr0 = block_sum(rr0, sh);  // barrier: x, p, v, rhat complete
+    if (!(rr0 > 0.0)) return 0;
+    __shared__ double shn[32 * 3];
+    const double target = tol2rel * rr0;
+    cpx<double> rho_old = mk<double>(1.0, 0.0), alpha = mk<double>(1.0, 0.0), omega = mk<double>(1.0, 0.0);
+    int it = 0;
+    while (it < maxit) {
+        // rho = <rhat, r>
+        double d0 = 0.0, d1 = 0.0;
+        for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+            Spinor<R> a, b;
+            rhat.load(j, a);
+            r.load(j, b);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                d0 += (double)(a.c[k].x * b.c[k].x + a.c[k].y * b.c[k].y);
+                d1 += (double)(a.c[k].x * b.c[k].y - a.c[k].y * b.c[k].x);
+            }
+        }
+        double red[3] = {d0, d1, 0.0};
+        block_sum_n<2>(red, shn);
+        const cpx<double> rho = mk<double>(red[0], red[1]);
+        if (!(norm2(rho) > 0.0)) break;
+        const double den = norm2(rho_old) * norm2(omega);
+        if (!(den > 0.0)) break;
+        // beta = (rho / rho_old) (alpha / omega)
+        const cpx<double> beta = (1.0 / den) * cmul(cmul(rho, conj(rho_old)), cmul(alpha, conj(omega)));
+        const cpx<R> bR = mk<R>((R)beta.x, (R)beta.y), oR = mk<R>((R)omega.x, (R)omega.y);
+        for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+            Spinor<R> pp, rr, vv;
+            p.load(j, pp);
+            r.load(j, rr);
+            v.load(j, vv);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) pp.c[k] = rr.c[k] + cmul(bR, pp.c[k] - cmul(oR, vv.c[k]));
+            p.store(j, pp);
+        }
+        __syncthreads();
+        dirichlet_apply<R>(c, p, v, lk, 0);
+        __syncthreads();
+        d0 = d1 = 0.0;
+        for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+            Spinor<R> a, b;
+            rhat.load(j, a);
+            v.load(j, b);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                d0 += (double)(a.c[k].x * b.c[k].x + a.c[k].y * b.c[k].y);
+                d1 += (double)(a.c[k].x * b.c[k].y - a.c[k].y * b.c[k].x);
+            }
+        }
+        red[0] = d0;
+        red[1] = d1;
+        block_sum_n<2>(red, shn);
+        const cpx<double> rv = mk<double>(red[0], red[1]);
+        if (!(norm2(rv) > 0.0)) break;
+        alpha = (1.0 / norm2(rv)) * cmul(rho, conj(rv));
+        const cpx<R> aR = mk<R>((R)alpha.x, (R)alpha.y);
+        double ss = 0.0;
+        for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+            Spinor<R> rr, vv;
+            r.load(j, rr);
+            v.load(j, vv);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) rr.c[k] = rr.c[k] - cmul(aR, vv.c[k]);
+            s.store(j, rr);
+            ss += (double)snorm2(rr);
+        }
+        ss = block_sum(ss, sh);  // barrier: s complete
+        ++it;
+        if (ss <= target) {
+            for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+                Spinor<R> xx, pp;
+                x.load(j, xx);
+                p.load(j, pp);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) xx.c[k] = xx.c[k] + cmul(aR, pp.c[k]);
+                x.store(j, xx);
+            }
+            __syncthreads();
+            break;
+        }
+        dirichlet_apply<R>(c, s, t, lk, 0);
+        __syncthreads();
+        double ts0 = 0.0, ts1 = 0.0, tt = 0.0;
+        for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+            Spinor<R> a, b;
+            t.load(j, a);
+            s.load(j, b);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                ts0 += (double)(a.c[k].x * b.c[k].x + a.c[k].y * b.c[k].y);
+                ts1 += (double)(a.c[k].x * b.c[k].y - a.c[k].y * b.c[k].x);
+            }
+            tt += (double)snorm2(a);
+        }
+        red[0] = ts0;
+        red[1] = ts1;
+        red[2] = tt;
+        block_sum_n<3>(red, shn);
+        const cpx<double> ts = mk<double>(red[0], red[1]);
+        tt = red[2];
+        if (!(tt > 0.0)) break;
+        omega = (1.0 / tt) * ts;
+        const cpx<R> wR = mk<R>((R)omega.x, (R)omega.y);
+        double rr = 0.0;
+        for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
+            Spinor<R> xx, pp, sv, tv;
+            x.load(j, xx);
+            p.load(j, pp);
+            s.load(j, sv);
+            t.load(j, tv);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                xx.c[k] = xx.c[k] + cmul(aR, pp.c[k]) + cmul(wR, sv.c[k]);
+                sv.c[k] = sv.c[k] - cmul(wR, tv.c[k]);
+            }
+            x.store(j, xx);
+            r.store(j, sv);
+            rr += (double)snorm2(sv);
+        }
+        rr = block_sum(rr, sh);  // barrier: x and r complete
+        rho_old = rho;
+        if (rr <= target || !(norm2(omega) > 0.0)) break;
     }
     return it;
 }
@@ -380,7 +548,15 @@ __global__ void __launch_bounds__(256, 2) block_solve_kernel(BlockArgs A) {
                 ri.store(j, v);
             }
             __syncthreads();
-            block_cgnr<RI>(c, xi, ri, pi, qi, zi, lsoli, A.tol2_inner, A.maxit_inner, sh);
+            if constexpr (std::is_same<RI, float>::value) {
+                // FP32 inner vectors are half the size of the slot's FP64 ones:
+                // room for the seven BiCGStab vectors
+                SI hi = scratch_spinor<SI>(ib, 5, nb), si = scratch_spinor<SI>(ib, 6, nb),
+                   ti = scratch_spinor<SI>(ib, 7, nb);
+                block_bicgstab<RI>(c, xi, ri, hi, pi, qi, si, ti, lsoli, A.tol2_inner, A.maxit_inner, sh);
+            } else {
+                block_cgnr<RI>(c, xi, ri, pi, qi, zi, lsoli, A.tol2_inner, A.maxit_inner, sh);
+            }
             // x += |r| e; r = b - D_b x (FP64)
             for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
                 Spinor<double> a;
