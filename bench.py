@@ -465,11 +465,32 @@ def measure_batched_filter(dev, stream, reps=3):
         Us.append(U)
         Ups.append(Up)
     items = sum(h.nblocks for h in hs) * n
-    # launch shape of the persistent block solver, timed on the first lattice
-    tune = api.dd_autotune(hs[0], api.DD_TUNE_BLOCK, Us[0], Ups[0], reps=10)
-    for h in hs[1:]:
-        api.dd_set_tuning(h, block_tpb=tune["block_tpb"], block_ctas_per_sm=tune["block_ctas_per_sm"])
     work = [u.clone() for u in Ups]
+
+    def one_call(ctr):
+        for w, u in zip(work, Ups):
+            w.copy_(u)
+        api.dd_block_filter_batch(hs, Us, work, 3, n, 4, ctr)
+
+    # launch shape of the persistent block solver for this mix of block sizes:
+    # the candidates of the autotuner, each timed on one batch call
+    best = None
+    for tpb, ctas in ((256, 2), (256, 1), (128, 4), (128, 2)):
+        for h in hs:
+            api.dd_set_tuning(h, block_tpb=tpb, block_ctas_per_sm=ctas)
+        one_call(1)
+        torch.cuda.synchronize(dev)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        one_call(1)
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = c0.elapsed_time(c1)
+        if best is None or ms < best[0]:
+            best = (ms, tpb, ctas)
+    for h in hs:
+        api.dd_set_tuning(h, block_tpb=best[1], block_ctas_per_sm=best[2])
+    tune = {"block_tpb": best[1], "block_ctas_per_sm": best[2]}
     for _ in range(2):
         for w, u in zip(work, Ups):
             w.copy_(u)
