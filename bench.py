@@ -43,7 +43,9 @@ BETA = 5.3
 # algorithmic bytes per output site of the eo hop kernels (input spinor + 8
 # links with two stored rows + output; FP16 spinor = 48 B + 4 B scale,
 # FP16 link rows = 24 B, FP32 spinor = 96 B, FP64 spinor 192 B, FP64 link 144 B)
-HOP_BYTES = {0: 52 + 8 * 24 + 52, 1: 52 + 8 * 24 + 96 + 96, 2: 192 + 8 * 144 + 192}
+# algorithmic bytes per output site: input spinor once, 8 links, xpay input, output
+# (kind 3, the double-float residual hop: the t = H_oe x form, FP64-sized vectors and links)
+HOP_BYTES = {0: 52 + 8 * 24 + 52, 1: 52 + 8 * 24 + 96 + 96, 2: 192 + 8 * 144 + 192, 3: 192 + 8 * 144 + 192}
 
 
 def parse():
@@ -59,6 +61,10 @@ def parse():
     p.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay measurement")
     p.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
     p.add_argument("--no-recursive", action="store_true", help="skip the step with one level of recursion")
+    p.add_argument("--outer", default="f64", choices=["f64", "df64"],
+                   help="arithmetic of the defect-correction residual of the timed step")
+    p.add_argument("--no-outer-df64", action="store_true",
+                   help="skip the extra measurement of the step with the double-float residual")
     p.add_argument("--tol-inner", type=float, default=1e-3,
                    help="residual reduction of one inner (FP32/FP16) solve inside the FP64 defect correction")
     p.add_argument("--fp64-steps", type=int, default=0,
@@ -253,9 +259,10 @@ def run_gpu(args, cfg):
     nmax = max(cfg["n_global"], cfg["n_block"])
     stream = torch.cuda.current_stream(dev)
     krylov = {"cgnr": api.DD_KRYLOV_CGNR, "bicgstab": api.DD_KRYLOV_BICGSTAB}[args.krylov]
+    outer = {"f64": api.DD_PREC_F64, "df64": api.DD_PREC_DF64}[args.outer]
     h = api.dd_init(cfg["dims"], cfg["block"], cfg["kappa"], max_rhs=nmax, inner_prec=prec,
                     block_prec=api.DD_PREC_F32, tol_global=1e-10, tol_block=1e-12, tol_inner=args.tol_inner,
-                    maxit=40000, stream=stream, device=dev, krylov=krylov)
+                    maxit=40000, stream=stream, device=dev, krylov=krylov, outer_prec=outer)
     U_np = synthetic.random_gauge(cfg["dims"], cfg["eps"], replica_seeds(cfg, rank)[0])
     U = torch.from_numpy(U_np).to(dev)
     tune = None
@@ -289,13 +296,13 @@ def run_gpu(args, cfg):
         barrier()
     t_ms = e0.elapsed_time(e1)
     launches = api.dd_launch_count(h) - l0
-    timing = {kind: api.dd_kernel_timer(h, 2, kind) for kind in (0, 1, 2)}
+    timing = {kind: api.dd_kernel_timer(h, 2, kind) for kind in (0, 1, 2, 3)}
     api.dd_kernel_timer(h, 0, 0)
     t_max = max_over_ranks(t_ms, world, dev)
     est = cfg["n_global"] * args.steps * world
     value = job_rate(cfg["n_global"] * args.steps, world, t_max)
     # dominant hop kernel: the kind with most time
-    kind = max(timing, key=lambda k: timing[k][0])
+    kind = max((0, 1, 2), key=lambda k: timing[k][0])
     ms_k, cnt_k, sites_k = timing[kind]
     peak, peak_src = peaks()
     achieved = (sites_k * HOP_BYTES[kind] / 1e9) / (ms_k / 1e3) if ms_k > 0 else None
@@ -310,12 +317,13 @@ def run_gpu(args, cfg):
     except Exception:
         traffic = None
     # hop work per estimate (global solve only), for the CPU-baseline scaling
-    hop_sites = sum(timing[k][2] for k in (0, 1, 2))
+    hop_sites = sum(timing[k][2] for k in (0, 1, 2, 3))
     D_apps_per_est = hop_sites / (2.0 * Vh) / max(1, cfg["n_global"] * args.steps) * 1.0
     line = {
         "metric": METRIC, "value": value, "unit": "estimates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"f16": "f16-storage/f32", "f32": "f32", "f64": "f64"}[args.prec] + "+f64",
+        "vs_baseline": None,
+        "dtype": {"f16": "f16-storage/f32", "f32": "f32", "f64": "f64"}[args.prec] + "+" + args.outer,
         "data": "synthetic",
         "config": config_dict(args, cfg, world),
         "roofline": {"bound": "hbm", "kernel": f"hop_eo_kernel kind {kind}",
@@ -327,7 +335,8 @@ def run_gpu(args, cfg):
         "clocks": clocks.summary(),
         "D_applications_per_estimate": D_apps_per_est,
         "dslash_GBps": {name: (timing[k][2] * HOP_BYTES[k] / 1e9 / (timing[k][0] / 1e3) if timing[k][0] > 0 else None)
-                        for k, name in ((0, "fp16_to_fp16"), (1, "fp16_to_fp32_xpay"), (2, "fp64"))},
+                        for k, name in ((0, "fp16_to_fp16"), (1, "fp16_to_fp32_xpay"), (2, "fp64"),
+                                        (3, "double_float"))},
         "block_accept_rate_last_step": float(chain.acc_b.float().mean().item()),
         "autotune": tune,
     }
@@ -387,6 +396,8 @@ def run_gpu(args, cfg):
     del chain
     del h
     torch.cuda.empty_cache()
+    if not args.no_outer_df64 and args.outer == "f64" and args.prec != "f64":
+        line["outer_df64"] = measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune)
     if args.compare_config:
         # mixed versus plain FP64 on a smaller workload (the FP64 path at the
         # full volume would hold the GPU for minutes per step)
@@ -408,6 +419,48 @@ def run_gpu(args, cfg):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune):
+    """The timed step again with the defect-correction residual in
+    double-float arithmetic (outer_prec DD_PREC_DF64), same workload, seeds
+    and launch shapes; the hop kernels of the residual timed by kind."""
+    import torch
+    from paper_1112_1243_gb300 import api
+    from paper_1112_1243_gb300.chain import HierarchicalStep
+    prec = {"f16": api.DD_PREC_F16, "f32": api.DD_PREC_F32}[args.prec]
+    krylov = {"cgnr": api.DD_KRYLOV_CGNR, "bicgstab": api.DD_KRYLOV_BICGSTAB}[args.krylov]
+    nmax = max(cfg["n_global"], cfg["n_block"])
+    h = api.dd_init(cfg["dims"], cfg["block"], cfg["kappa"], max_rhs=nmax, inner_prec=prec,
+                    block_prec=api.DD_PREC_F32, tol_global=1e-10, tol_block=1e-12, tol_inner=args.tol_inner,
+                    maxit=40000, stream=stream, device=dev, krylov=krylov, outer_prec=api.DD_PREC_DF64)
+    if tune:
+        api.dd_set_tuning(h, hop_tpb=tune["hop_tpb"], hop_spt=tune["hop_spt"], hop64_tpb=tune["hop64_tpb"],
+                          hop64_spt=tune["hop64_spt"], block_tpb=tune["block_tpb"],
+                          block_ctas_per_sm=tune["block_ctas_per_sm"], filter_masked=tune["filter_masked"])
+    U = torch.from_numpy(U_np).to(dev)
+    chain = HierarchicalStep(h, BETA, n_inner=1, n_block=cfg["n_block"], n_global=cfg["n_global"],
+                             seed=replica_seeds(cfg, rank)[1])
+    for k in range(args.warmup):
+        chain.step(U, k)
+    torch.cuda.synchronize(dev)
+    api.dd_kernel_timer(h, 1, 0, 1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        chain.step(U, args.warmup + k)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    ms3, cnt3, _ = api.dd_kernel_timer(h, 2, 3)
+    api.dd_kernel_timer(h, 0, 0)
+    out = {"value": job_rate(cfg["n_global"] * args.steps, world, t_ms), "unit": "estimates/s",
+           "ms_per_step": t_ms / args.steps, "device_status": api.dd_status(h)[0],
+           "residual_hop_avg_us": 1e3 * ms3 / max(1, cnt3), "residual_hop_launches_timed": cnt3}
+    del chain
+    del h
+    torch.cuda.empty_cache()
+    return out
 
 
 def compare_precisions(args, cfg, dev, stream, rank):
@@ -561,8 +614,9 @@ def run_solve(args, cfg):
     dev = torch.device("cuda", 0)
     prec = {"f16": api.DD_PREC_F16, "f32": api.DD_PREC_F32, "f64": api.DD_PREC_F64}[args.prec]
     krylov = {"cgnr": api.DD_KRYLOV_CGNR, "bicgstab": api.DD_KRYLOV_BICGSTAB}[args.krylov]
+    outer = {"f64": api.DD_PREC_F64, "df64": api.DD_PREC_DF64}[args.outer]
     h = api.dd_init(cfg["dims"], cfg["block"], cfg["kappa"], max_rhs=1, inner_prec=prec, tol_global=1e-10,
-                    maxit=40000, features=api.DD_FEAT_SOLVE, device=dev, krylov=krylov)
+                    maxit=40000, features=api.DD_FEAT_SOLVE, device=dev, krylov=krylov, outer_prec=outer)
     U = torch.from_numpy(synthetic.random_gauge(cfg["dims"], cfg["eps"], cfg["seed"])).to(dev)
     b = torch.from_numpy(synthetic.random_spinor(cfg["dims"], 1)).to(dev)
     x = torch.zeros_like(b)
@@ -577,9 +631,10 @@ def run_solve(args, cfg):
         its += it
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
-    out = {"mode": "solve", "config": args.config, "prec": args.prec, "seconds_per_solve": t / args.steps,
+    out = {"mode": "solve", "config": args.config, "prec": args.prec, "outer": args.outer,
+           "seconds_per_solve": t / args.steps,
            "inner_iterations_per_solve": its / args.steps, "relres": res[0]}
-    for kind in (0, 1, 2):
+    for kind in (0, 1, 2, 3):
         ms, cnt, sites = api.dd_kernel_timer(h, 2, kind)
         if cnt:
             out[f"hop_kind{kind}"] = {"launches": cnt, "avg_us": 1e3 * ms / cnt,

@@ -61,6 +61,8 @@ extern "C" {
 #define DD_PREC_F64 0 /* FP64 storage and arithmetic */
 #define DD_PREC_F32 1 /* FP32 storage (links: rows 1-2, third row rebuilt), FP32 arithmetic */
 #define DD_PREC_F16 2 /* FP16 storage (spinors with a per-site FP32 scale), FP32 arithmetic */
+#define DD_PREC_DF64 3 /* dd_params.outer_prec only: double-float (pairs of FP32, 48-bit significand)
+                          arithmetic on FP64-sized storage */
 
 /* active-link sets (Sec. 3: links with at most one end on a block boundary) */
 #define DD_ACTIVE_AUTO 0   /* INTRA if a block extent <= 2, INNER6 if all >= 8, else PAPER */
@@ -122,6 +124,11 @@ typedef struct {
                           to the sub-blocks; dd_chain_step needs PAPER or INNER6),
                           dd_block_filter acts on the sub-blocks (Eq. 4step step 1)
                           and dd_block_schur_filter on the blocks (step 2). */
+    int outer_prec;    /* arithmetic of the true residual r = b - D x in the defect-correction
+                          loop of mixed-precision solves (Sec. 5): DD_PREC_F64 (default, 0) or
+                          DD_PREC_DF64 (double-float: every operation on the FP32 pipe, rounding
+                          error about 2^-47 of the summed term magnitudes; the workspace then
+                          holds one more FP64-sized copy of each gauge-field slot) */
 } dd_params;
 
 /* inner Krylov method of the FP32/FP16 solves (the FP64 solver is always CGNR) */
@@ -144,7 +151,8 @@ int dd_default_params(dd_params* p);
  * the handle is enqueued on it.  Builds the geometry tables on the host and
  * uploads them (the only allocation the library makes itself).
  * Errors: DD_ERR_INVALID_ARG for odd or non-dividing extents, blocks per
- * direction odd or < 2, kappa <= 0, max_rhs < 1; DD_ERR_CUDA on a CUDA error. */
+ * direction odd or < 2, kappa <= 0, max_rhs < 1, an unknown precision or
+ * active mode; DD_ERR_CUDA on a CUDA error. */
 int dd_init(dd_t* h, const dd_params* p, void* stream);
 
 /* Bytes of device workspace the handle needs for its max_rhs. */
@@ -322,7 +330,7 @@ const char* dd_last_error(dd_t h);
  * the handle has launched since dd_init (host, written before return).
  * dd_kernel_timer: CUDA-event timing, on the handle's stream, of the
  * even-odd hop kernel of one kind (0: FP16 in / FP16 out, 1: FP16 in / FP32
- * out with the xpay term, 2: FP64).  op 1 = reset and start timing every
+ * out with the xpay term, 2: FP64, 3: double-float residual hops).  op 1 = reset and start timing every
  * `every`-th launch of each kind, op 0 = stop, op 2 = synchronise the stream
  * and return the summed duration (ms), the number of timed launches and the
  * output sites those launches processed (systems already converged in a

@@ -19,7 +19,7 @@ DD_ERR_NUMERIC = -5
 DD_ERR_TIMEOUT = -6
 DD_ERR_NO_WORKSPACE = -7
 
-DD_PREC_F64, DD_PREC_F32, DD_PREC_F16 = 0, 1, 2
+DD_PREC_F64, DD_PREC_F32, DD_PREC_F16, DD_PREC_DF64 = 0, 1, 2, 3
 DD_ACTIVE_AUTO, DD_ACTIVE_PAPER, DD_ACTIVE_INNER6, DD_ACTIVE_INTRA, DD_ACTIVE_ALL = 0, 1, 2, 3, 4
 DD_OP_D, DD_OP_DDAG, DD_OP_DTILDE, DD_OP_DTILDE_DAG, DD_OP_HEO, DD_OP_INTER = 0, 1, 2, 3, 4, 5
 DD_PURPOSE_GLOBAL_NOISE = 1
@@ -61,6 +61,7 @@ class dd_params(ctypes.Structure):
         ("features", ctypes.c_int),
         ("krylov", ctypes.c_int),
         ("sub_block", ctypes.c_int * 4),
+        ("outer_prec", ctypes.c_int),
     ]
 
 

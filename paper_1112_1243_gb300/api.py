@@ -76,10 +76,11 @@ def dd_default_params():
 def dd_init(dims, block, kappa, bc_time=-1, active_mode=_lib.DD_ACTIVE_AUTO, max_rhs=1,
             inner_prec=_lib.DD_PREC_F16, block_prec=_lib.DD_PREC_F32, tol_global=1e-10,
             tol_block=1e-12, tol_inner=1e-3, maxit=20000, stream=None, device=None, features=0,
-            krylov=_lib.DD_KRYLOV_CGNR, sub_block=None):
+            krylov=_lib.DD_KRYLOV_CGNR, sub_block=None, outer_prec=_lib.DD_PREC_F64):
     """Create a handle and give it a torch-allocated workspace on `device`.
     sub_block: extents of the sub-blocks of one level of recursion (None: no
-    recursion)."""
+    recursion).  outer_prec: arithmetic of the defect-correction residual of
+    mixed-precision solves (DD_PREC_F64 or DD_PREC_DF64)."""
     lib = _lib.load()
     p = dd_default_params()
     for a in range(4):
@@ -99,6 +100,7 @@ def dd_init(dims, block, kappa, bc_time=-1, active_mode=_lib.DD_ACTIVE_AUTO, max
     p.krylov = int(krylov)
     for a in range(4):
         p.sub_block[a] = int(sub_block[a]) if sub_block is not None else 0
+    p.outer_prec = int(outer_prec)
     device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
     if stream is None:
         stream = torch.cuda.current_stream(device)

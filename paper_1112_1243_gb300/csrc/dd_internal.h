@@ -58,6 +58,7 @@ struct FieldSlot {
     double2* dd64;   // block order, FP64 [blockpos][dir][chunk][bsites]
     float4* dd32;    // block order, FP32 rows 0-1
     double2* canon;  // canonical FP64 copy (interpolated fields)
+    float4* eodf;    // eo layout, double-float (hi, lo) pairs, 9 chunks (outer_prec DD_PREC_DF64 only)
 };
 
 // Vectors of one right-hand side of the global solver (eo layout, Vh sites).
@@ -91,7 +92,9 @@ struct SolverVecs {
     float* q16n;
 };
 
-constexpr int DD_BLOCK_CTAS_MAX = 4;  // scratch slots of the persistent block solver per SM
+constexpr int DD_BLOCK_CTAS_MAX = 4;
+// timed hop kinds: 0 FP16 -> FP16, 1 FP16 -> FP32 (xpay), 2 FP64, 3 double-float
+constexpr int DD_TIMER_KINDS = 4;  // scratch slots of the persistent block solver per SM
 
 // Launch shapes chosen by the autotuner (dd_autotune); defaults are the
 // shapes the kernels were written for.
@@ -147,10 +150,10 @@ struct dd_handle {
     unsigned long long launches = 0;
     int timer_on = 0;
     int timer_every = 1;
-    unsigned long long timer_seen[3] = {0, 0, 0};
-    std::vector<cudaEvent_t> timer_ev[3];
-    size_t timer_used[3] = {0, 0, 0};
-    unsigned long long* d_sites = nullptr;  // [3] output sites of the timed launches
+    unsigned long long timer_seen[DD_TIMER_KINDS] = {};
+    std::vector<cudaEvent_t> timer_ev[DD_TIMER_KINDS];
+    size_t timer_used[DD_TIMER_KINDS] = {};
+    unsigned long long* d_sites = nullptr;  // [DD_TIMER_KINDS] output sites of the timed launches
     // even-odd indices of the sites of each block colour (null when the
     // block extent along axis 0 is odd); Dirichlet solves of one colour
     // visit only these

@@ -142,6 +142,13 @@ __global__ void format_gauge_kernel(Geo g, const double* __restrict__ U, FieldSl
             double2* o = f.eo64 + ((long long)par * 4 + a) * 9 * Vh + h;
             for (int k = 0; k < 9; ++k) o[k * Vh] = make_double2(u[2 * k], u[2 * k + 1]);
         }
+        if (f.eo64 && f.eodf) {
+            float4* o = f.eodf + ((long long)par * 4 + a) * 9 * Vh + h;
+            for (int k = 0; k < 9; ++k) {
+                const float rh = (float)u[2 * k], ih = (float)u[2 * k + 1];
+                o[k * Vh] = make_float4(rh, ih, (float)(u[2 * k] - (double)rh), (float)(u[2 * k + 1] - (double)ih));
+            }
+        }
         if (f.eo32) {
             float4* o = f.eo32 + ((long long)par * 4 + a) * 3 * Vh + h;
             for (int k = 0; k < 3; ++k)
@@ -338,6 +345,7 @@ void plan(dd_handle* h, char* base) {
         f.eo64 = c.take<double2>((size_t)2 * 4 * 9 * Vh);
         f.eo32 = c.take<float4>((size_t)2 * 4 * 3 * Vh);
         f.eo16 = c.take<uint2>((size_t)2 * 4 * 3 * Vh);
+        f.eodf = h->prm.outer_prec == DD_PREC_DF64 ? c.take<float4>((size_t)2 * 4 * 9 * Vh) : nullptr;
         if (est) {
             f.dd64 = c.take<double2>((size_t)4 * 9 * V);
             f.dd32 = c.take<float4>((size_t)4 * 3 * V);
@@ -467,7 +475,8 @@ extern "C" int dd_init(dd_t* out, const dd_params* p, void* stream) {
         return DD_ERR_INVALID_ARG;
     }
     if (p->inner_prec < DD_PREC_F64 || p->inner_prec > DD_PREC_F16 || p->block_prec < DD_PREC_F64 ||
-        p->block_prec > DD_PREC_F32 || p->active_mode < DD_ACTIVE_AUTO || p->active_mode > DD_ACTIVE_ALL) {
+        p->block_prec > DD_PREC_F32 || p->active_mode < DD_ACTIVE_AUTO || p->active_mode > DD_ACTIVE_ALL ||
+        (p->outer_prec != DD_PREC_F64 && p->outer_prec != DD_PREC_DF64)) {
         delete h;
         return DD_ERR_INVALID_ARG;
     }
@@ -542,8 +551,8 @@ extern "C" int dd_init(dd_t* out, const dd_params* p, void* stream) {
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_hb_fails, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(h->d_hb_fails, 0, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_sites, 3 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(h->d_sites, 0, 3 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_sites, DD_TIMER_KINDS * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(h->d_sites, 0, DD_TIMER_KINDS * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_ctr_off, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(h->d_ctr_off, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_loop, sizeof(int) * DD_LOOP_SLOTS);
@@ -673,15 +682,15 @@ extern "C" int dd_launch_count(dd_t h, long long* launches) {
 
 extern "C" int dd_kernel_timer(dd_t h, int op, int kind, int every, double* total_ms, long long* timed,
                                long long* sites) {
-    if (!h || kind < 0 || kind > 2) return DD_ERR_INVALID_ARG;
+    if (!h || kind < 0 || kind >= DD_TIMER_KINDS) return DD_ERR_INVALID_ARG;
     if (op == 1) {
         h->timer_on = 1;
         h->timer_every = every > 0 ? every : 1;
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < DD_TIMER_KINDS; ++k) {
             h->timer_used[k] = 0;
             h->timer_seen[k] = 0;
         }
-        DD_CUDA(h, cudaMemsetAsync(h->d_sites, 0, 3 * sizeof(unsigned long long), h->stream));
+        DD_CUDA(h, cudaMemsetAsync(h->d_sites, 0, DD_TIMER_KINDS * sizeof(unsigned long long), h->stream));
         return DD_OK;
     }
     if (op == 0) {
@@ -698,7 +707,7 @@ extern "C" int dd_kernel_timer(dd_t h, int op, int kind, int every, double* tota
         tot += ms;
         ++cnt;
     }
-    unsigned long long ns[3] = {0, 0, 0};
+    unsigned long long ns[DD_TIMER_KINDS] = {};
     DD_CUDA(h, cudaMemcpy(ns, h->d_sites, sizeof(ns), cudaMemcpyDeviceToHost));
     if (total_ms) *total_ms = tot;
     if (timed) *timed = cnt;
@@ -708,7 +717,7 @@ extern "C" int dd_kernel_timer(dd_t h, int op, int kind, int every, double* tota
 
 extern "C" int dd_finalize(dd_t h) {
     if (!h) return DD_ERR_INVALID_ARG;
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < DD_TIMER_KINDS; ++k)
         for (cudaEvent_t e : h->timer_ev[k]) cudaEventDestroy(e);
     cudaFree(h->d_active_links);
     cudaFree(h->d_active_mask);

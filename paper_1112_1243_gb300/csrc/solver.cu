@@ -17,6 +17,7 @@
 #include <cmath>
 #include <vector>
 
+#include "dfhop.cuh"
 #include "dslash.cuh"
 #include "solver.h"
 
@@ -99,8 +100,15 @@ __global__ void cg_arm_kernel(int nrhs, CGState* st, const CGState* outer, const
     CGState c;
     c.zz = c.qq = c.alpha = c.beta = 0.0;
     c.rr = rr0[r];
-    // relative target tol^2 |r0|^2, or a fraction of the outer absolute target
-    c.tol2 = (abs_fac > 0.0 && outer) ? abs_fac * outer[r].tol2 : tol * tol * rr0[r];
+    // relative target tol^2 |r0|^2, or a fraction of the outer absolute target.
+    // A mixed inner solve is asked for no more than the outer loop still
+    // needs: when ||r_outer|| is within 1/tol_inner of the outer target, the
+    // relative target rises to 0.3 target / ||r_outer|| (capped at 0.1), so the
+    // last defect cycle does not over-solve.
+    double rel2 = tol * tol;
+    if (abs_fac < 0.0 && outer && outer[r].rr > 0.0)
+        rel2 = fmin(fmax(rel2, 0.09 * outer[r].tol2 / outer[r].rr), 0.01);
+    c.tol2 = (abs_fac > 0.0 && outer) ? abs_fac * outer[r].tol2 : rel2 * rr0[r];
     c.active = (outer ? outer[r].active : 1) && rr0[r] > 0.0;
     c.iters = 0;
     c.maxit = maxit;
@@ -336,8 +344,11 @@ DD_DEV cpx<R> cscal(double re, double im) {
     return mk<R>((R)re, (R)im);
 }
 
-template <class R, class SM>
-__global__ void bicg_start_kernel(SiteSet S, SM x, SM r, SM rhat, SM p, SM v, const CGState* outer) {
+// p and rhat live only in the hop storage SH: the rounded p is the one that
+// both v = Dtilde p and x += alpha p use, and rhat (any fixed vector) is the
+// rounded r0.
+template <class R, class SM, class SH>
+__global__ void bicg_start_kernel(SiteSet S, SM x, SM r, SH rhat, SH p, SM v, const CGState* outer) {
     const int rhs = blockIdx.y;
     if (outer && !outer[rhs].active) return;
     const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -361,8 +372,8 @@ __global__ void bicg_arm_kernel(int nrhs, CGState* st) {
     c.be_re = c.be_im = 0.0;
 }
 
-template <class R, class SM>
-__global__ void __launch_bounds__(128) bicg_rho_kernel(SiteSet S, SM rhat, SM r, const CGState* st, Reduce red) {
+template <class R, class SM, class SH>
+__global__ void __launch_bounds__(128) bicg_rho_kernel(SiteSet S, SH rhat, SM r, const CGState* st, Reduce red) {
     __shared__ double sh[34];
     const int rhs = blockIdx.y;
     if (!st[rhs].active) return;
@@ -386,10 +397,9 @@ __global__ void __launch_bounds__(128) bicg_rho_kernel(SiteSet S, SM rhat, SM r,
     grid_reduce3(red, rhs, v, sh);
 }
 
-// p = r + beta (p - omega v), hop copy of p
+// p = r + beta (p - omega v)
 template <class R, class SM, class SH>
-__global__ void __launch_bounds__(128) bicg_p_kernel(SiteSet S, SM p, SM r, SM v, SH ph, int copy,
-                                                     const CGState* st) {
+__global__ void __launch_bounds__(128) bicg_p_kernel(SiteSet S, SH p, SM r, SM v, const CGState* st) {
     const int rhs = blockIdx.y;
     if (!st[rhs].active) return;
     const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -404,7 +414,6 @@ __global__ void __launch_bounds__(128) bicg_p_kernel(SiteSet S, SM p, SM r, SM v
 #pragma unroll
     for (int k = 0; k < 12; ++k) pp.c[k] = rr.c[k] + cmul(be, pp.c[k] - cmul(om, vv.c[k]));
     at_rhs(p, rhs).store(i, pp);
-    if (copy) at_rhs(ph, rhs).store(i, pp);
 }
 
 // s = r - alpha v, hop copy of s
@@ -428,8 +437,8 @@ __global__ void __launch_bounds__(128) bicg_s_kernel(SiteSet S, SM s, SM r, SM v
 }
 
 // x += alpha p + omega s, r = s - omega t; <rh, r>, |r|^2 -> FIN_BI_RHO
-template <class R, class SM>
-__global__ void __launch_bounds__(128) bicg_xr_kernel(SiteSet S, SM x, SM r, SM p, SM s, SM t, SM rhat,
+template <class R, class SM, class SH>
+__global__ void __launch_bounds__(128) bicg_xr_kernel(SiteSet S, SM x, SM r, SH p, SM s, SM t, SH rhat,
                                                       const CGState* st, Reduce red) {
     __shared__ double sh[34];
     const int rhs = blockIdx.y;
@@ -469,8 +478,8 @@ template <class R, class SM, class SH, class LK, int MASK = 0>
 struct BiCGStab {
     dd_handle* h;
     int nrhs;
-    SM x, r, p, v, s, t, rhat;
-    SH ph, shop, th;
+    SM x, r, v, s, t;
+    SH p, rhat, shop, th;  // p and rhat only in hop storage; shop: hop copy of s
     int copies;
     LK lk;
     long long lk_rs;
@@ -508,15 +517,19 @@ struct BiCGStab {
         A.st = st;
         A.red = red(op);
         A.red3 = red3;
-        A.rhat = rhat;
+        if constexpr (std::is_same<SX, SH>::value)
+            A.rhat = rhat;  // read by the red3 == 1 form only
+        else
+            A.rhat = xin;
         A.S = S;
         return A;
     }
-    // out = Dtilde in_h (in_m: the same vector in master storage for the xpay term)
-    void apply(SH in_h, SM in_m, SM out, int op, int red3) {
+    // out = Dtilde in_h (in_m: the same vector in the storage of the xpay term)
+    template <class SX>
+    void apply(SH in_h, SX in_m, SM out, int op, int red3) {
         const double k2 = h->prm.kappa * h->prm.kappa;
-        launch_hop<R, SH, SM, SH, LK, MASK>(args(1, in_h, in_m, th, 0.0, 1.0, 0, FIN_NONE, 0), nrhs, h);
-        launch_hop<R, SH, SM, SM, LK, MASK>(args(0, th, in_m, out, 1.0, -k2, 1, op, red3), nrhs, h);
+        launch_hop<R, SH, SM, SH, LK, MASK>(args(1, in_h, v, th, 0.0, 1.0, 0, FIN_NONE, 0), nrhs, h);
+        launch_hop<R, SH, SX, SM, LK, MASK>(args(0, th, in_m, out, 1.0, -k2, 1, op, red3), nrhs, h);
     }
     // solve Dtilde x = r (r holds the right-hand side; x starts at 0)
     int run(const double* rr0, double tol, double abs_fac, int maxit, int chunk, int* iters_out) {
@@ -524,19 +537,19 @@ struct BiCGStab {
         if (maxit < 1) maxit = 1;
         DD_KLAUNCH(h, cg_arm_kernel<<<1, 64, 0, h->stream>>>(nrhs, st, outer, rr0, tol, abs_fac, maxit));
         DD_KLAUNCH(h, bicg_arm_kernel<<<1, 64, 0, h->stream>>>(nrhs, st));
-        DD_KLAUNCH(h, bicg_start_kernel<R, SM><<<grid, 128, 0, h->stream>>>(S, x, r, rhat, p, v, outer));
-        DD_KLAUNCH(h, bicg_rho_kernel<R, SM><<<grid, 128, 0, h->stream>>>(S, rhat, r, st, red(FIN_BI_RHO)));
+        DD_KLAUNCH(h, bicg_start_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(S, x, r, rhat, p, v, outer));
+        DD_KLAUNCH(h, bicg_rho_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(S, rhat, r, st, red(FIN_BI_RHO)));
         std::vector<CGState> hs(nrhs);
         int done = 0;
         bool polled = false;
         auto body = [&]() -> int {
             for (int it = 0; it < chunk; ++it) {
-                DD_KLAUNCH(h, bicg_p_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(S, p, r, v, ph, copies, st));
-                apply(ph, p, v, FIN_BI_ALPHA, 1);
+                DD_KLAUNCH(h, bicg_p_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(S, p, r, v, st));
+                apply(p, p, v, FIN_BI_ALPHA, 1);
                 DD_KLAUNCH(h, bicg_s_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(S, s, r, v, shop, copies, st));
                 apply(shop, s, t, FIN_BI_OMEGA, 2);
-                DD_KLAUNCH(h, bicg_xr_kernel<R, SM><<<grid, 128, 0, h->stream>>>(S, x, r, p, s, t, rhat, st,
-                                                                                 red(FIN_BI_RHO)));
+                DD_KLAUNCH(h, bicg_xr_kernel<R, SM, SH><<<grid, 128, 0, h->stream>>>(S, x, r, p, s, t, rhat, st,
+                                                                                     red(FIN_BI_RHO)));
             }
             return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
         };
@@ -637,11 +650,19 @@ __global__ void add_scalars_kernel(int n, double* a, const double* b) {
     if (r < n) a[r] += b[r];
 }
 
+template <int MASK, class Inner>
+int defect_correction_df(dd_handle* h, int nrhs, int field0, int step, Inner& cg, double tol, int maxit,
+                         int* iters, double* relres);
+
 // One defect-correction solve around an inner solver (NormalCG or BiCGStab;
 // its x is the correction, its r starts as the FP64 outer residual).
 template <int MASK, class Inner>
 int defect_correction(dd_handle* h, int nrhs, int field0, int step, Inner& cg, bool fp64_inner, double tol,
                       int maxit, int* iters, double* relres) {
+    if constexpr (std::is_same<decltype(cg.x), SpinorF32>::value) {
+        if (!fp64_inner && h->prm.outer_prec == DD_PREC_DF64)
+            return defect_correction_df<MASK>(h, nrhs, field0, step, cg, tol, maxit, iters, relres);
+    }
     typedef decltype(cg.x) SM;
     SolverVecs& v = h->vecs[0];
     const long long Vh = h->g.Vh;
@@ -737,6 +758,255 @@ int defect_correction(dd_handle* h, int nrhs, int field0, int step, Inner& cg, b
     return conv ? DD_OK : DD_ERR_NOT_CONVERGED;
 }
 
+
+// ------------------------------------------- double-float defect correction
+// The outer loop of a mixed-precision solve with the true residual formed in
+// double-float arithmetic (dd_params.outer_prec = DD_PREC_DF64, dfhop.cuh).
+// Per right-hand side every double-float vector holds sigma times the FP64
+// value, sigma = 2^e with |sigma b| in [1, 2); residual norms are reported
+// unscaled.
+
+// e_r = -floor(log2 |b_r|) (0 for b_r = 0)
+__global__ void df_scale_kernel(int nrhs, const double* bb, double* sig_exp) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrhs) return;
+    sig_exp[r] = bb[r] > 0.0 ? -(double)ilogb(sqrt(bb[r])) : 0.0;
+}
+// out = sigma in, split into double-float
+__global__ void __launch_bounds__(128) to_df_kernel(SiteSet S, SpinorF64 in, SpinorDF out, const double* sig_exp) {
+    const int rhs = blockIdx.y;
+    const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ti >= S.n) return;
+    const long long i = S.at(ti);
+    const int e = (int)sig_exp[rhs];
+    const SpinorF64 a = at_rhs(in, rhs);
+    const SpinorDF o = at_rhs(out, rhs);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const double2 v = a.p[k * a.stride + i];
+        o.st(i, k, cdf{df_from_double(ldexp(v.x, e)), df_from_double(ldexp(v.y, e))});
+    }
+}
+// out = (hi + lo) / sigma in FP64
+__global__ void __launch_bounds__(128) from_df_kernel(SiteSet S, SpinorDF in, SpinorF64 out, const double* sig_exp) {
+    const int rhs = blockIdx.y;
+    const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ti >= S.n) return;
+    const long long i = S.at(ti);
+    const int e = -(int)sig_exp[rhs];
+    const SpinorDF a = at_rhs(in, rhs);
+    const SpinorF64 o = at_rhs(out, rhs);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const cdf c = a.ld(i, k);
+        o.p[k * o.stride + i] = make_double2(ldexp(df_to_double(c.re), e), ldexp(df_to_double(c.im), e));
+    }
+}
+// r = in rounded to FP32, |r|^2 / sigma^2 (the residual of x = 0)
+__global__ void __launch_bounds__(128) df_round_kernel(SiteSet S, SpinorDF in, SpinorF32 r, const double* sig_exp,
+                                                       Reduce red) {
+    __shared__ double sh[34];
+    const int rhs = blockIdx.y;
+    const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double nrm = 0.0;
+    if (ti < S.n) {
+        const long long i = S.at(ti);
+        const SpinorDF a = at_rhs(in, rhs);
+        Spinor<float> v;
+        float n2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const cdf c = a.ld(i, k);
+            v.c[k] = mk<float>(__fadd_rn(c.re.hi, c.re.lo), __fadd_rn(c.im.hi, c.im.lo));
+            n2 = fmaf(v.c[k].x, v.c[k].x, fmaf(v.c[k].y, v.c[k].y, n2));
+        }
+        at_rhs(r, rhs).store(i, v);
+        nrm = ldexp((double)n2, -2 * (int)sig_exp[rhs]);
+    }
+    grid_reduce(red, rhs, nrm, sh);
+}
+// r /= sigma |r| (the inner solver's unit-norm right-hand side)
+__global__ void __launch_bounds__(128) df_normalise_kernel(SiteSet S, SpinorF32 r, const double* rr,
+                                                           const double* sig_exp, const CGState* outer) {
+    const int rhs = blockIdx.y;
+    if (outer && !outer[rhs].active) return;
+    const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ti >= S.n) return;
+    const long long i = S.at(ti);
+    const float inv = rr[rhs] > 0.0 ? (float)ldexp(1.0 / sqrt(rr[rhs]), -(int)sig_exp[rhs]) : 0.f;
+    const SpinorF32 a = at_rhs(r, rhs);
+    Spinor<float> v;
+    a.load(i, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v.c[k] = inv * v.c[k];
+    a.store(i, v);
+}
+// x += sigma |r| e (e: the inner solution of the unit-norm system)
+template <class SE>
+__global__ void __launch_bounds__(128) df_add_correction_kernel(SiteSet S, SpinorDF x, SE e, const double* rr,
+                                                                const double* sig_exp, const CGState* outer) {
+    const int rhs = blockIdx.y;
+    if (outer && !outer[rhs].active) return;
+    const long long ti = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ti >= S.n) return;
+    const long long i = S.at(ti);
+    const dfl sc = df_from_double(ldexp(sqrt(rr[rhs]), (int)sig_exp[rhs]));
+    const SpinorDF xr = at_rhs(x, rhs);
+    Spinor<float> b;
+    at_rhs(e, rhs).load(i, b);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        cdf c = xr.ld(i, k);
+        df_mac(c.re, sc, dfl{b.c[k].x, 0.f});
+        df_mac(c.im, sc, dfl{b.c[k].y, 0.f});
+        xr.st(i, k, c);
+    }
+}
+
+template <int MASK, int MODE>
+void hopdf(dd_handle* h, int nrhs, DFHopArgs A) {
+    const int tpb = std::min(h->tune.hop64_tpb, 128);
+    dim3 grid(grid_for(A.S.n, tpb), nrhs);
+    bool timed = false;
+    if (MASK == 0 && h->timer_on && !h->capturing && !dd_stream_capturing(h))
+        timed = (h->timer_seen[3]++ % h->timer_every) == 0;
+    A.sites = nullptr;
+    if (timed) {
+        cudaEvent_t e = dd_timer_event(h, 3);
+        if (e) cudaEventRecord(e, h->stream);
+        A.sites = h->d_sites + 3;
+    }
+    DD_KLAUNCH(h, hop_df_kernel<MASK, MODE><<<grid, tpb, 0, h->stream>>>(A));
+    if (timed) {
+        cudaEvent_t e = dd_timer_event(h, 3);
+        if (e) cudaEventRecord(e, h->stream);
+    }
+}
+
+template <int MASK, class Inner>
+int defect_correction_df(dd_handle* h, int nrhs, int field0, int step, Inner& cg, double tol, int maxit,
+                         int* iters, double* relres) {
+    typedef decltype(cg.x) SM;
+    SolverVecs& v = h->vecs[0];
+    const long long Vh = h->g.Vh;
+    const double kappa = h->prm.kappa;
+    const SiteSet S = cg.S;
+    dim3 grid(grid_for(S.n, 128), nrhs);
+    SpinorF64 be{v.be, Vh}, bo{v.bo, Vh}, xe{v.xe, Vh}, xo{v.xo, Vh};
+    // double-float vectors in the FP64 buffers of the plain FP64 solver (same bytes per site)
+    SpinorDF xd{reinterpret_cast<float4*>(v.x64), Vh}, td{reinterpret_cast<float4*>(v.p64), Vh},
+        btd{reinterpret_cast<float4*>(v.q64), Vh}, bod{reinterpret_cast<float4*>(v.z64), Vh};
+    const SpinorF32 r32 = cg.r;
+    FieldSlot& f0 = h->fields[field0];
+    if (!f0.eodf) return DD_ERR_INVALID_ARG;
+    LinkDF lk{f0.eodf, Vh};
+    const long long rs = (step && h->fields.size() > 1) ? (long long)(h->fields[1].eodf - h->fields[0].eodf) : 0;
+    CGState* outer = h->d_cg + h->prm.max_rhs;
+    double* bb = h->d_scalars;
+    double* tmp = h->d_scalars + nrhs;
+    double* rr = h->d_scalars + 2 * nrhs;
+    double* ones = h->d_scalars + 3 * nrhs;
+    double* sig = h->d_scalars + 4 * nrhs;
+    DFHopArgs A;
+    A.g = h->g;
+    A.lk = lk;
+    A.lk_rhs_stride = rs;
+    A.st = nullptr;
+    A.sig_exp = sig;
+    A.red.op = FIN_NONE;
+    A.S = S;
+    // |b|^2 over both parities, the scales, b~ = b_e + kappa H_eo b_o
+    DD_KLAUNCH(h, norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(S, be, store_reduce(h, bb)));
+    DD_KLAUNCH(h, norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(S, bo, store_reduce(h, tmp)));
+    DD_KLAUNCH(h, add_scalars_kernel<<<1, 64, 0, h->stream>>>(nrhs, bb, tmp));
+    DD_KLAUNCH(h, df_scale_kernel<<<1, 64, 0, h->stream>>>(nrhs, bb, sig));
+    DD_KLAUNCH(h, to_df_kernel<<<grid, 128, 0, h->stream>>>(S, be, btd, sig));
+    DD_KLAUNCH(h, to_df_kernel<<<grid, 128, 0, h->stream>>>(S, bo, bod, sig));
+    A.p = 0;
+    A.in = bod;
+    A.xin = btd;
+    A.out = btd;
+    A.c = df_from_double(kappa);
+    hopdf<MASK, 1>(h, nrhs, A);
+    DD_KLAUNCH(h, outer_arm_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, bb, tol));
+    DD_KLAUNCH(h, zero64_kernel<<<grid, 128, 0, h->stream>>>(S, SpinorF64{v.x64, Vh}));
+    DD_KLAUNCH(h, df_round_kernel<<<grid, 128, 0, h->stream>>>(S, btd, r32, sig, store_reduce(h, rr)));
+    DD_KLAUNCH(h, outer_update_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, rr));
+    if (cudaGetLastError() != cudaSuccess) return DD_ERR_CUDA;
+    int total = 0, cycles = 0;
+    bool polled = false;
+    std::vector<CGState> hs(nrhs);
+    auto body = [&]() -> int {
+        DD_KLAUNCH(h, df_normalise_kernel<<<grid, 128, 0, h->stream>>>(S, r32, rr, sig, outer));
+        DD_KLAUNCH(h, fill_kernel<<<1, 64, 0, h->stream>>>(nrhs, ones, 1.0));
+        int it = 0;
+        int rc = cg.run(ones, h->prm.tol_inner, -1.0, maxit - total, 16, &it);
+        total += it;
+        if (rc) return rc;
+        DD_KLAUNCH(h, df_add_correction_kernel<SM><<<grid, 128, 0, h->stream>>>(S, xd, cg.x, rr, sig, outer));
+        // true residual r = b~ - x + kappa^2 H_eo H_oe x (double-float), rounded into the inner r
+        DFHopArgs B = A;
+        B.st = outer;
+        B.p = 1;
+        B.in = xd;
+        B.out = td;
+        hopdf<MASK, 0>(h, nrhs, B);
+        B.p = 0;
+        B.in = td;
+        B.xin = xd;
+        B.bin = btd;
+        B.rout = r32;
+        B.c = df_from_double(kappa * kappa);
+        B.red = store_reduce(h, rr);
+        hopdf<MASK, 2>(h, nrhs, B);
+        DD_KLAUNCH(h, outer_update_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, rr));
+        return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+    };
+    auto more = [&](bool& m) -> int {
+        ++cycles;
+        if (cudaMemcpyAsync(hs.data(), outer, sizeof(CGState) * nrhs, cudaMemcpyDeviceToHost, h->stream) !=
+            cudaSuccess)
+            return DD_ERR_CUDA;
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) return DD_ERR_CUDA;
+        polled = true;
+        bool any = false;
+        for (int k = 0; k < nrhs; ++k) any = any || hs[k].active;
+        m = any && total < maxit && cycles < 200;
+        return DD_OK;
+    };
+    const LoopCond lc{outer, nrhs, 200, cg.st, (long long)maxit, 0};
+    int rc = dd_loop(h, body, more, lc);
+    if (rc) return rc;
+    // x_o = b_o + kappa H_oe x_e, both parities back to FP64
+    A.p = 1;
+    A.in = xd;
+    A.xin = bod;
+    A.out = td;
+    A.c = df_from_double(kappa);
+    hopdf<MASK, 1>(h, nrhs, A);
+    DD_KLAUNCH(h, from_df_kernel<<<grid, 128, 0, h->stream>>>(S, xd, xe, sig));
+    DD_KLAUNCH(h, from_df_kernel<<<grid, 128, 0, h->stream>>>(S, td, xo, sig));
+    if (cudaGetLastError() != cudaSuccess) return DD_ERR_CUDA;
+    if (!polled) {
+        DD_KLAUNCH(h, not_converged_kernel<<<1, 1, 0, h->stream>>>(nrhs, outer, h->d_status));
+        return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+    }
+    std::vector<double> hb(nrhs);
+    if (cudaMemcpyAsync(hb.data(), bb, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        return DD_ERR_CUDA;
+    if (cudaMemcpyAsync(hs.data(), outer, sizeof(CGState) * nrhs, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        return DD_ERR_CUDA;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return DD_ERR_CUDA;
+    bool conv = true;
+    for (int k = 0; k < nrhs; ++k) {
+        double rel = hb[k] > 0 ? std::sqrt(hs[k].rr / hb[k]) : 0.0;
+        if (relres) relres[k] = rel;
+        if (hs[k].active) conv = false;
+    }
+    if (iters) *iters = total;
+    return conv ? DD_OK : DD_ERR_NOT_CONVERGED;
+}
+
 }  // namespace
 
 template <class B>
@@ -746,11 +1016,9 @@ static void fill_bicg(dd_handle* h, B& bi, long long Vh, CGState* inner, CGState
     bi.h = h;
     bi.x = SpinorF32{v.x32, Vh};
     bi.r = SpinorF32{v.r32, Vh};
-    bi.p = SpinorF32{v.p32, Vh};
     bi.v = SpinorF32{v.q32, Vh};
     bi.s = SpinorF32{v.z32, Vh};
     bi.t = SpinorF32{v.w32, Vh};
-    bi.rhat = SpinorF32{v.h32, Vh};
     bi.st = inner;
     bi.outer = outer;
 }
@@ -786,7 +1054,8 @@ static int solve_packed_mask(dd_handle* h, SiteSet S, int nrhs, int field0, int 
         if (prec == DD_PREC_F32) {
             BiCGStab<float, SpinorF32, SpinorF32, LinkF32, MASK> bi;
             fill_bicg(h, bi, Vh, inner, outer, nrhs);
-            bi.ph = bi.p;
+            bi.p = SpinorF32{v.p32, Vh};
+            bi.rhat = SpinorF32{v.h32, Vh};
             bi.shop = bi.s;
             bi.th = SpinorF32{v.t32, Vh};
             bi.copies = 0;
@@ -797,7 +1066,8 @@ static int solve_packed_mask(dd_handle* h, SiteSet S, int nrhs, int field0, int 
         }
         BiCGStab<float, SpinorF32, SpinorF16, LinkF16, MASK> bi;
         fill_bicg(h, bi, Vh, inner, outer, nrhs);
-        bi.ph = SpinorF16{v.p16, v.p16n, Vh};
+        bi.p = SpinorF16{v.p16, v.p16n, Vh};
+        bi.rhat = SpinorF16{v.q16, v.q16n, Vh};
         bi.shop = SpinorF16{v.r16, v.r16n, Vh};
         bi.th = SpinorF16{v.t16, v.t16n, Vh};
         bi.copies = 1;

@@ -59,7 +59,8 @@ def test_workspace_size_query_without_gpu():
     from paper_1112_1243_gb300 import _lib
     names = [f[0] for f in _lib.dd_params._fields_]
     assert names == ["dims", "block", "kappa", "bc_time", "active_mode", "max_rhs", "inner_prec", "block_prec",
-                     "tol_global", "tol_block", "tol_inner", "maxit", "features", "krylov", "sub_block"]
+                     "tol_global", "tol_block", "tol_inner", "maxit", "features", "krylov", "sub_block",
+                     "outer_prec"]
     assert ctypes.sizeof(_lib.dd_params) % 8 == 0
 
 
