@@ -121,25 +121,6 @@ DD_DEV void cdf_macc(cdf& acc, cdf u, cdf h) {
     df_mac(acc.im, df_neg(u.im), h.re);
 }
 
-// lower spin pair from the upper one: the spin structure of Sec. 5's
-// projectors in the chiral basis (time: lower = +-h; space: lower =
-// -+ i sigma_k h), as in the FP64/FP32 stencil
-DD_DEV void df_isigma(int a, const cdf* v0, const cdf* v1, cdf* o0, cdf* o1) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        if (a == 0) {
-            o0[c] = cdf_i(v1[c]);
-            o1[c] = cdf_i(v0[c]);
-        } else if (a == 1) {
-            o0[c] = v1[c];
-            o1[c] = cdf_neg(v0[c]);
-        } else {
-            o0[c] = cdf_i(v0[c]);
-            o1[c] = cdf_neg(cdf_i(v1[c]));
-        }
-    }
-}
-
 struct DFHopArgs {
     Geo g;
     int p;             // output parity
@@ -157,6 +138,100 @@ struct DFHopArgs {
     SiteSet S;
     unsigned long long* sites;  // timed launches: output sites processed (may be null)
 };
+
+// (i sigma_a) applied to a spin pair (v0, v1) -> (o0, o1), a = 0, 1, 2 (runtime,
+// the same in every thread of a warp): the spin structure of Sec. 5's
+// projectors in the chiral basis, as in the FP64/FP32 stencil
+DD_DEV void df_isigma_rt(int a, const cdf* v0, const cdf* v1, cdf* o0, cdf* o1) {
+    if (a == 0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            o0[c] = cdf_i(v1[c]);
+            o1[c] = cdf_i(v0[c]);
+        }
+    } else if (a == 1) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            o0[c] = v1[c];
+            o1[c] = cdf_neg(v0[c]);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            o0[c] = cdf_i(v0[c]);
+            o1[c] = cdf_neg(cdf_i(v1[c]));
+        }
+    }
+}
+// exact multiplication by +-1
+DD_DEV cdf cdf_sign(cdf a, float sg) {
+    return cdf{dfl{a.re.hi * sg, a.re.lo * sg}, dfl{a.im.hi * sg, a.im.lo * sg}};
+}
+
+// One hop: acc += (1 -+ gamma_a) U psi(y) for the forward hop (sg = +1,
+// U = U_a(x)) or (1 + gamma_a) U_a(y)^dag psi(y) for the backward hop
+// (sg = -1, y = x - a); ph = -1 flips the sign of a time-wrapping hop.  The
+// direction is a runtime value (uniform across the warp): one copy of the
+// body keeps the kernel inside the instruction cache.
+DD_DEV void df_hop(int a, float sg, float ph, int yh, const float4* lk_site, const SpinorDF& in, cdf* acc) {
+    // projected half spinor: upper + sg * (lower pair mapped back)
+    cdf hf[6];
+    {
+        cdf up[6], lo[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            up[k] = in.ld(yh, k);
+            lo[k] = in.ld(yh, 6 + k);
+        }
+        if (a == 3) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) hf[k] = cdf_add(up[k], cdf_sign(lo[k], sg));
+        } else {
+            cdf t[6];
+            df_isigma_rt(a, &lo[0], &lo[3], &t[0], &t[3]);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) hf[k] = cdf_add(up[k], cdf_sign(t[k], sg));
+        }
+    }
+    // U h (forward) or U^dag h (backward): entry (i, j) of the applied matrix
+    // is chunk 3i+j, or the conjugate of chunk 3j+i
+    const long long cs = in.stride;  // links share the per-parity stride Vh
+    cdf uh[6];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        cdf u[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int k = sg > 0.f ? 3 * i + j : 3 * j + i;
+            const float4 v = lk_site[k * cs];
+            u[j] = cdf{dfl{v.x, v.z}, dfl{v.y * sg, v.w * sg}};
+        }
+#pragma unroll
+        for (int sp = 0; sp < 2; ++sp) {
+            const cdf* v = &hf[3 * sp];
+            cdf r;
+            r.re = df_mul(u[0].re, v[0].re);
+            r.im = df_mul(u[0].re, v[0].im);
+            df_mac(r.re, df_neg(u[0].im), v[0].im);
+            df_mac(r.im, u[0].im, v[0].re);
+#pragma unroll
+            for (int j = 1; j < 3; ++j) cdf_mac(r, u[j], v[j]);
+            uh[3 * sp + i] = cdf_sign(r, ph);
+        }
+    }
+    // rebuild the lower spin pair and accumulate
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k] = cdf_add(acc[k], uh[k]);
+    if (a == 3) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc[6 + k] = cdf_add(acc[6 + k], cdf_sign(uh[k], sg));
+    } else {
+        cdf t[6];
+        df_isigma_rt(a, &uh[0], &uh[3], &t[0], &t[3]);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc[6 + k] = cdf_add(acc[6 + k], cdf_sign(t[k], -sg));
+    }
+}
 
 // MODE 0: out = H in; MODE 1: out = xin + c H in; MODE 2: rout = bin - xin + c H in with |rout|^2 / sigma^2
 template <int MASK, int MODE>
@@ -182,87 +257,22 @@ __global__ void __launch_bounds__(128) hop_df_kernel(DFHopArgs A) {
         cdf acc[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) acc[k] = cdf_zero();
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const int loc = x[a] % g.b[a];
-#pragma unroll
-            for (int dir = 1; dir >= -1; dir -= 2) {
-                bool ok = true;
-                if (MASK == 1) ok = dir > 0 ? loc != g.b[a] - 1 : loc != 0;
-                if (!ok) continue;
-                const int yh = neighbour_index(g, s, x, a, dir) >> 1;
-                // projected half spinor: h = upper + sgn * (lower pair mapped back)
-                cdf hf[6];
-                {
-                    cdf up[6], lo[6];
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) {
-                        up[k] = in.ld(yh, k);
-                        lo[k] = in.ld(yh, 6 + k);
-                    }
-                    if (a == 3) {
-#pragma unroll
-                        for (int k = 0; k < 6; ++k) hf[k] = dir > 0 ? cdf_add(up[k], lo[k]) : cdf_sub(up[k], lo[k]);
-                    } else {
-                        cdf t0[3], t1[3];
-                        df_isigma(a, &lo[0], &lo[3], t0, t1);
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            hf[c] = dir > 0 ? cdf_add(up[c], t0[c]) : cdf_sub(up[c], t0[c]);
-                            hf[3 + c] = dir > 0 ? cdf_add(up[3 + c], t1[c]) : cdf_sub(up[3 + c], t1[c]);
-                        }
-                    }
-                }
-                // U h (forward, U_a(x)) or U^dag h (backward, U_a(x - a))
-                cdf uh[6];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    cdf u[3];
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) u[j] = dir > 0 ? lk_p.ld(h, a, 3 * i + j) : lk_q.ld(yh, a, 3 * j + i);
-#pragma unroll
-                    for (int sp = 0; sp < 2; ++sp) {
-                        cdf r = cdf_zero();
-                        if (dir > 0) {
-                            r.re = df_mul(u[0].re, hf[3 * sp].re);
-                            r.im = df_mul(u[0].re, hf[3 * sp].im);
-                            df_mac(r.re, df_neg(u[0].im), hf[3 * sp].im);
-                            df_mac(r.im, u[0].im, hf[3 * sp].re);
-#pragma unroll
-                            for (int j = 1; j < 3; ++j) cdf_mac(r, u[j], hf[3 * sp + j]);
-                        } else {
-                            r.re = df_mul(u[0].re, hf[3 * sp].re);
-                            r.im = df_mul(u[0].re, hf[3 * sp].im);
-                            df_mac(r.re, u[0].im, hf[3 * sp].im);
-                            df_mac(r.im, df_neg(u[0].im), hf[3 * sp].re);
-#pragma unroll
-                            for (int j = 1; j < 3; ++j) cdf_macc(r, u[j], hf[3 * sp + j]);
-                        }
-                        uh[3 * sp + i] = r;
-                    }
-                }
-                // fermion phase on time-wrapping hops
-                const bool flip = (a == 3) && (g.bc < 0) && (dir > 0 ? x[3] == g.L[3] - 1 : x[3] == 0);
-                if (flip) {
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) uh[k] = cdf_neg(uh[k]);
-                }
-                // rebuild the lower spin pair and accumulate
-#pragma unroll
-                for (int k = 0; k < 6; ++k) acc[k] = cdf_add(acc[k], uh[k]);
-                if (a == 3) {
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) acc[6 + k] = dir > 0 ? cdf_add(acc[6 + k], uh[k]) : cdf_sub(acc[6 + k], uh[k]);
-                } else {
-                    cdf t0[3], t1[3];
-                    df_isigma(a, &uh[0], &uh[3], t0, t1);
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        acc[6 + c] = dir > 0 ? cdf_sub(acc[6 + c], t0[c]) : cdf_add(acc[6 + c], t0[c]);
-                        acc[9 + c] = dir > 0 ? cdf_sub(acc[9 + c], t1[c]) : cdf_add(acc[9 + c], t1[c]);
-                    }
-                }
+        // the 8 hops in a runtime loop (see df_hop)
+#pragma unroll 1
+        for (int d = 0; d < 8; ++d) {
+            const int a = d >> 1;
+            const bool fwd = (d & 1) == 0;
+            const int xa = a == 0 ? x[0] : a == 1 ? x[1] : a == 2 ? x[2] : x[3];
+            const int La = g.L[a], ba = g.b[a];
+            if (MASK == 1) {
+                const int loc = xa % ba;
+                if (fwd ? loc == ba - 1 : loc == 0) continue;
             }
+            const int yh = (fwd ? (xa == La - 1 ? s - (La - 1) * g.st[a] : s + g.st[a])
+                                : (xa == 0 ? s + (La - 1) * g.st[a] : s - g.st[a])) >> 1;
+            const float ph = (a == 3 && g.bc < 0 && xa == (fwd ? La - 1 : 0)) ? -1.f : 1.f;
+            const float4* lk_site = fwd ? lk_p.p + (long long)a * 9 * Vh + h : lk_q.p + (long long)a * 9 * Vh + yh;
+            df_hop(a, fwd ? 1.f : -1.f, ph, yh, lk_site, in, acc);
         }
         if (MODE == 0) {
             const SpinorDF out = at_rhs(A.out, rhs);

@@ -26,6 +26,8 @@
 
 int launch_interpolate(dd_handle* h, const double* U, const double* Up, double* out, int num, int den,
                        bool all_links);
+int launch_interpolate_slots(dd_handle* h, const double* U, const double* Up, double* out, long long slot_stride,
+                             int nslots, int den, bool all_links);
 
 namespace {
 
@@ -87,14 +89,16 @@ __global__ void inter_hop_kernel(Geo g, BlockCtx c, const double2* in_bank, doub
     zero(acc);
     if (col == target) {
         const int s = canon_index(g, x);
-        const int bid = block_id_of(g, x);
         for (int a = 0; a < 4; ++a) {
+            // a hop crosses a block face iff x sits on that face (two or more blocks per direction)
+            const int loc = x[a] % g.b[a];
             for (int dir = +1; dir >= -1; dir -= 2) {
+                if (dir > 0 ? loc != g.b[a] - 1 : loc != 0) continue;
                 int y[4] = {x[0], x[1], x[2], x[3]};
                 y[a] += dir;
                 if (y[a] == g.L[a]) y[a] = 0;
                 if (y[a] < 0) y[a] = g.L[a] - 1;
-                if (block_id_of(g, y) == bid || !same_outer_block(ob, x, y)) continue;
+                if (!same_outer_block(ob, x, y)) continue;
                 long long qy = dd_position(g, y);
                 SpinorF64 src{(double2*)in_bank + (long long)i * vs + (qy / c.nb) * 12 * c.nb, c.nb};
                 Spinor<double> sp;
@@ -277,12 +281,13 @@ static int prepare_fields(dd_handle* h, const double* U_old, const double* U_new
                           bool all_links = false) {
     const int nslots = factors ? n + 1 : 2;
     const int ip = h->prm.inner_prec;
+    // all slots of the chain in one launch (slots are equally spaced in the workspace)
+    const long long slot_stride = (long long)(h->fields[1].canon - h->fields[0].canon) * 2;
+    int rc = launch_interpolate_slots(h, U_old, U_new, (double*)h->fields[0].canon, slot_stride, nslots,
+                                      factors ? n : 1, all_links);
+    if (rc) return rc;
     for (int k = 0; k < nslots; ++k) {
         FieldSlot& f = h->fields[k];
-        int num = factors ? k : (k == 0 ? 0 : 1);
-        int den = factors ? n : 1;
-        int rc = launch_interpolate(h, U_old, U_new, (double*)f.canon, num, den, all_links);
-        if (rc) return rc;
         bool need_eo = eo;  // old and new fields both enter even-odd solves
         rc = format_field(h, (const double*)f.canon, f, need_eo, need_eo && ip == DD_PREC_F32,
                           need_eo && ip == DD_PREC_F16, true, true);
@@ -426,24 +431,45 @@ static int dirichlet_solve_bank(dd_handle* h, const double2* in_bank, double2* o
 // element 12 s + k, sub i) on the blocks of colour_mask;
 // b_i = (D_b[U_i] - D_b[U_{i+1}]) eta_i = -kappa (H_b[U_i] - H_b[U_{i+1}]) eta_i,
 // where only the active links differ.
-__global__ void filter_source_kernel(Geo g, int colour_mask, uint64_t seed, uint64_t ctr0,
-                                     const unsigned long long* ctr_off, const double* canon0, long long canon_fs,
-                                     const uint8_t* active, double2* eta_e, double2* eta_o, double2* be,
-                                     double2* bo, double kappa) {
+
+// Block-filter noise: eta on the sites of the blocks in colour_mask (0
+// elsewhere), one Gaussian stream per factor i, stored in even-odd order.
+__global__ void filter_noise_kernel(Geo g, int colour_mask, uint64_t seed, uint64_t ctr0,
+                                    const unsigned long long* ctr_off, double2* eta_e, double2* eta_o) {
     const uint64_t ctr = stream_ctr(ctr0, ctr_off);
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (s >= g.V) return;
     int x[4];
     canon_coords(g, s, x);
-    const bool in = (colour_mask >> block_colour_of(g, x)) & 1;
-    Spinor<double> e, acc;
+    Spinor<double> e;
     zero(e);
-    zero(acc);
-    if (in) {
+    if ((colour_mask >> block_colour_of(g, x)) & 1) {
 #pragma unroll
         for (int k = 0; k < 12; ++k)
             e.c[k] = gaussian((uint32_t)s * 12u + k, DD_PURPOSE_BLOCK_NOISE, (uint32_t)i, seed, ctr);
+    }
+    const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+    SpinorF64 eo{(par ? eta_o : eta_e) + (long long)i * 12 * g.Vh, g.Vh};
+    eo.store(s >> 1, e);
+}
+
+// Block-filter source b = -kappa (D_b[U_i] - D_b[U_{i+1}]) eta restricted to
+// the hops inside a block whose link differs (active links), from the noise
+// stored by filter_noise_kernel (a neighbour inside the block has the same
+// colour, so its noise is stored).
+__global__ void filter_source_kernel(Geo g, int colour_mask, const double* canon0, long long canon_fs,
+                                     const uint8_t* active, const double2* eta_e, const double2* eta_o, double2* be,
+                                     double2* bo, double kappa) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (s >= g.V) return;
+    int x[4];
+    canon_coords(g, s, x);
+    const bool in = (colour_mask >> block_colour_of(g, x)) & 1;
+    Spinor<double> acc;
+    zero(acc);
+    if (in) {
         const double* U1 = canon0 + (long long)i * canon_fs;
         const double* U2 = canon0 + (long long)(i + 1) * canon_fs;
         const int bid = block_id_of(g, x);
@@ -464,10 +490,10 @@ __global__ void filter_source_kernel(Geo g, int colour_mask, uint64_t seed, uint
                     same = same && p1[0] == p2[0] && p1[1] == p2[1];
                 }
                 if (same) continue;
+                const int py = (xy[0] + xy[1] + xy[2] + xy[3]) & 1;
+                const SpinorF64 ein{const_cast<double2*>(py ? eta_o : eta_e) + (long long)i * 12 * g.Vh, g.Vh};
                 Spinor<double> ey;
-#pragma unroll
-                for (int k = 0; k < 12; ++k)
-                    ey.c[k] = gaussian((uint32_t)y * 12u + k, DD_PURPOSE_BLOCK_NOISE, (uint32_t)i, seed, ctr);
+                ein.load(y >> 1, ey);
                 Half<double> hf, uh;
                 project<double>(a, dir, ey, hf);
                 if (dir > 0)
@@ -481,14 +507,10 @@ __global__ void filter_source_kernel(Geo g, int colour_mask, uint64_t seed, uint
         for (int k = 0; k < 12; ++k) acc.c[k] = (-kappa) * acc.c[k];
     }
     const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
-    SpinorF64 eo{(par ? eta_o : eta_e) + (long long)i * 12 * g.Vh, g.Vh};
     SpinorF64 bo_{(par ? bo : be) + (long long)i * 12 * g.Vh, g.Vh};
-    eo.store(s >> 1, e);
     bo_.store(s >> 1, acc);
 }
 
-// ln_b[b] = -sum_i sum_{x in b} (2 Re<eta_i, d_i>_x + |d_i|_x^2), one thread
-// block per block (fixed order); 0 for blocks outside colour_mask
 __global__ void __launch_bounds__(256) filter_estimate_kernel(Geo g, int colour_mask, const double2* eta_e,
                                                               const double2* eta_o, const double2* xe,
                                                               const double2* xo, int n, double* ln_b) {
@@ -532,10 +554,10 @@ static int block_filter_masked(dd_handle* h, int colour_mask, int n, uint64_t se
     double2* eta_o = h->dd_vec + (long long)h->prm.max_rhs * 12 * Vh;
     const long long canon_fs = (long long)(h->fields[1].canon - h->fields[0].canon) * 2;
     dim3 gv(grid_for(g.V, 128), n);
-    DD_KLAUNCH(h, filter_source_kernel<<<gv, 128, 0, h->stream>>>(g, colour_mask, seed, ctr, h->d_ctr_off,
-                                                                 (const double*)h->fields[0].canon, canon_fs,
-                                                                 h->d_active_mask, eta_e, eta_o, v.be, v.bo,
-                                                                 h->prm.kappa));
+    DD_KLAUNCH(h, filter_noise_kernel<<<gv, 128, 0, h->stream>>>(g, colour_mask, seed, ctr, h->d_ctr_off, eta_e, eta_o));
+    DD_KLAUNCH(h, filter_source_kernel<<<gv, 128, 0, h->stream>>>(g, colour_mask, (const double*)h->fields[0].canon,
+                                                                 canon_fs, h->d_active_mask, eta_e, eta_o, v.be,
+                                                                 v.bo, h->prm.kappa));
     DD_LAUNCH_CHECK(h, "filter_source_kernel");
     const int colour = colour_mask == 1 ? 0 : colour_mask == 2 ? 1 : -1;
     int it = 0;

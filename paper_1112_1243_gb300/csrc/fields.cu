@@ -60,6 +60,51 @@ __global__ void interpolate_kernel(long long nlinks, const double* __restrict__ 
     store_m3(o, mul(u, wt));
 }
 
+// Every slot k = 0 .. nslots - 1 of one chain U_{k/den} (slot k at out +
+// k * slot_stride doubles): the eigen-decomposition of U^dag U' is computed
+// once per link for all slots.
+__global__ void interpolate_slots_kernel(long long nlinks, const double* __restrict__ U, const double* __restrict__ Up,
+                                         const uint8_t* __restrict__ active, double* out, long long slot_stride,
+                                         int nslots, int den) {
+    long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nlinks) return;
+    const double* a = U + l * 18;
+    const double* b = Up + l * 18;
+    bool same = true;
+    for (int k = 0; k < 18; ++k) same = same && (a[k] == b[k]);
+    if ((active && !active[l]) || same) {
+        for (int s = 0; s < nslots; ++s) {
+            const double* src = (s == den && !(active && !active[l])) ? b : a;
+            double* o = out + s * slot_stride + l * 18;
+            for (int k = 0; k < 18; ++k) o[k] = src[k];
+        }
+        return;
+    }
+    M3 u = load_m3(a), up = load_m3(b);
+    M3 V;
+    double th[3];
+    su3_eig(mul_dag_left(u, up), V, th);
+    for (int s = 0; s < nslots; ++s) {
+        double* o = out + s * slot_stride + l * 18;
+        if (s == 0) {
+            for (int k = 0; k < 18; ++k) o[k] = a[k];
+        } else if (s == den) {
+            for (int k = 0; k < 18; ++k) o[k] = b[k];
+        } else {
+            store_m3(o, mul(u, su3_power_eig(V, th, (double)s / (double)den)));
+        }
+    }
+}
+
+int launch_interpolate_slots(dd_handle* h, const double* U, const double* Up, double* out, long long slot_stride,
+                             int nslots, int den, bool all_links) {
+    const long long n = (long long)h->g.V * 4;
+    DD_KLAUNCH(h, interpolate_slots_kernel<<<grid_for(n, 128), 128, 0, h->stream>>>(
+                      n, U, Up, all_links ? nullptr : h->d_active_mask, out, slot_stride, nslots, den));
+    DD_LAUNCH_CHECK(h, "interpolate_slots_kernel");
+    return DD_OK;
+}
+
 // all_links: interpolate every link that differs (after a relative gauge
 // fixing), else the active links only (the rest is taken from U)
 int launch_interpolate(dd_handle* h, const double* U, const double* Up, double* out, int num, int den,

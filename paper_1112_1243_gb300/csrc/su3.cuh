@@ -160,7 +160,9 @@ DD_DEV M3 jacobi_eigvecs(M3 K) {
 // Stage 1 diagonalises the Hermitian K = Re(W) + c Im(W) (generic c); stage 2
 // resolves pairs left coupled by (near-)degenerate eigenvalues of K with the
 // orthogonal combination S = Im(e^{-i phi0} W), phi0 = atan(c).
-DD_DEV M3 su3_power(const M3& W, double t) {
+// The decomposition (V, theta) is computed once per link by su3_eig and
+// W^t = V diag(e^{i t theta}) V^dag evaluated per t by su3_power_eig.
+DD_DEV void su3_eig(const M3& W, M3& V, double th[3]) {
     const double c = 0.6180339887498949;
     M3 K;
 #pragma unroll
@@ -172,7 +174,7 @@ DD_DEV M3 su3_power(const M3& W, double t) {
             cpx<double> im = mk<double>(0.5 * (w.y - wd.y) * 1.0, -0.5 * (w.x - wd.x));  // (W - W^dag)/(2i)
             K.m[i][j] = re + c * im;
         }
-    M3 V = jacobi_eigvecs(K);
+    V = jacobi_eigvecs(K);
     const double n0 = 1.0 / sqrt(1.0 + c * c);
     const double ca = n0, sa = c * n0;  // e^{i phi0} = ca + i sa
     for (int sweep = 0; sweep < 3; ++sweep) {
@@ -198,7 +200,6 @@ DD_DEV M3 su3_power(const M3& W, double t) {
         if (!any) break;
     }
     M3 G = mul_dag_left(V, mul(W, V));
-    double th[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) th[j] = atan2(G.m[j][j].y, G.m[j][j].x);
     double sum = th[0] + th[1] + th[2];
@@ -209,6 +210,8 @@ DD_DEV M3 su3_power(const M3& W, double t) {
         int j = (th[0] <= th[1] && th[0] <= th[2]) ? 0 : (th[1] <= th[2] ? 1 : 2);
         th[j] += 6.283185307179586;
     }
+}
+DD_DEV M3 su3_power_eig(const M3& V, const double th[3], double t) {
     M3 out;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -224,4 +227,10 @@ DD_DEV M3 su3_power(const M3& W, double t) {
             out.m[i][j] = s;
         }
     return out;
+}
+DD_DEV M3 su3_power(const M3& W, double t) {
+    M3 V;
+    double th[3];
+    su3_eig(W, V, th);
+    return su3_power_eig(V, th, t);
 }
