@@ -177,7 +177,7 @@ int dd_get_maps(dd_t h, int32_t* nbr, int32_t* sign, int32_t* dd_order, int32_t*
 
 /* out = op(U) in for nrhs spinors (op = DD_OP_*), in precision prec
  * (the FP32/FP16 forms round links and spinors to that storage first).
- * Definition: the Wilson-Dirac operator (Sec. 5: "plain Wilson-Dirac"), its
+ * Definition: the Wilson-Dirac operator (Sec. 5: the unimproved Wilson-Dirac operator), its
  * even-odd Schur complement and the block-interaction terms of Eq. domdec.
  * in/out: device, canonical spinors (even-site vectors for DTILDE/DTILDE_DAG,
  * odd-site in / even-site out for HEO; the sites of one parity in canonical
@@ -221,7 +221,7 @@ int dd_interpolate(dd_t h, void* U_t, const void* U, const void* U_new, int i, i
 int dd_det_ratio_estimate(dd_t h, const void* U_old, const void* U_new, int n, uint64_t seed, uint64_t ctr,
                           int mode, double* ln_out);
 
-/* Block filter (Eq. 4step step 1; Sec. 5 "block-wise accepted"): for every
+/* Block filter (Eq. 4step step 1; Sec. 5, acceptance block by block): for every
  * block of a colour in colour_mask, ln_b[block] (device, nblocks doubles) =
  * sum over n factors of -(2 Re<eta, d> + |d|^2), d = D_b[U_{i+1}]^{-1}
  * (D_b[U_i] - D_b[U_{i+1}]) eta_{b,i} (DD_FILTER_STOCHASTIC, purpose

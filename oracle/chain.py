@@ -1,6 +1,6 @@
 """The hierarchical Markov step (oracle).
 
-Paper Sec. 5 ("3-step algorithm"): update the active links of a block
+Paper Sec. 5 (the three-step algorithm): update the active links of a block
 decomposition, accept the change block-wise with the block determinant
 ratios, repeat this pair "some iterations", then pass the result to the
 global acceptance step with the Schur complement (Eq. 4step steps 0, 1, 3;

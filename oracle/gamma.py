@@ -1,7 +1,7 @@
 """Euclidean gamma matrices in the chiral basis (oracle).
 
-The paper uses "the plain Wilson-Dirac operator" (Sec. 5) without fixing a
-basis.  Reading taken: the chiral basis
+The paper names the unimproved Wilson-Dirac operator (Sec. 5) without fixing
+a basis.  Reading taken: the chiral basis
     gamma_0 = [[0, -1], [-1, 0]],   gamma_k = [[0, -i sigma_k], [i sigma_k, 0]]
 in 2x2 spin blocks, gamma_5 = gamma_0 gamma_1 gamma_2 gamma_3 = diag(1, 1, -1, -1).
 gamma index 0 is time, i.e. lattice axis 3; gamma_k (k = 1, 2, 3) belongs to

@@ -1,4 +1,4 @@
-"""The hierarchical Markov step (Sec. 5, "3-step algorithm"; Eq. 4step
+"""The hierarchical Markov step (Sec. 5, the three-step algorithm; Eq. 4step
 steps 0, 1 and 3) on top of the C ABI.
 
 The step itself runs in libdd.so (dd_chain_step): U0 <- U; n_inner times

@@ -1,5 +1,5 @@
-// Even-odd Wilson hopping kernel (Sec. 5 "plain Wilson-Dirac"; Eq. domdec
-// for the intra-/inter-block restrictions).
+// Even-odd Wilson hopping kernel (Sec. 5, the unimproved Wilson-Dirac
+// operator; Eq. domdec for the intra-/inter-block restrictions).
 //
 // One thread per output site of parity p:
 //   out(x) = a * xin(x) + b * G5out( sum_hops (1 -+ gamma_a) U psi(x +- a) ),

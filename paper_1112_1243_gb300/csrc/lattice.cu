@@ -2,7 +2,7 @@
 // the operator-application entry points (dd_apply_D, dd_apply_D_block).
 //
 // Geometry follows Sec. 3 of the paper: non-overlapping blocks, checkerboard
-// colouring of the blocks, block ordering "black blocks first", and the
+// colouring of the blocks, block ordering with the black blocks first, and the
 // active-link rule (links with at most one endpoint on a block boundary).
 #include <algorithm>
 #include <cmath>

@@ -1,5 +1,5 @@
-// Exact check path (Sec. 3: block determinants "computed exactly by ...
-// LU-decomposition"; Eq. ddfactor for the Schur complement): dense FP64
+// Exact check path (Sec. 3: the block determinants are obtained exactly from
+// an LU factorisation; Eq. ddfactor for the Schur complement): dense FP64
 // complex LU with partial pivoting on the GPU, giving ln|det| of
 //   D      the whole Wilson-Dirac operator (12V x 12V),
 //   D_b    every Dirichlet block operator (batched),

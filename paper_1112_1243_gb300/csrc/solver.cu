@@ -1,18 +1,19 @@
-// Global Krylov solves (Sec. 4: "one inversion for each factor"; the
-// inversions behind the stochastic acceptance steps).
+// Global Krylov solves (Sec. 4: every factor of the stochastic estimate
+// needs one solve; these are the inversions behind the acceptance steps).
 //
 // D x = b is solved through the even-site Schur complement
 //   Dtilde = 1 - kappa^2 H_eo H_oe,  b~ = b_e + kappa H_eo b_o,
-//   x_e = Dtilde^{-1} b~,  x_o = b_o + kappa H_oe x_e,
-// with CG on the normal equations Dtilde^dag Dtilde (CGNR), Dtilde^dag =
-// gamma5 Dtilde gamma5.  The plain FP64 path runs CGNR in FP64.  The mixed
-// path runs CGNR with FP32 arithmetic on FP32 or FP16 storage as the inner
-// solver of an FP64 defect-correction loop:
+//   x_e = Dtilde^{-1} b~,  x_o = b_o + kappa H_oe x_e.
+// The plain FP64 path runs CG on the normal equations Dtilde^dag Dtilde
+// (CGNR, Dtilde^dag = gamma5 Dtilde gamma5) in FP64.  The mixed path runs
+// CGNR or BiCGStab on Dtilde with FP32 arithmetic on FP32 or FP16 storage
+// as the inner solver of an FP64 defect-correction loop:
 //   r = b~ - Dtilde x (FP64), solve Dtilde e = r roughly, x += e,
 // until ||r|| <= tol ||b|| (that is the true residual of D x = b, because
-// x_o is formed exactly from x_e).  All Krylov scalars are FP64 grid
-// reductions finished on the device; the host only checks convergence
-// flags every few iterations.
+// x_o is formed exactly from x_e).  With outer_prec = DD_PREC_DF64 the
+// residual, x and b~ are held in double-float arithmetic instead (see
+// dfhop.cuh).  All Krylov scalars are FP64 grid reductions finished on the
+// device; the host only checks convergence flags every few iterations.
 #include <algorithm>
 #include <cmath>
 #include <vector>

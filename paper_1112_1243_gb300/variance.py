@@ -1,6 +1,6 @@
 """Variance of the stochastic global acceptance step against the number N of
 interpolation factors, its extrapolation in 1/N and the exact acceptance
-rate (Sec. 4, the paragraph of Eq. param; Sec. 5 "Exact acceptance rate";
+rate (Sec. 4, the paragraph of Eq. param; Sec. 5, the paragraph on the exact acceptance rate;
 Eq. acceptance).
 
 With N factors the variance of ln r = sum_i ln r_i over proposals and noise

@@ -2,8 +2,8 @@
 
 Every check compares the oracle with something other than itself: published
 test vectors, the Clifford algebra, brute-force enumeration, and the
-active-link fractions the paper prints (Sec. 5: "about 10%" for 4^4 blocks,
-"8%" for a 6^4 sub-block in each 8^4 block).
+active-link fractions the paper prints (Sec. 5: about 10% for 4^4 blocks,
+8% for a 6^4 sub-block in each 8^4 block).
 """
 import os
 
