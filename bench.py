@@ -203,6 +203,23 @@ def run_reference(args, cfg):
     return 0
 
 
+# FP64 hop: 1320 flops per site for the stencil + 48 for the xpay term;
+# GB300's dense FP64 rate (nominal, no measured FP64 peak on this machine)
+FP64_HOP_FLOPS = 1368
+FP64_PEAK_TFLOPS = 1.25
+
+
+def alu_roofline(sites, ms, flops_per_site, peak_tflops, kernel):
+    """FP64-ALU roofline entry of a kernel from its timed launches (None
+    when nothing was timed)."""
+    if not (ms and ms > 0 and sites and sites > 0):
+        return None
+    achieved = sites * flops_per_site / (ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops, "flops_per_site": flops_per_site,
+            "peak_source": "nominal FP64 rate (no measured FP64 peak)"}
+
+
 def replica_seeds(cfg, rank):
     """Seeds of the independent chain of one rank (replicas: no data-path
     exchange between ranks): gauge-field seed and random-stream seed."""
@@ -331,6 +348,8 @@ def run_gpu(args, cfg):
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "bytes_per_site": HOP_BYTES[kind], "launches_timed": cnt_k,
                      "avg_launch_us": 1e3 * ms_k / max(1, cnt_k), "peak_source": peak_src},
+        "roofline_fp64_hop": alu_roofline(timing[2][2], timing[2][0], FP64_HOP_FLOPS, FP64_PEAK_TFLOPS,
+                                          "hop_eo_kernel kind 2 (FP64 residual hops, whole lattice)"),
         "gpu_launches": launches,
         "clocks": clocks.summary(),
         "D_applications_per_estimate": D_apps_per_est,

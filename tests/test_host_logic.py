@@ -76,3 +76,15 @@ def test_variance_fits_and_acceptance():
     assert abs(variance.fit_through_zero([1, 2, 3], [2.0, 4.0, 6.0]) - 2.0) < 1e-12
     for s2 in (0.0, 0.3, 1.0, 4.0, 25.0):
         assert abs(variance.exact_acceptance(s2) - accept.gaussian_acceptance(s2)) < 1e-15
+
+
+def test_alu_roofline_entry():
+    """The FP64-ALU roofline entry of the benchmark: flops per second from
+    timed sites and milliseconds, against the nominal FP64 peak."""
+    import bench
+    r = bench.alu_roofline(12 * 1048576, 23.0, bench.FP64_HOP_FLOPS, bench.FP64_PEAK_TFLOPS, "k")
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - 12 * 1048576 * 1368 / 0.023 / 1e12) < 1e-12
+    assert abs(r["frac"] - r["achieved"] / 1.25) < 1e-15
+    assert bench.alu_roofline(0, 1.0, 1368, 1.25, "k") is None
+    assert bench.alu_roofline(10, 0.0, 1368, 1.25, "k") is None
