@@ -30,3 +30,15 @@ def test_library_exports_every_declared_symbol():
     # the Python binding covers the same set, with the same names
     assert sorted(_lib.SIGNATURES) == declared_symbols()
     _lib.load()
+
+
+def test_binding_constants_match_the_header():
+    """Every integer constant that include/dd.h defines has the same value in
+    the Python binding (precisions, modes, purposes, error codes)."""
+    from paper_1112_1243_gb300 import _lib
+    text = open(os.path.join(ROOT, "include", "dd.h")).read()
+    defs = re.findall(r"#define\s+(DD_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", text)
+    assert len(defs) > 30
+    for name, value in defs:
+        assert hasattr(_lib, name), name
+        assert getattr(_lib, name) == int(value), name
