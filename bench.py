@@ -71,8 +71,8 @@ def parse():
                    help="also time this many steps with the plain FP64 solver (same workload)")
     p.add_argument("--no-batched-filter", action="store_true",
                    help="skip the uneven-block batched filter measurement")
-    p.add_argument("--compare-config", default="c3",
-                   help="workload of the mixed-versus-FP64 comparison ('' to skip)")
+    p.add_argument("--compare-config", default="c2,c3",
+                   help="workloads of the mixed-versus-FP64 comparison, comma-separated ('' to skip)")
     p.add_argument("--krylov", default="bicgstab", choices=["cgnr", "bicgstab"],
                    help="inner Krylov method of the mixed-precision solves")
     p.add_argument("--mode", default="step", choices=["step", "solve"],
@@ -157,6 +157,67 @@ def oracle_sample(cfg, seconds=20.0):
     return t / n, n, t
 
 
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def _oracle_factor(a):
+    """One factor of the oracle's global estimate (delta form), timed alone;
+    returns (seconds, ln r_i).  Runs in a worker process."""
+    cfg, U, Up, i, n, seed, ctr, tol = a
+    from oracle import estimator, geometry
+    from oracle.interp import interpolate
+    lat = geometry.Lattice(cfg["dims"], cfg["block"])
+    Ui = interpolate(U, Up, i / n, lat.active)
+    Uj = interpolate(U, Up, (i + 1) / n, lat.active)
+    eta = estimator.global_noise(lat, i, seed, ctr)
+    t0 = time.perf_counter()
+    ln = estimator.ln_factor_delta(Ui, Uj, eta, lat, cfg["kappa"], tol=tol)
+    return time.perf_counter() - t0, float(ln)
+
+
+def oracle_estimate_rate(cfg, tol=1e-10, seed=1, ctr=0):
+    """The FP64 numpy oracle's global stochastic estimate on a whole workload
+    (no projection): the proposal (one oracle heat-bath sweep on the active
+    links) is made first; then factor 0 alone on one thread, and all
+    n_global factors at once, one process per core (start method spawn).
+    Returns estimates/s for both and what was run."""
+    import multiprocessing as mp
+    from oracle import geometry, heatbath
+    from paper_1112_1243_gb300 import synthetic
+    lat = geometry.Lattice(cfg["dims"], cfg["block"])
+    U = synthetic.random_gauge(cfg["dims"], cfg["eps"], cfg["seed"])
+    Up, _ = heatbath.gauge_update(U, lat, BETA, 1, 0, seed, ctr)
+    n = cfg["n_global"]
+    t1, _ = _oracle_factor((cfg, U, Up, 0, n, seed, ctr, tol))
+    cores = max(1, min(n, os.cpu_count() or 1))
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            pool.map(abs, range(cores))          # workers started and imported before timing
+            w0 = time.perf_counter()
+            res = pool.map(_oracle_factor, [(cfg, U, Up, i, n, seed, ctr, tol) for i in range(n)], chunksize=1)
+            wall = time.perf_counter() - w0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return {"one_thread": 1.0 / t1, "all_cores": n / wall, "cores": cores, "seconds_one_factor": t1,
+            "seconds_all_factors": wall, "factors": n, "tol": tol}
+
+
 def site_hops_per_estimate_default(cfg_name):
     """Full-lattice Wilson applications per global estimate, measured on the
     GPU path (global solve only) and recorded in profiles/; used by the
@@ -203,21 +264,63 @@ def run_reference(args, cfg):
     return 0
 
 
-# FP64 hop: 1320 flops per site for the stencil + 48 for the xpay term;
-# GB300's dense FP64 rate (nominal, no measured FP64 peak on this machine)
+# FP64 hop: 1320 flops per site for the stencil (165 per hop) + 48 for the xpay term
 FP64_HOP_FLOPS = 1368
-FP64_PEAK_TFLOPS = 1.25
+FLOPS_PER_HOP = 165
+# one BiCGStab iteration of the persistent block solver, per block site (FP32):
+# two Dirichlet applications (1368 flops each at most) + the vector updates and
+# inner products (about 960 flops over the 12 complex components)
+BLOCK_ITER_FLOPS = 2 * FP64_HOP_FLOPS + 960
+# unit counts and clock (152 SMs, 2070 MHz): FP64 2 FMA per SM per cycle,
+# FP32 128 FMA per SM per cycle -- the fallback when the live probe fails
+DERIVED_PEAKS = {"fp64_fma": 152 * 2 * 2 * 2.07e9 / 1e12, "fp32_fma": 152 * 128 * 2 * 2.07e9 / 1e12}
 
 
-def alu_roofline(sites, ms, flops_per_site, peak_tflops, kernel):
-    """FP64-ALU roofline entry of a kernel from its timed launches (None
-    when nothing was timed)."""
-    if not (ms and ms > 0 and sites and sites > 0):
+def hops_kept(block):
+    """Hops per site that stay inside a block (of 8), averaged over the block."""
+    return sum(2.0 * (1.0 - 1.0 / b) for b in block)
+
+
+def kernel_models(block):
+    """Timed kernel kinds -> (name, bound, algorithmic bytes per unit, flops
+    per unit, unit).  Units: output sites of one right-hand side (hops); block
+    sites x inner iterations (persistent block solver)."""
+    k = hops_kept(block)
+    return {
+        0: ("hop_eo_kernel FP16 -> FP16, whole lattice", "hbm", HOP_BYTES[0], 1320, "site"),
+        1: ("hop_eo_kernel FP16 -> FP32 + xpay, whole lattice", "hbm", HOP_BYTES[1], 1368, "site"),
+        2: ("hop_eo_kernel FP64 (defect-correction residual), whole lattice", "fp64", HOP_BYTES[2], 1368, "site"),
+        3: ("hop_df_kernel double-float residual, whole lattice", "fp32", HOP_BYTES[3], 8600, "site"),
+        4: ("hop_eo_kernel FP64 (defect-correction residual), Dirichlet blocks", "fp64",
+            192 + 144 * k + 192, 48 + FLOPS_PER_HOP * k, "site"),
+        5: ("hop_eo_kernel FP16 -> FP16, Dirichlet blocks", "hbm", 52 + 24 * k + 52, FLOPS_PER_HOP * k, "site"),
+        6: ("hop_eo_kernel FP16 -> FP32 + xpay, Dirichlet blocks", "hbm", 52 + 24 * k + 96 + 96,
+            48 + FLOPS_PER_HOP * k, "site"),
+        7: ("block_solve_kernel (persistent, FP32 BiCGStab + FP64 refinement)", "fp32", None, BLOCK_ITER_FLOPS,
+            "block site x inner iteration"),
+    }
+
+
+def roofline_entry(kind, model, ms, launches, units, step_ms, hbm_peak, alu, alu_src):
+    """Roofline entry of one timed kernel kind (None when nothing was timed)."""
+    name, bound, bpu, fpu, unit = model
+    if not (ms and ms > 0 and units and units > 0):
         return None
-    achieved = sites * flops_per_site / (ms / 1e3) / 1e12
-    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved / peak_tflops, "flops_per_site": flops_per_site,
-            "peak_source": "nominal FP64 rate (no measured FP64 peak)"}
+    e = {"kind": kind, "kernel": name, "launches_timed": launches, "total_ms": ms,
+         "share_of_step": ms / step_ms if step_ms else None, "avg_launch_us": 1e3 * ms / max(1, launches),
+         "units": units, "unit": unit}
+    if bound == "hbm":
+        ach = units * bpu / 1e9 / (ms / 1e3)
+        e.update(bound="hbm", achieved=ach, peak=hbm_peak, unit_rate="GB/s", frac=ach / hbm_peak,
+                 bytes_per_unit=bpu)
+    else:
+        key = "fp64_fma" if bound == "fp64" else "fp32_fma"
+        ach = units * fpu / 1e12 / (ms / 1e3)
+        e.update(bound="alu", pipe=key, achieved=ach, peak=alu[key], unit_rate="TFLOP/s", frac=ach / alu[key],
+                 flops_per_unit=fpu, peak_source=alu_src)
+        if bpu:
+            e["GB_per_s"] = units * bpu / 1e9 / (ms / 1e3)
+    return e
 
 
 def replica_seeds(cfg, rank):
@@ -292,6 +395,11 @@ def run_gpu(args, cfg):
         del Up_t
     chain = HierarchicalStep(h, BETA, n_inner=1, n_block=cfg["n_block"], n_global=cfg["n_global"],
                              seed=replica_seeds(cfg, rank)[1])
+    # roofline denominators of the ALU-bound kernels, measured on this GPU
+    try:
+        alu, alu_src = api.dd_alu_peaks(stream), "measured live (dd_alu_peaks: FMA chains, CUDA events)"
+    except api.DDError:
+        alu, alu_src = dict(DERIVED_PEAKS), "derived: SM count x FMA units per cycle x 2070 MHz"
 
     def barrier():
         if world > 1:
@@ -313,16 +421,24 @@ def run_gpu(args, cfg):
         barrier()
     t_ms = e0.elapsed_time(e1)
     launches = api.dd_launch_count(h) - l0
-    timing = {kind: api.dd_kernel_timer(h, 2, kind) for kind in (0, 1, 2, 3)}
+    timing = {kind: api.dd_kernel_timer(h, 2, kind) for kind in range(api.DD_TIMER_KIND_COUNT)}
+    stats = {name: api.dd_solver_stats(h, k) for k, name in ((0, "global"), (1, "dirichlet"), (2, "block_solver"))}
     api.dd_kernel_timer(h, 0, 0)
     t_max = max_over_ranks(t_ms, world, dev)
     est = cfg["n_global"] * args.steps * world
     value = job_rate(cfg["n_global"] * args.steps, world, t_max)
-    # dominant hop kernel: the kind with most time
-    kind = max((0, 1, 2), key=lambda k: timing[k][0])
-    ms_k, cnt_k, sites_k = timing[kind]
     peak, peak_src = peaks()
-    achieved = (sites_k * HOP_BYTES[kind] / 1e9) / (ms_k / 1e3) if ms_k > 0 else None
+    models = kernel_models(cfg["block"])
+    # persistent block solver: its unit is a block site x inner iteration
+    units = {k: timing[k][2] for k in timing}
+    units[7] = stats["block_solver"]["site_iterations"]
+    entries = [roofline_entry(k, models[k], timing[k][0], timing[k][1], units[k], t_ms, peak, alu, alu_src)
+               for k in sorted(models)]
+    entries = [e for e in entries if e]
+    # the roofline line: the timed kernel kind with the most time in the step
+    dom = max(entries, key=lambda e: e["total_ms"])
+    kind = dom["kind"]
+    ms_k, cnt_k, sites_k = timing[kind]
     traffic = None
     try:
         with open(os.path.join(ROOT, "profiles", "hop_traffic.json")) as f:
@@ -333,9 +449,29 @@ def run_gpu(args, cfg):
             traffic = tr["bytes_per_site"][str(kind)] * (sites_k / max(1, cnt_k))
     except Exception:
         traffic = None
-    # hop work per estimate (global solve only), for the CPU-baseline scaling
-    hop_sites = sum(timing[k][2] for k in (0, 1, 2, 3))
-    D_apps_per_est = hop_sites / (2.0 * Vh) / max(1, cfg["n_global"] * args.steps) * 1.0
+    # Wilson applications per estimate: whole-lattice and Dirichlet hops (two
+    # hops of Vh sites = one application of V sites) and the persistent block
+    # solver (two Dirichlet applications per inner iteration)
+    hop_sites = sum(timing[k][2] for k in (0, 1, 2, 3, 4, 5, 6))
+    blk_apps = 2.0 * stats["block_solver"]["site_iterations"]
+    D_apps_per_est = (hop_sites / (2.0 * Vh) + blk_apps / V) / max(1, cfg["n_global"] * args.steps)
+    iterations = {}
+    for name, st in stats.items():
+        n = st["systems"] if "systems" in st else st["items"]
+        iterations[name] = dict(st, inner_per_system=st["inner_iterations"] / n if n else None,
+                                outer_per_system=st["outer_cycles"] / n if n else None)
+    if dom["bound"] == "hbm":
+        roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": dom["achieved"], "peak": peak,
+                    "unit": "GB/s", "frac": dom["frac"], "traffic": traffic,
+                    "bytes_per_site": dom["bytes_per_unit"], "launches_timed": cnt_k,
+                    "avg_launch_us": dom["avg_launch_us"], "share_of_step": dom["share_of_step"],
+                    "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        roofline = {"bound": "alu", "kernel": dom["kernel"], "achieved": dom["achieved"], "peak": dom["peak"],
+                    "unit": "TFLOP/s", "frac": dom["frac"], "traffic": traffic,
+                    "flops_per_site": dom["flops_per_unit"], "launches_timed": cnt_k,
+                    "avg_launch_us": dom["avg_launch_us"], "share_of_step": dom["share_of_step"],
+                    "peak_source": dom["peak_source"]}
     line = {
         "metric": METRIC, "value": value, "unit": "estimates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -343,13 +479,10 @@ def run_gpu(args, cfg):
         "dtype": {"f16": "f16-storage/f32", "f32": "f32", "f64": "f64"}[args.prec] + "+" + args.outer,
         "data": "synthetic",
         "config": config_dict(args, cfg, world),
-        "roofline": {"bound": "hbm", "kernel": f"hop_eo_kernel kind {kind}",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "bytes_per_site": HOP_BYTES[kind], "launches_timed": cnt_k,
-                     "avg_launch_us": 1e3 * ms_k / max(1, cnt_k), "peak_source": peak_src},
-        "roofline_fp64_hop": alu_roofline(timing[2][2], timing[2][0], FP64_HOP_FLOPS, FP64_PEAK_TFLOPS,
-                                          "hop_eo_kernel kind 2 (FP64 residual hops, whole lattice)"),
+        "roofline": roofline,
+        "rooflines": entries,
+        "alu_peaks": dict(alu, source=alu_src),
+        "iterations": iterations,
         "gpu_launches": launches,
         "clocks": clocks.summary(),
         "D_applications_per_estimate": D_apps_per_est,
@@ -418,21 +551,34 @@ def run_gpu(args, cfg):
     if not args.no_outer_df64 and args.outer == "f64" and args.prec != "f64":
         line["outer_df64"] = measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune)
     if args.compare_config:
-        # mixed versus plain FP64 on a smaller workload (the FP64 path at the
+        # mixed versus plain FP64 on smaller workloads (the FP64 path at the
         # full volume would hold the GPU for minutes per step)
-        line["mixed_vs_fp64"] = compare_precisions(args, CONFIGS[args.compare_config], dev, stream, rank)
+        line["mixed_vs_fp64"] = {name: compare_precisions(args, CONFIGS[name], dev, stream, rank)
+                                 for name in args.compare_config.split(",") if name}
     if not args.no_batched_filter:
         line["batched_filter"] = measure_batched_filter(dev, stream)
     if not args.no_recursive:
         line["recursive"] = measure_recursive(cfg, dev, stream)
     if rank == 0 and not args.no_cpu_baseline:
+        c2 = CONFIGS["c2"]
+        r = oracle_estimate_rate(c2)
         per_app, n, t = oracle_sample(cfg, seconds=15.0)
         line["cpu_baseline"] = {
-            "value": 1.0 / (max(D_apps_per_est, 1e-9) * per_app), "unit": "estimates/s", "cores": 1,
-            "kind": "oracle",
-            "sample": f"numpy FP64 oracle apply_D at V={V}: {n} applications in {t:.1f} s, scaled by "
-                      f"{D_apps_per_est:.0f} Wilson applications per estimate measured on this run "
-                      f"(global solve only; block solves not counted)"}
+            "value": r["all_cores"], "unit": "estimates/s", "cores": r["cores"], "kind": "oracle",
+            "projected": False, "cpu": cpu_model(), "nproc": os.cpu_count(),
+            "one_thread": r["one_thread"],
+            "workload": "c2: 8^4 lattice, 4^4 blocks (active set of Sec. 3), eps 0.3, kappa 0.13, 16 factors",
+            "sample": f"numpy FP64 oracle, whole global estimate of c2 (Schur pieces + global solve, delta form, "
+                      f"every solve to relative residual 1e-10; proposal made before timing): factor 0 alone on "
+                      f"one thread {r['seconds_one_factor']:.1f} s; all {r['factors']} factors, one process per "
+                      f"core on {r['cores']} cores, {r['seconds_all_factors']:.1f} s",
+            "gpu_same_workload": line.get("mixed_vs_fp64", {}).get("c2"),
+            "c5_projection": {
+                "value": 1.0 / (max(D_apps_per_est, 1e-9) * per_app), "unit": "estimates/s", "cores": 1,
+                "projected": True,
+                "sample": f"numpy FP64 oracle apply_D at V={V}: {n} applications in {t:.1f} s, scaled by "
+                          f"{D_apps_per_est:.0f} Wilson applications per estimate measured on this run "
+                          f"(global, Dirichlet and block-solver applications)"}}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -152,7 +152,9 @@ int dd_default_params(dd_params* p);
  * uploads them (the only allocation the library makes itself).
  * Errors: DD_ERR_INVALID_ARG for odd or non-dividing extents, blocks per
  * direction odd or < 2, kappa <= 0, max_rhs < 1, an unknown precision or
- * active mode; DD_ERR_CUDA on a CUDA error. */
+ * active mode, more than 2^30 sites; DD_ERR_UNSUPPORTED when 12 V >= 2^32
+ * (the noise streams number the spinor components of site s as 12 s + k in
+ * one 32-bit counter word, which would wrap); DD_ERR_CUDA on a CUDA error. */
 int dd_init(dd_t* h, const dd_params* p, void* stream);
 
 /* Bytes of device workspace the handle needs for its max_rhs. */
@@ -338,6 +340,31 @@ const char* dd_last_error(dd_t h);
  * Event recording adds well under a microsecond per timed launch. */
 int dd_launch_count(dd_t h, long long* launches);
 int dd_kernel_timer(dd_t h, int op, int kind, int every, double* total_ms, long long* timed, long long* sites);
+/* Timer kinds beyond the whole-lattice hops 0-3: 4 FP64, 5 FP16 -> FP16 and
+ * 6 FP16 -> FP32 hops restricted to the blocks (Dirichlet solves of the
+ * Schur pieces and of the whole-lattice filter form); 7 the persistent block
+ * solver (sites = block items of the timed launches). */
+#define DD_TIMER_KIND_COUNT 8
+
+/* Iteration counts of the solves since the last dd_kernel_timer(op 1) (the
+ * paper has no counterpart: work accounting for the measurement).  kind 0:
+ * whole-lattice defect-correction solves (dd_solve, the global step); 1:
+ * Dirichlet solves restricted to the blocks (Schur pieces, whole-lattice
+ * filter form); 2: the persistent block solver.  out (host, 4 long long):
+ * kinds 0-1: systems solved, inner Krylov iterations summed over systems,
+ * outer (defect-correction) cycles, sites x inner iterations; kind 2: block
+ * items, inner iterations, outer cycles, sites x inner iterations.  Kinds 0-1
+ * count eager (polled) solves only; kind 2 synchronises the stream. */
+int dd_solver_stats(dd_t h, int kind, long long* out);
+
+/* Arithmetic peaks of the current GPU, measured (the paper has no
+ * counterpart: roofline denominators of the ALU-bound kernels).  Fills
+ * tflops[0] FP64 FMA, [1] FP32 FMA, [2] FP64 mma.sync m8n8k4 (tensor core)
+ * throughput in TFLOP/s: 8 thread blocks of 256 threads per SM, eight
+ * independent chains per thread, best of three CUDA-event timed launches on
+ * `stream`.  Allocates and frees one small device buffer; takes well under a
+ * second.  Returns DD_OK, DD_ERR_INVALID_ARG (tflops NULL) or DD_ERR_CUDA. */
+int dd_alu_peaks(double* tflops, void* stream);
 
 /* Allocation-free block log-ratios (the paper has no counterpart: this is an
  * interface variant for callers that cannot allocate device memory — code
@@ -350,11 +377,19 @@ int dd_kernel_timer(dd_t h, int op, int kind, int every, double* total_ms, long 
  *   ln_b[block id] = -(2 Re<eta, d> + |d|^2),  d = D_b[U_new]^{-1} (D_b[U_old] - D_b[U_new]) eta_b,
  * eta_b from purpose DD_PURPOSE_BLOCK_NOISE, sub 0 (the values dd_block_filter
  * gives for n = 1 when U_new differs from U_old only on active links);
- * 0 for the other blocks.  Same solver as dd_block_filter: FP32 inner CG,
- * FP64 defect correction to relative residual tol_block.
+ * 0 for the other blocks.  Solver (fixed caps, not the handle settings of
+ * dd_block_filter): FP64 defect correction to relative residual tol_block,
+ * at most 12 cycles, around an FP32 conjugate-gradient solve of the block's
+ * normal equations (relative target 1e-10, at most 2000 iterations per
+ * cycle).  dd_block_filter's inner solver is BiCGStab: both reach tol_block,
+ * by different iterations.  A block whose refinement does not reach
+ * tol_block within the 12 cycles, or whose residual or result is not finite,
+ * gets ln_b = NaN (the failure shows in the caller's own output, since the
+ * entry point has no handle and no status word).
  * dims/block: host arrays (extents even, blocks per direction even and >= 2);
  * U_old, U_new: device, canonical FP64 gauge fields; ln_b: device, nblocks
  * doubles.  Work is enqueued on `stream` (a cudaStream_t, NULL = default).
+ * 12 V >= 2^32 (V = sites): DD_ERR_UNSUPPORTED, as in dd_init.
  * Scratch: one file-scope device array of 64 MiB, held by every GPU that
  * loads the library until the process exits; a block may have at most
  * 64 MiB / 1248 B (about 53000) sites, else DD_ERR_UNSUPPORTED.  The first

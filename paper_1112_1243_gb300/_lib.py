@@ -32,6 +32,7 @@ DD_PURPOSE_BLOCK_SCHUR_NOISE = 4
 DD_PURPOSE_BLOCK_SCHUR_ACCEPT = 8
 DD_EST_FACTORS, DD_EST_REPLICAS, DD_EST_INTERP_ALL = 0, 1, 4
 DD_FILTER_STOCHASTIC, DD_FILTER_EXACT = 0, 1
+DD_TIMER_KIND_COUNT = 8
 
 ERROR_NAMES = {
     DD_ERR_INVALID_ARG: "DD_ERR_INVALID_ARG",
@@ -133,6 +134,8 @@ SIGNATURES = {
     "dd_launch_count": [_P, ctypes.POINTER(ctypes.c_longlong)],
     "dd_kernel_timer": [_P, _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong),
                         ctypes.POINTER(ctypes.c_longlong)],
+    "dd_solver_stats": [_P, _I, ctypes.POINTER(ctypes.c_longlong)],
+    "dd_alu_peaks": [ctypes.POINTER(_D), _P],
     "dd_block_ratios_noalloc": [ctypes.POINTER(_I), ctypes.POINTER(_I), _D, _I, _I, _P, _P, _U64, _U64, _D, _P,
                                 _P],
     "dd_chain_step": [_P, _P, ctypes.POINTER(dd_chain_params), ctypes.POINTER(dd_chain_buffers), ctypes.c_ulonglong],

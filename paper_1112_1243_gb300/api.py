@@ -285,6 +285,26 @@ def dd_kernel_timer(h, op, kind=0, every=1):
     return ms.value, cnt.value, sites.value
 
 
+def dd_solver_stats(h, kind):
+    """kind 0 whole-lattice solves, 1 Dirichlet solves, 2 persistent block
+    solver -> dict of the counters since the last dd_kernel_timer(op 1)."""
+    out = (ctypes.c_longlong * 4)()
+    _check(h, _lib.load().dd_solver_stats(h.ptr, int(kind), out))
+    names = ("systems", "inner_iterations", "outer_cycles", "site_iterations") if kind < 2 else \
+        ("items", "inner_iterations", "outer_cycles", "site_iterations")
+    return dict(zip(names, list(out)))
+
+
+def dd_alu_peaks(stream=None):
+    """Measured FP64 FMA, FP32 FMA and FP64 mma.sync throughput (TFLOP/s) of the current GPU."""
+    out = (ctypes.c_double * 3)()
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    rc = _lib.load().dd_alu_peaks(out, ctypes.c_void_p(s))
+    if rc != _lib.DD_OK:
+        raise DDError(rc, "dd_alu_peaks failed")
+    return {"fp64_fma": out[0], "fp32_fma": out[1], "fp64_mma": out[2]}
+
+
 def dd_block_ratios_noalloc(dims, block, kappa, bc_time, colour_mask, U_old, U_new, seed, ctr, tol_block, ln_b,
                             stream=None):
     """Allocation-free one-factor block log-ratios (no handle, no workspace);

@@ -407,6 +407,7 @@ struct BlockArgs {
     int max_outer;
     int inner_f64;
     int* status;
+    unsigned long long* stats;  // items, inner iterations, outer cycles, site-iterations (may be null)
 };
 
 // block id of the block at position pos of the block order
@@ -537,6 +538,7 @@ __global__ void __launch_bounds__(256, 2) block_solve_kernel(BlockArgs A) {
         bb = block_sum(bb, sh);
         double rr = bb;
         int outer = 0;
+        long long inner_its = 0;
         while (rr > A.tol2 * bb && outer < A.max_outer) {
             // inner right-hand side: the FP64 residual, normalised to unit norm
             const double rn = sqrt(rr), rinv = 1.0 / rn;
@@ -553,9 +555,9 @@ __global__ void __launch_bounds__(256, 2) block_solve_kernel(BlockArgs A) {
                 // room for the seven BiCGStab vectors
                 SI hi = scratch_spinor<SI>(ib, 5, nb), si = scratch_spinor<SI>(ib, 6, nb),
                    ti = scratch_spinor<SI>(ib, 7, nb);
-                block_bicgstab<RI>(c, xi, ri, hi, pi, qi, si, ti, lsoli, A.tol2_inner, A.maxit_inner, sh);
+                inner_its += block_bicgstab<RI>(c, xi, ri, hi, pi, qi, si, ti, lsoli, A.tol2_inner, A.maxit_inner, sh);
             } else {
-                block_cgnr<RI>(c, xi, ri, pi, qi, zi, lsoli, A.tol2_inner, A.maxit_inner, sh);
+                inner_its += block_cgnr<RI>(c, xi, ri, pi, qi, zi, lsoli, A.tol2_inner, A.maxit_inner, sh);
             }
             // x += |r| e; r = b - D_b x (FP64)
             for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
@@ -584,6 +586,12 @@ __global__ void __launch_bounds__(256, 2) block_solve_kernel(BlockArgs A) {
             ++outer;
         }
         if (rr > A.tol2 * bb && threadIdx.x == 0) raise_status(A.status, DD_ERR_NOT_CONVERGED);
+        if (A.stats && threadIdx.x == 0) {
+            atomicAdd(A.stats, 1ull);
+            atomicAdd(A.stats + 1, (unsigned long long)inner_its);
+            atomicAdd(A.stats + 2, (unsigned long long)outer);
+            atomicAdd(A.stats + 3, (unsigned long long)inner_its * (unsigned long long)nb);
+        }
         if (!isfinite(rr) && threadIdx.x == 0) raise_status(A.status, DD_ERR_NUMERIC);
         // ---- results
         if (A.mode == BLOCK_FILTER) {

@@ -93,8 +93,13 @@ struct SolverVecs {
 };
 
 constexpr int DD_BLOCK_CTAS_MAX = 4;
-// timed hop kinds: 0 FP16 -> FP16, 1 FP16 -> FP32 (xpay), 2 FP64, 3 double-float
-constexpr int DD_TIMER_KINDS = 4;  // scratch slots of the persistent block solver per SM
+// timed kernel kinds: whole-lattice hops 0 FP16 -> FP16, 1 FP16 -> FP32 (xpay),
+// 2 FP64, 3 double-float residual; Dirichlet (block-restricted) hops 4 FP64,
+// 5 FP16 -> FP16, 6 FP16 -> FP32; 7 the persistent block solver
+constexpr int DD_TIMER_KINDS = 8;
+// device counters after the timer sites: items, inner iterations, outer
+// cycles and site-iterations of the persistent block solver
+constexpr int DD_BLOCK_STATS = 4;
 
 // Launch shapes chosen by the autotuner (dd_autotune); defaults are the
 // shapes the kernels were written for.
@@ -153,7 +158,12 @@ struct dd_handle {
     unsigned long long timer_seen[DD_TIMER_KINDS] = {};
     std::vector<cudaEvent_t> timer_ev[DD_TIMER_KINDS];
     size_t timer_used[DD_TIMER_KINDS] = {};
-    unsigned long long* d_sites = nullptr;  // [DD_TIMER_KINDS] output sites of the timed launches
+    unsigned long long* d_sites = nullptr;  // [DD_TIMER_KINDS + DD_BLOCK_STATS] output sites of the timed launches,
+                                            // then the block-solver counters
+    // host counters of the polled (eager) defect-correction solves:
+    // [0] whole-lattice solves, [1] Dirichlet solves; {systems, inner
+    // iterations, outer cycles, site-iterations}; reset with the timer
+    long long solve_stats[2][4] = {};
     // even-odd indices of the sites of each block colour (null when the
     // block extent along axis 0 is odd); Dirichlet solves of one colour
     // visit only these

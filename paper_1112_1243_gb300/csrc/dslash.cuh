@@ -205,9 +205,11 @@ inline void launch_hop(const HopArgs<SIn, SX, SOut, LK>& A, int nrhs, dd_handle*
     constexpr int SPT2 = std::is_same<R, double>::value ? 1 : 2;
     const int spt = (!f64 && h->tune.hop_spt == 2) ? 2 : 1;
     dim3 grid(grid_for(B.S.n, (long long)tpb * spt), nrhs);
-    constexpr int kind = hop_kind<SIn, SOut>();
+    constexpr int kind0 = hop_kind<SIn, SOut>();
+    // whole-lattice hops keep kinds 0-2; Dirichlet hops are timed as 4 (FP64), 5, 6
+    constexpr int kind = MASK == 0 ? kind0 : (MASK == 1 && kind0 >= 0 ? (kind0 == 2 ? 4 : 5 + kind0) : -1);
     bool timed = false;
-    if (kind >= 0 && MASK == 0 && h->timer_on && !h->capturing && !dd_stream_capturing(h)) timed = (h->timer_seen[kind]++ % h->timer_every) == 0;
+    if (kind >= 0 && h->timer_on && !h->capturing && !dd_stream_capturing(h)) timed = (h->timer_seen[kind]++ % h->timer_every) == 0;
     B.sites = nullptr;
     if (timed) {
         cudaEvent_t e = dd_timer_event(h, kind);

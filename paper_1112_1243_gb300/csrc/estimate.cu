@@ -296,6 +296,23 @@ static int prepare_fields(dd_handle* h, const double* U_old, const double* U_new
     return DD_OK;
 }
 
+// CUDA-event timing of a persistent block-solver launch (timer kind 7; the
+// item count is added to the kind's site counter)
+__global__ void add_count_kernel(unsigned long long* p, unsigned long long v) { *p += v; }
+static bool block_timer_begin(dd_handle* h) {
+    const int kind = 7;
+    if (!h->timer_on || h->capturing || dd_stream_capturing(h)) return false;
+    if ((h->timer_seen[kind]++ % h->timer_every) != 0) return false;
+    cudaEvent_t e = dd_timer_event(h, kind);
+    if (e) cudaEventRecord(e, h->stream);
+    return true;
+}
+static void block_timer_end(dd_handle* h, int nitems) {
+    cudaEvent_t e = dd_timer_event(h, 7);
+    if (e) cudaEventRecord(e, h->stream);
+    add_count_kernel<<<1, 1, 0, h->stream>>>(h->d_sites + 7, (unsigned long long)nitems);
+}
+
 // block-filter items of the blocks at positions pos0 .. pos0 + nitems / n - 1,
 // n noise vectors each, in one persistent launch
 static int launch_blocks(dd_handle* h, int mode, int pos0, int n, int nitems, const double2* in_bank,
@@ -332,12 +349,15 @@ static int launch_blocks(dd_handle* h, int mode, int pos0, int n, int nitems, co
     A.maxit_inner = std::min(h->prm.maxit, 2000);
     A.max_outer = A.inner_f64 ? 3 : 12;
     A.status = h->d_status;
+    A.stats = h->d_sites + DD_TIMER_KINDS;
     const int grid = std::min(nitems, std::min(h->block_slots, std::max(1, h->num_sms) * h->tune.block_ctas_per_sm));
     const int tpb = h->tune.block_tpb;
+    const bool timed = block_timer_begin(h);
     if (A.inner_f64)
         DD_KLAUNCH(h, block_solve_kernel<double, SpinorF64, LinkF64><<<grid, tpb, 0, h->stream>>>(A));
     else
         DD_KLAUNCH(h, block_solve_kernel<float, SpinorF32, LinkF32><<<grid, tpb, 0, h->stream>>>(A));
+    if (timed) block_timer_end(h, nitems);
     DD_LAUNCH_CHECK(h, "block_solve_kernel");
     return DD_OK;
 }
@@ -808,12 +828,15 @@ extern "C" int dd_block_filter_batch(int nh, const dd_t* hs_, const void* const*
         A.maxit_inner = std::min(h0->prm.maxit, 2000);
         A.max_outer = A.inner_f64 ? 3 : 12;
         A.status = h0->d_status;
+        A.stats = h0->d_sites + DD_TIMER_KINDS;
         const int grid = std::min((int)items.size(), P.slots);
         const int tpb = h0->tune.block_tpb;
+        const bool timed = block_timer_begin(h0);
         if (A.inner_f64)
             DD_KLAUNCH(h0, block_solve_kernel<double, SpinorF64, LinkF64><<<grid, tpb, 0, s>>>(A));
         else
             DD_KLAUNCH(h0, block_solve_kernel<float, SpinorF32, LinkF32><<<grid, tpb, 0, s>>>(A));
+        if (timed) block_timer_end(h0, (int)items.size());
         DD_LAUNCH_CHECK(h0, "block_solve_kernel (batch)");
     }
     for (int k = 0; k < nh; ++k) {

@@ -474,6 +474,12 @@ extern "C" int dd_init(dd_t* out, const dd_params* p, void* stream) {
         delete h;
         return DD_ERR_INVALID_ARG;
     }
+    // the random streams number the spinor components of a site 12 s + k in
+    // one 32-bit counter word: a larger lattice would repeat its noise
+    if (12 * V > 0xFFFFFFFFLL) {
+        delete h;
+        return DD_ERR_UNSUPPORTED;
+    }
     if (p->inner_prec < DD_PREC_F64 || p->inner_prec > DD_PREC_F16 || p->block_prec < DD_PREC_F64 ||
         p->block_prec > DD_PREC_F32 || p->active_mode < DD_ACTIVE_AUTO || p->active_mode > DD_ACTIVE_ALL ||
         (p->outer_prec != DD_PREC_F64 && p->outer_prec != DD_PREC_DF64)) {
@@ -551,8 +557,8 @@ extern "C" int dd_init(dd_t* out, const dd_params* p, void* stream) {
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_hb_fails, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(h->d_hb_fails, 0, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_sites, DD_TIMER_KINDS * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(h->d_sites, 0, DD_TIMER_KINDS * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_sites, (DD_TIMER_KINDS + DD_BLOCK_STATS) * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(h->d_sites, 0, (DD_TIMER_KINDS + DD_BLOCK_STATS) * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_ctr_off, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(h->d_ctr_off, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_loop, sizeof(int) * DD_LOOP_SLOTS);
@@ -690,7 +696,10 @@ extern "C" int dd_kernel_timer(dd_t h, int op, int kind, int every, double* tota
             h->timer_used[k] = 0;
             h->timer_seen[k] = 0;
         }
-        DD_CUDA(h, cudaMemsetAsync(h->d_sites, 0, DD_TIMER_KINDS * sizeof(unsigned long long), h->stream));
+        DD_CUDA(h, cudaMemsetAsync(h->d_sites, 0, (DD_TIMER_KINDS + DD_BLOCK_STATS) * sizeof(unsigned long long),
+                                   h->stream));
+        for (auto& k : h->solve_stats)
+            for (long long& v : k) v = 0;
         return DD_OK;
     }
     if (op == 0) {
@@ -712,6 +721,19 @@ extern "C" int dd_kernel_timer(dd_t h, int op, int kind, int every, double* tota
     if (total_ms) *total_ms = tot;
     if (timed) *timed = cnt;
     if (sites) *sites = (long long)ns[kind];
+    return DD_OK;
+}
+
+extern "C" int dd_solver_stats(dd_t h, int kind, long long* out) {
+    if (!h || !out || kind < 0 || kind > 2) return DD_ERR_INVALID_ARG;
+    if (kind < 2) {
+        for (int k = 0; k < 4; ++k) out[k] = h->solve_stats[kind][k];
+        return DD_OK;
+    }
+    unsigned long long v[DD_BLOCK_STATS] = {};
+    DD_CUDA(h, cudaStreamSynchronize(h->stream));
+    DD_CUDA(h, cudaMemcpy(v, h->d_sites + DD_TIMER_KINDS, sizeof(v), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 4; ++k) out[k] = (long long)v[k];
     return DD_OK;
 }
 

@@ -7,10 +7,11 @@
 // cudaMalloc/cudaFree.  Such a caller passes only its inputs and outputs;
 // every temporary of the block solves lives in one file-scope device array.
 //
-// The arithmetic is that of the persistent block solver used by
-// dd_block_filter (FILTER mode, FP32 inner solver, FP64 defect correction),
-// with the links read straight from the caller's canonical FP64 fields
-// instead of from formatted copies in a workspace.
+// The arithmetic: FP64 defect correction around an FP32 conjugate-gradient
+// solve of each block's normal equations (the persistent block solver of
+// dd_block_filter runs BiCGStab inside the same refinement), with the links
+// read straight from the caller's canonical FP64 fields instead of from
+// formatted copies in a workspace.  A block that misses tol_block reports NaN.
 #include <mutex>
 
 #include "blocksolve.cuh"
@@ -22,6 +23,10 @@ namespace {
 // queue head and a status word; per-thread-block slots follow.
 constexpr size_t kNoallocScratchBytes = 64ull << 20;
 constexpr size_t kNoallocHeader = 256;
+// fixed solver caps of this entry point (stated in include/dd.h)
+constexpr int kNoallocMaxCycles = 12;        // FP64 defect-correction cycles
+constexpr double kNoallocInnerTol = 1e-10;   // relative target of one FP32 CG solve
+constexpr int kNoallocInnerMaxit = 2000;     // iterations of one FP32 CG solve
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 // links of one block, read from a canonical FP64 field (V x 4 x 3 x 3 complex)
@@ -146,7 +151,7 @@ __global__ void __launch_bounds__(256) noalloc_block_kernel(NoallocArgs A) {
         bb = block_sum(bb, sh);
         double rr = bb;
         int outer = 0;
-        while (rr > A.tol2 * bb && outer < 12) {
+        while (rr > A.tol2 * bb && outer < kNoallocMaxCycles) {
             const double rn = sqrt(rr), rinv = 1.0 / rn;
             for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
                 Spinor<double> v;
@@ -156,7 +161,7 @@ __global__ void __launch_bounds__(256) noalloc_block_kernel(NoallocArgs A) {
                 ri.store(j, v);
             }
             __syncthreads();
-            block_cgnr<float>(c, xi, ri, pi, qi, zi, lsoli, 1e-10, 2000, sh);
+            block_cgnr<float>(c, xi, ri, pi, qi, zi, lsoli, kNoallocInnerTol, kNoallocInnerMaxit, sh);
             for (int j = threadIdx.x; j < c.nb; j += blockDim.x) {
                 Spinor<double> a;
                 Spinor<float> e;
@@ -181,6 +186,9 @@ __global__ void __launch_bounds__(256) noalloc_block_kernel(NoallocArgs A) {
             rr = block_sum(rr, sh);
             ++outer;
         }
+        // a block that missed tol_block, or went non-finite, reports NaN in
+        // the caller's ln_b (the status word below is internal to the call)
+        const bool failed = !isfinite(rr) || rr > A.tol2 * bb;
         if (threadIdx.x == 0) {
             if (!isfinite(rr)) raise_status(status, DD_ERR_NUMERIC);
             else if (rr > A.tol2 * bb) raise_status(status, DD_ERR_NOT_CONVERGED);
@@ -194,7 +202,7 @@ __global__ void __launch_bounds__(256) noalloc_block_kernel(NoallocArgs A) {
             for (int k = 0; k < 12; ++k) s += 2.0 * (e.c[k].x * d.c[k].x + e.c[k].y * d.c[k].y) + norm2(d.c[k]);
         }
         s = block_sum(s, sh);
-        if (threadIdx.x == 0) A.ln_b[id] = -s;
+        if (threadIdx.x == 0) A.ln_b[id] = (failed || !isfinite(s)) ? __longlong_as_double(0x7FF8000000000000LL) : -s;
         __syncthreads();
     }
 }
@@ -224,6 +232,7 @@ extern "C" int dd_block_ratios_noalloc(const int dims[4], const int block[4], do
         V *= dims[a];
     }
     if (V > (1LL << 30)) return DD_ERR_INVALID_ARG;
+    if (12 * V > 0xFFFFFFFFLL) return DD_ERR_UNSUPPORTED;  // 32-bit noise element word (see dd_init)
     g.bc = bc_time;
     geo_finish(g);
     // one slot (FP64 eta, b, x, r and five FP32 inner vectors of one block) must fit

@@ -117,11 +117,18 @@ __global__ void cg_arm_kernel(int nrhs, CGState* st, const CGState* outer, const
     st[r] = c;
 }
 
-// outer (defect-correction) bookkeeping: active while rr > tol2
-__global__ void outer_update_kernel(int nrhs, CGState* outer, const double* rr) {
+// outer (defect-correction) bookkeeping: active while rr > tol2; a
+// non-finite true residual ends the system and is reported as NUMERIC
+__global__ void outer_update_kernel(int nrhs, CGState* outer, const double* rr, int* status) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrhs) return;
     outer[r].rr = rr[r];
+    if (!isfinite(rr[r])) {
+        outer[r].active = 0;
+        outer[r].flags |= 2;
+        raise_status(status, DD_ERR_NUMERIC);
+        return;
+    }
     outer[r].active = outer[r].active && (rr[r] > outer[r].tol2);
 }
 __global__ void outer_arm_kernel(int nrhs, CGState* outer, const double* bb, double tol) {
@@ -690,7 +697,7 @@ int defect_correction(dd_handle* h, int nrhs, int field0, int step, Inner& cg, b
     DD_KLAUNCH(h, zero64_kernel<<<grid, 128, 0, h->stream>>>(S, xe));
     DD_KLAUNCH(h, copy_kernel<SpinorF64, SpinorF64><<<grid, 128, 0, h->stream>>>(S, be, re, nullptr));
     DD_KLAUNCH(h, norm2_kernel<SpinorF64><<<grid, 128, 0, h->stream>>>(S, re, store_reduce(h, rr)));
-    DD_KLAUNCH(h, outer_update_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, rr));
+    DD_KLAUNCH(h, outer_update_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, rr, h->d_status));
     if (cudaGetLastError() != cudaSuccess) return DD_ERR_CUDA;
     const double tol_inner = fp64_inner ? 0.0 : h->prm.tol_inner;
     int total = 0, cycles = 0;
@@ -715,7 +722,7 @@ int defect_correction(dd_handle* h, int nrhs, int field0, int step, Inner& cg, b
         hop64<MASK>(h, S, nrhs, 1, xe, xe, t64, 0.0, 1.0, 0, lk64, rs64, outer, none);
         hop64<MASK>(h, S, nrhs, 0, t64, xe, t64b, 1.0, -kappa * kappa, 1, lk64, rs64, outer, none);
         DD_KLAUNCH(h, residual_kernel<<<grid, 128, 0, h->stream>>>(S, be, t64b, re, outer, store_reduce(h, rr)));
-        DD_KLAUNCH(h, outer_update_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, rr));
+        DD_KLAUNCH(h, outer_update_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, rr, h->d_status));
         return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
     };
     auto more = [&](bool& m) -> int {
@@ -749,13 +756,22 @@ int defect_correction(dd_handle* h, int nrhs, int field0, int step, Inner& cg, b
     if (cudaMemcpyAsync(hs.data(), outer, sizeof(CGState) * nrhs, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
         return DD_ERR_CUDA;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return DD_ERR_CUDA;
-    bool conv = true;
+    bool conv = true, finite = true;
     for (int k = 0; k < nrhs; ++k) {
         double rel = hb[k] > 0 ? std::sqrt(hs[k].rr / hb[k]) : 0.0;
         if (relres) relres[k] = rel;
         if (hs[k].active) conv = false;
+        if (!std::isfinite(hs[k].rr) || !std::isfinite(hb[k])) finite = false;
     }
     if (iters) *iters = total;
+    {
+        long long* st = h->solve_stats[MASK == 0 ? 0 : 1];
+        st[0] += nrhs;
+        st[1] += total;
+        st[2] += cycles;
+        st[3] += (long long)total * S.n;
+    }
+    if (!finite) return DD_ERR_NUMERIC;
     return conv ? DD_OK : DD_ERR_NOT_CONVERGED;
 }
 
@@ -932,7 +948,7 @@ int defect_correction_df(dd_handle* h, int nrhs, int field0, int step, Inner& cg
     DD_KLAUNCH(h, outer_arm_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, bb, tol));
     DD_KLAUNCH(h, zero64_kernel<<<grid, 128, 0, h->stream>>>(S, SpinorF64{v.x64, Vh}));
     DD_KLAUNCH(h, df_round_kernel<<<grid, 128, 0, h->stream>>>(S, btd, r32, sig, store_reduce(h, rr)));
-    DD_KLAUNCH(h, outer_update_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, rr));
+    DD_KLAUNCH(h, outer_update_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, rr, h->d_status));
     if (cudaGetLastError() != cudaSuccess) return DD_ERR_CUDA;
     int total = 0, cycles = 0;
     bool polled = false;
@@ -960,7 +976,7 @@ int defect_correction_df(dd_handle* h, int nrhs, int field0, int step, Inner& cg
         B.c = df_from_double(kappa * kappa);
         B.red = store_reduce(h, rr);
         hopdf<MASK, 2>(h, nrhs, B);
-        DD_KLAUNCH(h, outer_update_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, rr));
+        DD_KLAUNCH(h, outer_update_kernel<<<1, 64, 0, h->stream>>>(nrhs, outer, rr, h->d_status));
         return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
     };
     auto more = [&](bool& m) -> int {
@@ -998,13 +1014,22 @@ int defect_correction_df(dd_handle* h, int nrhs, int field0, int step, Inner& cg
     if (cudaMemcpyAsync(hs.data(), outer, sizeof(CGState) * nrhs, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
         return DD_ERR_CUDA;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return DD_ERR_CUDA;
-    bool conv = true;
+    bool conv = true, finite = true;
     for (int k = 0; k < nrhs; ++k) {
         double rel = hb[k] > 0 ? std::sqrt(hs[k].rr / hb[k]) : 0.0;
         if (relres) relres[k] = rel;
         if (hs[k].active) conv = false;
+        if (!std::isfinite(hs[k].rr) || !std::isfinite(hb[k])) finite = false;
     }
     if (iters) *iters = total;
+    {
+        long long* st = h->solve_stats[MASK == 0 ? 0 : 1];
+        st[0] += nrhs;
+        st[1] += total;
+        st[2] += cycles;
+        st[3] += (long long)total * S.n;
+    }
+    if (!finite) return DD_ERR_NUMERIC;
     return conv ? DD_OK : DD_ERR_NOT_CONVERGED;
 }
 

@@ -78,13 +78,25 @@ def test_variance_fits_and_acceptance():
         assert abs(variance.exact_acceptance(s2) - accept.gaussian_acceptance(s2)) < 1e-15
 
 
-def test_alu_roofline_entry():
-    """The FP64-ALU roofline entry of the benchmark: flops per second from
-    timed sites and milliseconds, against the nominal FP64 peak."""
+def test_roofline_entries():
+    """Roofline entries of the benchmark from timed units and milliseconds:
+    HBM kinds in GB/s against the copy bandwidth, ALU kinds in TFLOP/s
+    against the pipe's peak; the Dirichlet kinds count only the hops that
+    stay inside a block (7 of 8 for 8^4 blocks)."""
     import bench
-    r = bench.alu_roofline(12 * 1048576, 23.0, bench.FP64_HOP_FLOPS, bench.FP64_PEAK_TFLOPS, "k")
-    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert abs(bench.hops_kept((8, 8, 8, 8)) - 7.0) < 1e-15
+    assert abs(bench.hops_kept((4, 4, 4, 4)) - 6.0) < 1e-15
+    m = bench.kernel_models((8, 8, 8, 8))
+    alu = {"fp64_fma": 1.25, "fp32_fma": 78.0}
+    r = bench.roofline_entry(2, m[2], 23.0, 10, 12 * 1048576, 2300.0, 6800.0, alu, "probe")
+    assert r["bound"] == "alu" and r["unit_rate"] == "TFLOP/s" and r["pipe"] == "fp64_fma"
     assert abs(r["achieved"] - 12 * 1048576 * 1368 / 0.023 / 1e12) < 1e-12
     assert abs(r["frac"] - r["achieved"] / 1.25) < 1e-15
-    assert bench.alu_roofline(0, 1.0, 1368, 1.25, "k") is None
-    assert bench.alu_roofline(10, 0.0, 1368, 1.25, "k") is None
+    assert abs(r["share_of_step"] - 23.0 / 2300.0) < 1e-15
+    r4 = bench.roofline_entry(4, m[4], 10.0, 4, 1000, 100.0, 6800.0, alu, "probe")
+    assert r4["flops_per_unit"] == 48 + 165 * 7 and r4["bound"] == "alu"
+    r1 = bench.roofline_entry(1, m[1], 1.0, 1, 1e6, 100.0, 6800.0, alu, "probe")
+    assert r1["bound"] == "hbm" and abs(r1["achieved"] - 1e6 * 436 / 1e9 / 1e-3) < 1e-9
+    assert abs(r1["frac"] - r1["achieved"] / 6800.0) < 1e-15
+    assert bench.roofline_entry(2, m[2], 0.0, 1, 10, 1.0, 6800.0, alu, "probe") is None
+    assert bench.roofline_entry(2, m[2], 1.0, 1, 0, 1.0, 6800.0, alu, "probe") is None
