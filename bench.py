@@ -301,6 +301,16 @@ def kernel_models(block):
     }
 
 
+def peaks_alu(stream):
+    """FP64/FP32 FMA peaks measured live by the library (derived from unit
+    counts and the maximum clock if the probe fails), and where they came from."""
+    from paper_1112_1243_gb300 import api
+    try:
+        return api.dd_alu_peaks(stream), "measured live (dd_alu_peaks: FMA chains, CUDA events)"
+    except api.DDError:
+        return dict(DERIVED_PEAKS), "derived: SM count x FMA units per cycle x 2070 MHz"
+
+
 def roofline_entry(kind, model, ms, launches, units, step_ms, hbm_peak, alu, alu_src):
     """Roofline entry of one timed kernel kind (None when nothing was timed)."""
     name, bound, bpu, fpu, unit = model
@@ -396,10 +406,7 @@ def run_gpu(args, cfg):
     chain = HierarchicalStep(h, BETA, n_inner=1, n_block=cfg["n_block"], n_global=cfg["n_global"],
                              seed=replica_seeds(cfg, rank)[1])
     # roofline denominators of the ALU-bound kernels, measured on this GPU
-    try:
-        alu, alu_src = api.dd_alu_peaks(stream), "measured live (dd_alu_peaks: FMA chains, CUDA events)"
-    except api.DDError:
-        alu, alu_src = dict(DERIVED_PEAKS), "derived: SM count x FMA units per cycle x 2070 MHz"
+    alu, alu_src = peaks_alu(stream)
 
     def barrier():
         if world > 1:
@@ -458,8 +465,9 @@ def run_gpu(args, cfg):
     iterations = {}
     for name, st in stats.items():
         n = st["systems"] if "systems" in st else st["items"]
+        calls = st["solves"] if "solves" in st else st["items"]
         iterations[name] = dict(st, inner_per_system=st["inner_iterations"] / n if n else None,
-                                outer_per_system=st["outer_cycles"] / n if n else None)
+                                outer_cycles_per_solve=st["outer_cycles"] / calls if calls else None)
     if dom["bound"] == "hbm":
         roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": dom["achieved"], "peak": peak,
                     "unit": "GB/s", "frac": dom["frac"], "traffic": traffic,
@@ -714,6 +722,9 @@ def measure_batched_filter(dev, stream, reps=3):
             w.copy_(u)
         api.dd_block_filter_batch(hs, Us, work, 3, n, 4, 2)
     torch.cuda.synchronize(dev)
+    # the persistent launch timed with CUDA events on the first handle's
+    # stream, with the kernel's own counts of inner iterations
+    api.dd_kernel_timer(hs[0], 1, 0, 1)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for r in range(reps):
@@ -723,10 +734,19 @@ def measure_batched_filter(dev, stream, reps=3):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     t = e0.elapsed_time(e1) / 1e3 / reps
+    ms7, cnt7, _ = api.dd_kernel_timer(hs[0], 2, 7)
+    st = api.dd_solver_stats(hs[0], 2)
+    api.dd_kernel_timer(hs[0], 0, 0)
+    alu = peaks_alu(stream)
+    kmodel = kernel_models((8, 8, 8, 8))[7]
+    roof = roofline_entry(7, kmodel, ms7, cnt7, st["site_iterations"], 1e3 * t * reps, 6800.0, alu[0], alu[1])
     out = {"workload": "256 x 4^4 (16^4), 16 x 6^4 (12^4), 16 x 8^4 (16^4) blocks, 4 noise vectors each, "
                        "one persistent launch", "items_per_launch": items, "seconds_per_call": t,
            "block_estimates_per_s": items / t,
-           "launch_shape": {"threads": tune["block_tpb"], "blocks_per_sm": tune["block_ctas_per_sm"]}}
+           "launch_shape": {"threads": tune["block_tpb"], "blocks_per_sm": tune["block_ctas_per_sm"]},
+           "iterations": dict(st, inner_per_item=st["inner_iterations"] / max(1, st["items"]),
+                              outer_per_item=st["outer_cycles"] / max(1, st["items"])),
+           "roofline": roof}
     for h in hs:
         del h
     return out

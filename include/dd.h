@@ -350,11 +350,13 @@ int dd_kernel_timer(dd_t h, int op, int kind, int every, double* total_ms, long 
  * paper has no counterpart: work accounting for the measurement).  kind 0:
  * whole-lattice defect-correction solves (dd_solve, the global step); 1:
  * Dirichlet solves restricted to the blocks (Schur pieces, whole-lattice
- * filter form); 2: the persistent block solver.  out (host, 4 long long):
- * kinds 0-1: systems solved, inner Krylov iterations summed over systems,
- * outer (defect-correction) cycles, sites x inner iterations; kind 2: block
- * items, inner iterations, outer cycles, sites x inner iterations.  Kinds 0-1
- * count eager (polled) solves only; kind 2 synchronises the stream. */
+ * filter form); 2: the persistent block solver.  out (host, 5 long long):
+ * kinds 0-1: batched solves, systems (right-hand sides) solved, inner Krylov
+ * iterations summed over systems, outer (defect-correction) cycles summed
+ * over the batched solves, sites x inner iterations; kind 2: launches, block
+ * items, inner iterations summed over items, outer cycles summed over items,
+ * block sites x inner iterations.  Kinds 0-1 count eager (polled) solves
+ * only; kind 2 synchronises the stream. */
 int dd_solver_stats(dd_t h, int kind, long long* out);
 
 /* Arithmetic peaks of the current GPU, measured (the paper has no
@@ -365,6 +367,27 @@ int dd_solver_stats(dd_t h, int kind, long long* out);
  * `stream`.  Allocates and frees one small device buffer; takes well under a
  * second.  Returns DD_OK, DD_ERR_INVALID_ARG (tflops NULL) or DD_ERR_CUDA. */
 int dd_alu_peaks(double* tflops, void* stream);
+
+/* The block filter of Eq. 4step step 1 in two parts, for a filter whose
+ * blocks are shared out among several GPUs (the blocks decouple because the
+ * active links of different blocks share no plaquette, Sec. 3):
+ * dd_block_ratios_range computes the stochastic log-ratios (n factors, as
+ * dd_block_filter with DD_FILTER_STOCHASTIC in its persistent per-block form,
+ * same random streams) of the blocks at block-order positions
+ * [pos0, pos0 + npos) (black blocks occupy positions 0 .. nblocks/2 - 1,
+ * white blocks the rest); ln_b (device, nblocks doubles, by block id) gets
+ * them, and 0 for every other block.  Summing the ln_b of disjoint ranges
+ * that cover the selected colours gives dd_block_filter's ln_b bit for bit.
+ * dd_block_accept then takes decisions from a complete ln_b (ln u_b < ln_b,
+ * u_b from DD_PURPOSE_BLOCK_ACCEPT keyed by block id; blocks outside
+ * colour_mask accepted) into accept (device, nblocks bytes) and restores
+ * U_old on the active links of rejected blocks of U_new (in place).
+ * Errors: DD_ERR_INVALID_ARG for a range outside [0, nblocks), n outside
+ * [1, max_rhs] or null pointers. */
+int dd_block_ratios_range(dd_t h, const void* U_old, const void* U_new, int pos0, int npos, int n, uint64_t seed,
+                          uint64_t ctr, double* ln_b);
+int dd_block_accept(dd_t h, const void* U_old, void* U_new, int colour_mask, const double* ln_b, uint64_t seed,
+                    uint64_t ctr, uint8_t* accept);
 
 /* Allocation-free block log-ratios (the paper has no counterpart: this is an
  * interface variant for callers that cannot allocate device memory — code

@@ -135,6 +135,8 @@ SIGNATURES = {
     "dd_kernel_timer": [_P, _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong),
                         ctypes.POINTER(ctypes.c_longlong)],
     "dd_solver_stats": [_P, _I, ctypes.POINTER(ctypes.c_longlong)],
+    "dd_block_ratios_range": [_P, _P, _P, _I, _I, _I, _U64, _U64, _P],
+    "dd_block_accept": [_P, _P, _P, _I, _P, _U64, _U64, _P],
     "dd_alu_peaks": [ctypes.POINTER(_D), _P],
     "dd_block_ratios_noalloc": [ctypes.POINTER(_I), ctypes.POINTER(_I), _D, _I, _I, _P, _P, _U64, _U64, _D, _P,
                                 _P],

@@ -285,13 +285,32 @@ def dd_kernel_timer(h, op, kind=0, every=1):
     return ms.value, cnt.value, sites.value
 
 
+def dd_block_ratios_range(h, U_old, U_new, pos0, npos, n, seed, ctr, ln_b=None):
+    """Stochastic block log-ratios of the blocks at block-order positions
+    [pos0, pos0 + npos); 0 for the other blocks."""
+    if ln_b is None:
+        ln_b = torch.zeros(h.nfine, dtype=torch.float64, device=h.workspace.device)
+    _check(h, _lib.load().dd_block_ratios_range(h.ptr, _ptr(U_old), _ptr(U_new), int(pos0), int(npos), int(n),
+                                                int(seed), int(ctr), _ptr(ln_b)))
+    return ln_b
+
+
+def dd_block_accept(h, U_old, U_new, colour_mask, ln_b, seed, ctr, accept=None):
+    """Block decisions from a complete ln_b and the restore of rejected blocks in U_new."""
+    if accept is None:
+        accept = torch.zeros(h.nfine, dtype=torch.uint8, device=h.workspace.device)
+    _check(h, _lib.load().dd_block_accept(h.ptr, _ptr(U_old), _ptr(U_new), int(colour_mask), _ptr(ln_b), int(seed),
+                                          int(ctr), _ptr(accept)))
+    return accept
+
+
 def dd_solver_stats(h, kind):
     """kind 0 whole-lattice solves, 1 Dirichlet solves, 2 persistent block
     solver -> dict of the counters since the last dd_kernel_timer(op 1)."""
-    out = (ctypes.c_longlong * 4)()
+    out = (ctypes.c_longlong * 5)()
     _check(h, _lib.load().dd_solver_stats(h.ptr, int(kind), out))
-    names = ("systems", "inner_iterations", "outer_cycles", "site_iterations") if kind < 2 else \
-        ("items", "inner_iterations", "outer_cycles", "site_iterations")
+    names = ("solves", "systems", "inner_iterations", "outer_cycles", "site_iterations") if kind < 2 else \
+        ("launches", "items", "inner_iterations", "outer_cycles", "site_iterations")
     return dict(zip(names, list(out)))
 
 

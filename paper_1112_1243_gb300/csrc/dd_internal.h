@@ -161,9 +161,11 @@ struct dd_handle {
     unsigned long long* d_sites = nullptr;  // [DD_TIMER_KINDS + DD_BLOCK_STATS] output sites of the timed launches,
                                             // then the block-solver counters
     // host counters of the polled (eager) defect-correction solves:
-    // [0] whole-lattice solves, [1] Dirichlet solves; {systems, inner
-    // iterations, outer cycles, site-iterations}; reset with the timer
-    long long solve_stats[2][4] = {};
+    // [0] whole-lattice solves, [1] Dirichlet solves; {solves, systems,
+    // inner iterations, outer cycles, site-iterations}; launches of the
+    // persistent block solver; reset with the timer
+    long long solve_stats[2][5] = {};
+    long long block_launches = 0;
     // even-odd indices of the sites of each block colour (null when the
     // block extent along axis 0 is odd); Dirichlet solves of one colour
     // visit only these

@@ -353,6 +353,7 @@ static int launch_blocks(dd_handle* h, int mode, int pos0, int n, int nitems, co
     const int grid = std::min(nitems, std::min(h->block_slots, std::max(1, h->num_sms) * h->tune.block_ctas_per_sm));
     const int tpb = h->tune.block_tpb;
     const bool timed = block_timer_begin(h);
+    ++h->block_launches;
     if (A.inner_f64)
         DD_KLAUNCH(h, block_solve_kernel<double, SpinorF64, LinkF64><<<grid, tpb, 0, h->stream>>>(A));
     else
@@ -664,6 +665,56 @@ extern "C" int dd_block_filter(dd_t h, const void* U_old, void* U_new, int colou
     return DD_OK;
 }
 
+// --------------------------------------------- block filter by block ranges
+// ln_b of the blocks at block-order positions [pos0, pos0 + npos), 0 elsewhere
+__global__ void sum_range_kernel(Geo g, int pos0, int npos, int n, const double* item_out, double* ln_b) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= g.nblocks) return;
+    int B[4] = {b % g.nbk[0], (b / g.nbk[0]) % g.nbk[1], (b / (g.nbk[0] * g.nbk[1])) % g.nbk[2],
+                b / (g.nbk[0] * g.nbk[1] * g.nbk[2])};
+    const int pos = block_pos_of(g, b, (B[0] + B[1] + B[2] + B[3]) & 1);
+    double s = 0.0;
+    if (pos >= pos0 && pos < pos0 + npos)
+        for (int i = 0; i < n; ++i) s += item_out[(pos - pos0) * n + i];
+    ln_b[b] = s;
+}
+
+extern "C" int dd_block_ratios_range(dd_t h, const void* U_old, const void* U_new, int pos0, int npos, int n,
+                                     uint64_t seed, uint64_t ctr, double* ln_b) {
+    int rc = dd_require_ws(h);
+    if (rc) return rc;
+    rc = dd_require_feature(h, h->feat_estimate, "dd_block_ratios_range");
+    if (rc) return rc;
+    LevelScope level(h, true);
+    const Geo& g = h->g;
+    if (!U_old || !U_new || !ln_b || n < 1 || n > h->prm.max_rhs || pos0 < 0 || npos < 0 || pos0 + npos > g.nblocks)
+        return dd_fail(h, DD_ERR_INVALID_ARG, "dd_block_ratios_range: bad arguments");
+    rc = prepare_fields(h, (const double*)U_old, (const double*)U_new, n, true, false);
+    if (rc) return rc;
+    rc = launch_blocks(h, BLOCK_FILTER, pos0, n, npos * n, nullptr, nullptr, seed, ctr);
+    if (rc) return rc;
+    DD_KLAUNCH(h, sum_range_kernel<<<grid_for(g.nblocks, 128), 128, 0, h->stream>>>(g, pos0, npos, n, h->d_item_out,
+                                                                                   ln_b));
+    DD_LAUNCH_CHECK(h, "sum_range_kernel");
+    return DD_OK;
+}
+
+extern "C" int dd_block_accept(dd_t h, const void* U_old, void* U_new, int colour_mask, const double* ln_b,
+                               uint64_t seed, uint64_t ctr, uint8_t* accept) {
+    if (!h) return DD_ERR_INVALID_ARG;
+    if (!U_old || !U_new || !ln_b || !accept || colour_mask < 1 || colour_mask > 3)
+        return dd_fail(h, DD_ERR_INVALID_ARG, "dd_block_accept: bad arguments");
+    LevelScope level(h, true);
+    DD_KLAUNCH(h, block_accept_kernel<<<grid_for(h->g.nblocks, 128), 128, 0, h->stream>>>(h->g, colour_mask, ln_b,
+                                                                                         accept, seed, ctr,
+                                                                                         h->d_ctr_off));
+    if (h->n_active > 0)
+        DD_KLAUNCH(h, restore_kernel<<<grid_for(h->n_active, 128), 128, 0, h->stream>>>(
+                          h->g, h->n_active, h->d_active_links, accept, (const double*)U_old, (double*)U_new));
+    DD_LAUNCH_CHECK(h, "dd_block_accept");
+    return DD_OK;
+}
+
 // ------------------------------------------------ multi-lattice block filter
 namespace {
 struct BatchPlan {
@@ -832,6 +883,7 @@ extern "C" int dd_block_filter_batch(int nh, const dd_t* hs_, const void* const*
         const int grid = std::min((int)items.size(), P.slots);
         const int tpb = h0->tune.block_tpb;
         const bool timed = block_timer_begin(h0);
+        ++h0->block_launches;
         if (A.inner_f64)
             DD_KLAUNCH(h0, block_solve_kernel<double, SpinorF64, LinkF64><<<grid, tpb, 0, s>>>(A));
         else

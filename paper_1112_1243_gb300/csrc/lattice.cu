@@ -700,6 +700,7 @@ extern "C" int dd_kernel_timer(dd_t h, int op, int kind, int every, double* tota
                                    h->stream));
         for (auto& k : h->solve_stats)
             for (long long& v : k) v = 0;
+        h->block_launches = 0;
         return DD_OK;
     }
     if (op == 0) {
@@ -727,13 +728,14 @@ extern "C" int dd_kernel_timer(dd_t h, int op, int kind, int every, double* tota
 extern "C" int dd_solver_stats(dd_t h, int kind, long long* out) {
     if (!h || !out || kind < 0 || kind > 2) return DD_ERR_INVALID_ARG;
     if (kind < 2) {
-        for (int k = 0; k < 4; ++k) out[k] = h->solve_stats[kind][k];
+        for (int k = 0; k < 5; ++k) out[k] = h->solve_stats[kind][k];
         return DD_OK;
     }
     unsigned long long v[DD_BLOCK_STATS] = {};
     DD_CUDA(h, cudaStreamSynchronize(h->stream));
     DD_CUDA(h, cudaMemcpy(v, h->d_sites + DD_TIMER_KINDS, sizeof(v), cudaMemcpyDeviceToHost));
-    for (int k = 0; k < 4; ++k) out[k] = (long long)v[k];
+    out[0] = h->block_launches;
+    for (int k = 0; k < 4; ++k) out[1 + k] = (long long)v[k];
     return DD_OK;
 }
 

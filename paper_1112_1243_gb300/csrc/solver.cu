@@ -766,10 +766,11 @@ int defect_correction(dd_handle* h, int nrhs, int field0, int step, Inner& cg, b
     if (iters) *iters = total;
     {
         long long* st = h->solve_stats[MASK == 0 ? 0 : 1];
-        st[0] += nrhs;
-        st[1] += total;
-        st[2] += cycles;
-        st[3] += (long long)total * S.n;
+        st[0] += 1;
+        st[1] += nrhs;
+        st[2] += total;
+        st[3] += cycles;
+        st[4] += (long long)total * S.n;
     }
     if (!finite) return DD_ERR_NUMERIC;
     return conv ? DD_OK : DD_ERR_NOT_CONVERGED;
@@ -1024,10 +1025,11 @@ int defect_correction_df(dd_handle* h, int nrhs, int field0, int step, Inner& cg
     if (iters) *iters = total;
     {
         long long* st = h->solve_stats[MASK == 0 ? 0 : 1];
-        st[0] += nrhs;
-        st[1] += total;
-        st[2] += cycles;
-        st[3] += (long long)total * S.n;
+        st[0] += 1;
+        st[1] += nrhs;
+        st[2] += total;
+        st[3] += cycles;
+        st[4] += (long long)total * S.n;
     }
     if (!finite) return DD_ERR_NUMERIC;
     return conv ? DD_OK : DD_ERR_NOT_CONVERGED;
