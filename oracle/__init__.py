@@ -30,6 +30,12 @@ Modules
               Kennedy-Pendleton SU(2) sampler, over-relaxation
   accept      Metropolis acceptance steps (Eq. 2.1-2.3) and the Gaussian
               acceptance law (Eq. acceptance)
+  chain       one step of the hierarchy (Sec. 5, Eq. 4step steps 0, 1, 3)
+  recursive   one level of recursive decomposition (Eq. ddrec, step 2)
+  gaugefix    relative gauge fixing of the proposal (Sec. 4)
+  schwarz     Schwarz alternating procedure over the block decomposition
+              and flexible GCR (the domain-decomposition solver the block
+              decomposition comes from)
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test to a
 closed form, an identity of the paper, a published test vector or a library
