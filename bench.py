@@ -73,8 +73,14 @@ def parse():
                    help="skip the uneven-block batched filter measurement")
     p.add_argument("--compare-config", default="c2,c3",
                    help="workloads of the mixed-versus-FP64 comparison, comma-separated ('' to skip)")
-    p.add_argument("--krylov", default="bicgstab", choices=["cgnr", "bicgstab"],
+    p.add_argument("--krylov", default="bicgstab", choices=["cgnr", "bicgstab", "sap"],
                    help="inner Krylov method of the mixed-precision solves")
+    p.add_argument("--no-lu", action="store_true", help="skip the timing of the dense LU check path (c1)")
+    p.add_argument("--no-sap", action="store_true",
+                   help="skip the measurement of the step with SAP-preconditioned GCR global solves")
+    p.add_argument("--sap-ncy", type=int, default=4, help="Schwarz cycles per SAP-GCR preconditioner application")
+    p.add_argument("--sap-nmr", type=int, default=4, help="BiCGStab iterations per approximate SAP block solve")
+    p.add_argument("--sap-nkv", type=int, default=6, help="directions of the flexible GCR before a restart")
     p.add_argument("--mode", default="step", choices=["step", "solve"],
                    help="step: the hierarchical step (the benchmark); solve: one-rhs global solves on a lean "
                         "handle (kernel captures and Dslash GB/s)")
@@ -388,11 +394,12 @@ def run_gpu(args, cfg):
     Vh = V // 2
     nmax = max(cfg["n_global"], cfg["n_block"])
     stream = torch.cuda.current_stream(dev)
-    krylov = {"cgnr": api.DD_KRYLOV_CGNR, "bicgstab": api.DD_KRYLOV_BICGSTAB}[args.krylov]
+    krylov = {"cgnr": api.DD_KRYLOV_CGNR, "bicgstab": api.DD_KRYLOV_BICGSTAB, "sap": api.DD_KRYLOV_SAP_GCR}[args.krylov]
     outer = {"f64": api.DD_PREC_F64, "df64": api.DD_PREC_DF64}[args.outer]
     h = api.dd_init(cfg["dims"], cfg["block"], cfg["kappa"], max_rhs=nmax, inner_prec=prec,
                     block_prec=api.DD_PREC_F32, tol_global=1e-10, tol_block=1e-12, tol_inner=args.tol_inner,
-                    maxit=40000, stream=stream, device=dev, krylov=krylov, outer_prec=outer)
+                    maxit=40000, stream=stream, device=dev, krylov=krylov, outer_prec=outer,
+                    sap_ncy=args.sap_ncy, sap_nmr=args.sap_nmr, sap_nkv=args.sap_nkv)
     U_np = synthetic.random_gauge(cfg["dims"], cfg["eps"], replica_seeds(cfg, rank)[0])
     U = torch.from_numpy(U_np).to(dev)
     tune = None
@@ -558,6 +565,12 @@ def run_gpu(args, cfg):
     torch.cuda.empty_cache()
     if not args.no_outer_df64 and args.outer == "f64" and args.prec != "f64":
         line["outer_df64"] = measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune)
+    if not args.no_sap and args.prec != "f64":
+        # the global solves by SAP-preconditioned flexible GCR instead of BiCGStab
+        sap = {"sap_ncy": args.sap_ncy, "sap_nmr": args.sap_nmr, "sap_nkv": args.sap_nkv}
+        line["sap_gcr"] = dict(measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune,
+                                                  krylov=api.DD_KRYLOV_SAP_GCR, outer=api.DD_PREC_F64, sap=sap),
+                               parameters=sap, bicgstab_global_solves=iterations.get("global"))
     if args.compare_config:
         # mixed versus plain FP64 on smaller workloads (the FP64 path at the
         # full volume would hold the GPU for minutes per step)
@@ -567,6 +580,8 @@ def run_gpu(args, cfg):
         line["batched_filter"] = measure_batched_filter(dev, stream)
     if not args.no_recursive:
         line["recursive"] = measure_recursive(cfg, dev, stream)
+    if not args.no_lu:
+        line["exact_lu"] = measure_lu(dev, stream)
     if rank == 0 and not args.no_cpu_baseline:
         c2 = CONFIGS["c2"]
         r = oracle_estimate_rate(c2)
@@ -594,19 +609,24 @@ def run_gpu(args, cfg):
     return 0
 
 
-def measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune):
+def measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune, krylov=None, outer=None, sap=None):
     """The timed step again with the defect-correction residual in
-    double-float arithmetic (outer_prec DD_PREC_DF64), same workload, seeds
-    and launch shapes; the hop kernels of the residual timed by kind."""
+    double-float arithmetic (outer_prec DD_PREC_DF64), or with another inner
+    Krylov method (krylov, sap: DD_KRYLOV_SAP_GCR and its parameters), same
+    workload, seeds and launch shapes; the hop kernels of the residual timed
+    by kind, the iterations of the global solves counted."""
     import torch
     from paper_1112_1243_gb300 import api
     from paper_1112_1243_gb300.chain import HierarchicalStep
     prec = {"f16": api.DD_PREC_F16, "f32": api.DD_PREC_F32}[args.prec]
-    krylov = {"cgnr": api.DD_KRYLOV_CGNR, "bicgstab": api.DD_KRYLOV_BICGSTAB}[args.krylov]
+    if krylov is None:
+        krylov = {"cgnr": api.DD_KRYLOV_CGNR, "bicgstab": api.DD_KRYLOV_BICGSTAB,
+                  "sap": api.DD_KRYLOV_SAP_GCR}[args.krylov]
+    outer = api.DD_PREC_DF64 if outer is None else outer
     nmax = max(cfg["n_global"], cfg["n_block"])
     h = api.dd_init(cfg["dims"], cfg["block"], cfg["kappa"], max_rhs=nmax, inner_prec=prec,
                     block_prec=api.DD_PREC_F32, tol_global=1e-10, tol_block=1e-12, tol_inner=args.tol_inner,
-                    maxit=40000, stream=stream, device=dev, krylov=krylov, outer_prec=api.DD_PREC_DF64)
+                    maxit=40000, stream=stream, device=dev, krylov=krylov, outer_prec=outer, **(sap or {}))
     if tune:
         api.dd_set_tuning(h, hop_tpb=tune["hop_tpb"], hop_spt=tune["hop_spt"], hop64_tpb=tune["hop64_tpb"],
                           hop64_spt=tune["hop64_spt"], block_tpb=tune["block_tpb"],
@@ -626,10 +646,14 @@ def measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune):
     torch.cuda.synchronize(dev)
     t_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     ms3, cnt3, _ = api.dd_kernel_timer(h, 2, 3)
+    glob = api.dd_solver_stats(h, 0)
     api.dd_kernel_timer(h, 0, 0)
     out = {"value": job_rate(cfg["n_global"] * args.steps, world, t_ms), "unit": "estimates/s",
            "ms_per_step": t_ms / args.steps, "device_status": api.dd_status(h)[0],
-           "residual_hop_avg_us": 1e3 * ms3 / max(1, cnt3), "residual_hop_launches_timed": cnt3}
+           "global_solves": dict(glob, inner_per_system=glob["inner_iterations"] / max(1, glob["systems"]),
+                                 outer_cycles_per_solve=glob["outer_cycles"] / max(1, glob["solves"]))}
+    if cnt3:
+        out.update(residual_hop_avg_us=1e3 * ms3 / max(1, cnt3), residual_hop_launches_timed=cnt3)
     del chain
     del h
     torch.cuda.empty_cache()
@@ -752,6 +776,38 @@ def measure_batched_filter(dev, stream, reps=3):
     return out
 
 
+def measure_lu(dev, stream, reps=3):
+    """The exact check path on the 4^4 lattice with 2^4 blocks (c1): ln|det|
+    of D (3072 x 3072 complex), of the 16 Dirichlet blocks (192 x 192) and
+    of the Schur complement (1536 x 1536, assembled with block solves and a
+    product), by dense LU with partial pivoting; CUDA-event time per call and
+    the FP64 rate of the full-matrix LU (8 n^3 / 3 real flops)."""
+    import torch
+    from paper_1112_1243_gb300 import api, synthetic
+    dims, block = (4, 4, 4, 4), (2, 2, 2, 2)
+    h = api.dd_init(dims, block, 0.12, features=api.DD_FEAT_EXACT, stream=stream, device=dev)
+    U = torch.from_numpy(synthetic.random_gauge(dims, 0.4, 1)).to(dev)
+    out = {"workload": "c1: 4^4 lattice, 2^4 blocks, kappa 0.12, eps 0.4"}
+    alu, src = peaks_alu(stream)
+    for which, name, n, nmat in ((0, "D", 3072, 1), (1, "D_b", 192, 16), (2, "Dhat", 1536, 1)):
+        api.dd_logdet_exact(h, U, which)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            api.dd_logdet_exact(h, U, which)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms": ms, "n": n, "matrices": nmat}
+        if which == 0:
+            tf = 8.0 * n ** 3 / 3.0 / (ms / 1e3) / 1e12
+            out[name].update(achieved_tflops=tf, peak_fp64_tflops=alu["fp64_fma"], frac=tf / alu["fp64_fma"],
+                             peak_fp64_mma_tflops=alu["fp64_mma"], peak_source=src)
+    del h
+    return out
+
+
 def measure_recursive(cfg, dev, stream, n_schur=4, steps=1):
     """The benchmark step with one level of recursion (Eq. 4step steps 0-3):
     the blocks of the workload split into 4^4 sub-blocks, step 1 on the
@@ -798,10 +854,11 @@ def run_solve(args, cfg):
     build.build()
     dev = torch.device("cuda", 0)
     prec = {"f16": api.DD_PREC_F16, "f32": api.DD_PREC_F32, "f64": api.DD_PREC_F64}[args.prec]
-    krylov = {"cgnr": api.DD_KRYLOV_CGNR, "bicgstab": api.DD_KRYLOV_BICGSTAB}[args.krylov]
+    krylov = {"cgnr": api.DD_KRYLOV_CGNR, "bicgstab": api.DD_KRYLOV_BICGSTAB, "sap": api.DD_KRYLOV_SAP_GCR}[args.krylov]
     outer = {"f64": api.DD_PREC_F64, "df64": api.DD_PREC_DF64}[args.outer]
     h = api.dd_init(cfg["dims"], cfg["block"], cfg["kappa"], max_rhs=1, inner_prec=prec, tol_global=1e-10,
-                    maxit=40000, features=api.DD_FEAT_SOLVE, device=dev, krylov=krylov, outer_prec=outer)
+                    maxit=40000, features=api.DD_FEAT_SOLVE, device=dev, krylov=krylov, outer_prec=outer,
+                    sap_ncy=args.sap_ncy, sap_nmr=args.sap_nmr, sap_nkv=args.sap_nkv)
     U = torch.from_numpy(synthetic.random_gauge(cfg["dims"], cfg["eps"], cfg["seed"])).to(dev)
     b = torch.from_numpy(synthetic.random_spinor(cfg["dims"], 1)).to(dev)
     x = torch.zeros_like(b)

@@ -129,11 +129,26 @@ typedef struct {
                           DD_PREC_DF64 (double-float: every operation on the FP32 pipe, rounding
                           error about 2^-47 of the summed term magnitudes; the workspace then
                           holds one more FP64-sized copy of each gauge-field slot) */
+    int sap_ncy;       /* DD_KRYLOV_SAP_GCR: Schwarz cycles per preconditioner application (default 4, 1..16) */
+    int sap_nmr;       /* DD_KRYLOV_SAP_GCR: BiCGStab iterations per approximate block solve (default 4, 1..64) */
+    int sap_nkv;       /* DD_KRYLOV_SAP_GCR: directions kept by the flexible GCR before a restart (default 6, at most 16) */
 } dd_params;
 
 /* inner Krylov method of the FP32/FP16 solves (the FP64 solver is always CGNR) */
 #define DD_KRYLOV_CGNR 0     /* CG on the even-odd normal equations Dtilde^dag Dtilde */
 #define DD_KRYLOV_BICGSTAB 1 /* BiCGStab on Dtilde (van der Vorst), restarted by the FP64 loop */
+/* Global solves by flexible GCR on the whole operator D, preconditioned with
+ * sap_ncy cycles of the Schwarz alternating procedure over the black/white
+ * blocks (the domain-decomposition solver the block decomposition of Sec. 3
+ * comes from): per cycle and colour the residual of that colour's blocks and
+ * an approximate solve of every such block (sap_nmr BiCGStab iterations of
+ * its even-odd Dirichlet system).  The inner system Dtilde e = r of the FP64
+ * defect correction is solved as D (e, e_o) = (r, 0), whose even part is e.
+ * FP32 arithmetic, hop inputs and links in the inner precision (F16 or F32);
+ * Dirichlet solves (Schur pieces, filter) use BiCGStab.  Eager calls only
+ * (the GCR polls its residuals from the host): inside a graph capture the
+ * global solve returns DD_ERR_UNSUPPORTED; outer_prec must be DD_PREC_F64. */
+#define DD_KRYLOV_SAP_GCR 2
 
 /* workspace features (dd_params.features); entry points that need a part the
  * workspace was not planned with fail with DD_ERR_UNSUPPORTED */
@@ -143,7 +158,8 @@ typedef struct {
 
 /* Fill p with defaults: kappa 0.125, bc_time -1, DD_ACTIVE_AUTO, max_rhs 1,
  * inner F16, block F32, tol_global 1e-10, tol_block 1e-12, tol_inner 1e-3,
- * maxit 20000.  dims/block are zeroed and must be set by the caller. */
+ * maxit 20000, krylov CGNR, sap_ncy 4, sap_nmr 4, sap_nkv 6.  dims/block are
+ * zeroed and must be set by the caller. */
 int dd_default_params(dd_params* p);
 
 /* Create a handle for one lattice and block decomposition (Sec. 3, Eq. domdec).
@@ -199,6 +215,19 @@ int dd_apply_D_block(dd_t h, void* out, const void* in, const void* U, int colou
  * NULL) the final true relative residuals.  DD_ERR_NOT_CONVERGED if maxit was
  * reached first (x then holds the last iterate). */
 int dd_solve(dd_t h, void* x, const void* b, const void* U, int nrhs, int prec, int* iters, double* relres);
+
+/* The Schwarz preconditioner of DD_KRYLOV_SAP_GCR alone: out = sap_ncy
+ * cycles of the Schwarz alternating procedure over the black/white blocks
+ * (Sec. 3 decomposition; per cycle black blocks, then white blocks, each
+ * after the residual rho - D z of its sites is formed) applied to in, from
+ * z = 0, with approximate block solves of sap_nmr BiCGStab iterations in
+ * the precision prec (DD_PREC_F32 or DD_PREC_F16).  With exact block solves
+ * one cycle is the block Gauss-Seidel step z = [[A, 0], [C, E]]^{-1} rho.
+ * in, out: device canonical FP64 spinors (nrhs of them, 24 V doubles each);
+ * U: device canonical FP64 gauge field.  The handle must have been created
+ * with krylov DD_KRYLOV_SAP_GCR (else DD_ERR_UNSUPPORTED) and an even block
+ * extent along axis 0. */
+int dd_sap_apply(dd_t h, void* out, const void* in, const void* U, int nrhs, int prec);
 
 /* Complex Gaussian noise (density ~ exp(-|eta|^2), Sec. 4) on every site for
  * nrhs vectors: component (s, spin, c) of vector r uses element

@@ -33,6 +33,7 @@ DD_PURPOSE_BLOCK_SCHUR_ACCEPT = 8
 DD_EST_FACTORS, DD_EST_REPLICAS, DD_EST_INTERP_ALL = 0, 1, 4
 DD_FILTER_STOCHASTIC, DD_FILTER_EXACT = 0, 1
 DD_TIMER_KIND_COUNT = 8
+DD_KRYLOV_CGNR, DD_KRYLOV_BICGSTAB, DD_KRYLOV_SAP_GCR = 0, 1, 2
 
 ERROR_NAMES = {
     DD_ERR_INVALID_ARG: "DD_ERR_INVALID_ARG",
@@ -63,6 +64,9 @@ class dd_params(ctypes.Structure):
         ("krylov", ctypes.c_int),
         ("sub_block", ctypes.c_int * 4),
         ("outer_prec", ctypes.c_int),
+        ("sap_ncy", ctypes.c_int),
+        ("sap_nmr", ctypes.c_int),
+        ("sap_nkv", ctypes.c_int),
     ]
 
 
@@ -98,7 +102,6 @@ class dd_tune_report(ctypes.Structure):
 
 DD_TUNE_HOP, DD_TUNE_BLOCK, DD_TUNE_NO_CACHE = 1, 2, 4
 DD_FEAT_SOLVE, DD_FEAT_ESTIMATE, DD_FEAT_EXACT = 1, 2, 4
-DD_KRYLOV_CGNR, DD_KRYLOV_BICGSTAB = 0, 1
 
 
 _P = ctypes.c_void_p
@@ -135,6 +138,7 @@ SIGNATURES = {
     "dd_kernel_timer": [_P, _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong),
                         ctypes.POINTER(ctypes.c_longlong)],
     "dd_solver_stats": [_P, _I, ctypes.POINTER(ctypes.c_longlong)],
+    "dd_sap_apply": [_P, _P, _P, _P, _I, _I],
     "dd_block_ratios_range": [_P, _P, _P, _I, _I, _I, _U64, _U64, _P],
     "dd_block_accept": [_P, _P, _P, _I, _P, _U64, _U64, _P],
     "dd_alu_peaks": [ctypes.POINTER(_D), _P],

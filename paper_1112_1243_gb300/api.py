@@ -76,7 +76,8 @@ def dd_default_params():
 def dd_init(dims, block, kappa, bc_time=-1, active_mode=_lib.DD_ACTIVE_AUTO, max_rhs=1,
             inner_prec=_lib.DD_PREC_F16, block_prec=_lib.DD_PREC_F32, tol_global=1e-10,
             tol_block=1e-12, tol_inner=1e-3, maxit=20000, stream=None, device=None, features=0,
-            krylov=_lib.DD_KRYLOV_CGNR, sub_block=None, outer_prec=_lib.DD_PREC_F64):
+            krylov=_lib.DD_KRYLOV_CGNR, sub_block=None, outer_prec=_lib.DD_PREC_F64, sap_ncy=None, sap_nmr=None,
+            sap_nkv=None):
     """Create a handle and give it a torch-allocated workspace on `device`.
     sub_block: extents of the sub-blocks of one level of recursion (None: no
     recursion).  outer_prec: arithmetic of the defect-correction residual of
@@ -101,6 +102,12 @@ def dd_init(dims, block, kappa, bc_time=-1, active_mode=_lib.DD_ACTIVE_AUTO, max
     for a in range(4):
         p.sub_block[a] = int(sub_block[a]) if sub_block is not None else 0
     p.outer_prec = int(outer_prec)
+    if sap_ncy is not None:
+        p.sap_ncy = int(sap_ncy)
+    if sap_nmr is not None:
+        p.sap_nmr = int(sap_nmr)
+    if sap_nkv is not None:
+        p.sap_nkv = int(sap_nkv)
     device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
     if stream is None:
         stream = torch.cuda.current_stream(device)
@@ -150,6 +157,11 @@ def dd_solve(h, x, b, U, nrhs=1, prec=_lib.DD_PREC_F64, check=True):
     if check:
         _check(h, rc)
     return it.value, res.tolist(), rc
+
+
+def dd_sap_apply(h, out, inp, U, nrhs=1, prec=_lib.DD_PREC_F32):
+    """sap_ncy Schwarz cycles (the SAP-GCR preconditioner) applied to inp."""
+    return _check(h, _lib.load().dd_sap_apply(h.ptr, _ptr(out), _ptr(inp), _ptr(U), int(nrhs), int(prec)))
 
 
 def dd_noise(h, eta, nrhs, purpose, seed, ctr):

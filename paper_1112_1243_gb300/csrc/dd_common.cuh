@@ -260,6 +260,10 @@ struct LinkF16 {
 struct SiteSet {
     const int* map;
     long long n;
+    // >= 0: the set is the sites of the blocks of this colour (even block
+    // extent along axis 0), map holds them in increasing even-odd index, and
+    // the hop kernel may compute them instead of loading them (colour_site)
+    int colour = -1;
     DD_DEV long long at(long long t) const { return map ? (long long)__ldg(map + t) : t; }
 };
 
@@ -276,6 +280,8 @@ struct Geo {
     int st[4];    // canonical strides 1, L0, L0 L1, L0 L1 L2
     // multipliers for division by Lh0, L1, L2 with __umulhi (exact for n * d < 2^32; 0: use '/')
     unsigned mLh0, mL1, mL2;
+    // the same for Lh0 / 2, b0 / 2, b1, b2, b3 (colour site sets)
+    unsigned mQ, mB, mb1, mb2, mb3;
 };
 
 // derived members of a Geo whose L, b, nbk and bc are set (host side)
@@ -298,6 +304,11 @@ inline void geo_finish(Geo& g) {
     g.mLh0 = magic(g.Lh0);
     g.mL1 = magic(g.L[1]);
     g.mL2 = magic(g.L[2]);
+    g.mQ = magic(g.Lh0 / 2);
+    g.mB = magic(g.b[0] / 2);
+    g.mb1 = magic(g.b[1]);
+    g.mb2 = magic(g.b[2]);
+    g.mb3 = magic(g.b[3]);
 }
 
 // n / d with a precomputed multiplier (m = 0: plain division)
@@ -313,6 +324,28 @@ DD_DEV void eo_coords(const Geo& g, int p, int h, int x[4]) {
     x[2] = q - t * g.L[2];
     x[3] = t;
     x[0] = 2 * hx + ((p + x[1] + x[2] + x[3]) & 1);
+}
+
+// The t-th site (increasing even-odd index h) of the blocks of colour c,
+// for an even block extent along axis 0: every row (x1, x2, x3) holds Lh0/2
+// such sites, in runs of b0/2 consecutive h (one run per block of that
+// colour along axis 0, every second block).  Returns h; x = coordinates of
+// the parity-p site h.  The same list the host stores in the colour maps.
+DD_DEV int colour_site(const Geo& g, int c, int t, int p, int x[4]) {
+    const int q = g.Lh0 >> 1;
+    const int r = fast_div(t, q, g.mQ);
+    const int u = t - r * q;
+    const int B = g.b[0] >> 1;
+    const int m = fast_div(u, B, g.mB);
+    const int k = u - m * B;
+    const int s1 = fast_div(r, g.L[1], g.mL1);
+    x[1] = r - s1 * g.L[1];
+    x[3] = fast_div(s1, g.L[2], g.mL2);
+    x[2] = s1 - x[3] * g.L[2];
+    const int cr = (fast_div(x[1], g.b[1], g.mb1) + fast_div(x[2], g.b[2], g.mb2) + fast_div(x[3], g.b[3], g.mb3)) & 1;
+    const int hx = (2 * m + ((c + cr) & 1)) * B + k;
+    x[0] = 2 * hx + ((p + x[1] + x[2] + x[3]) & 1);
+    return hx + g.Lh0 * r;
 }
 
 // canonical index of s +- a-hat from the coordinates x of s (periodic)

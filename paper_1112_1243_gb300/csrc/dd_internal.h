@@ -92,6 +92,23 @@ struct SolverVecs {
     float* q16n;
 };
 
+// Work vectors of the SAP-preconditioned GCR: `halves` holds FP32 half
+// vectors (one parity of R systems, 6 chunks x Vh float4 each): 0 X_o,
+// 1 R_o, 2-3 Y, 4-5 Q, 6 the odd part of a block correction, 7-11 the block
+// solver's x, r, v, s, t, 12-15 its hop copies p, rhat, s, t (FP16 or FP32
+// storage), then Z_0..Z_{nkv-1} and W_0..W_{nkv-1} (two halves each).
+constexpr int DD_SAP_MAX_NKV = 16;
+struct SapVecs {
+    static constexpr int kFixedHalves = 16;
+    float4* halves = nullptr;
+    size_t half = 0;        // float4 per half vector
+    int nkv = 0;
+    double* partials = nullptr;
+    int nblk = 0;           // thread blocks of a reduction over Vh sites
+    double* sc = nullptr;   // per-system scalars
+    float4* at(int k) const { return halves + (size_t)k * half; }
+};
+
 constexpr int DD_BLOCK_CTAS_MAX = 4;
 // timed kernel kinds: whole-lattice hops 0 FP16 -> FP16, 1 FP16 -> FP32 (xpay),
 // 2 FP64, 3 double-float residual; Dirichlet (block-restricted) hops 4 FP64,
@@ -129,7 +146,8 @@ struct dd_handle {
     std::vector<FieldSlot> fields;   // max_rhs + 1 slots
     std::vector<SolverVecs> vecs;    // max_rhs systems
     double2* dd_vec = nullptr;       // block-ordered FP64 vectors: [6][max_rhs][12][V]
-    CGState* d_cg = nullptr;         // [2 * max_rhs]
+    CGState* d_cg = nullptr;         // [3 * max_rhs + 2]: inner, outer, SAP block-solver states
+    SapVecs sap;                     // SAP-preconditioned GCR (krylov DD_KRYLOV_SAP_GCR)
     double* d_partials = nullptr;    // reduction partials
     unsigned* d_counters = nullptr;  // reduction tickets
     size_t partials_cap = 0;

@@ -124,14 +124,19 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 7 : 0)
     for (int pass = 0; pass < SPT; ++pass) {
         const long long t = (long long)blockIdx.x * tile + (long long)pass * blockDim.x + threadIdx.x;
         if (t >= A.S.n) break;
-        const int h = (int)A.S.at(t);
+        int x[4];
+        int h;
+        if (A.S.colour >= 0) {
+            h = colour_site(A.g, A.S.colour, (int)t, A.p, x);
+        } else {
+            h = (int)A.S.at(t);
+            eo_coords(A.g, A.p, h, x);
+        }
         const SIn in = at_rhs(A.in, rhs);
         LK lk = A.lk;
         lk.p += (long long)rhs * A.lk_rhs_stride;
         const LK lk_p = link_parity(lk, A.p, Vh);
         const LK lk_q = link_parity(lk, 1 - A.p, Vh);
-        int x[4];
-        eo_coords(A.g, A.p, h, x);
         Spinor<R> acc;
         hop_site<R, SIn, LK, MASK>(A.g, A.p, h, x, in, lk_p, lk_q, A.g5in, acc);
         if (A.g5out) gamma5(acc);

@@ -391,7 +391,22 @@ void plan(dd_handle* h, char* base) {
     }
     // block-ordered FP64 vectors: 6 banks of R vectors (estimator)
     h->dd_vec = c.take<double2>(est ? (size_t)6 * R * 12 * V : 0);
-    h->d_cg = c.take<CGState>((size_t)2 * R + 2);
+    h->d_cg = c.take<CGState>((size_t)3 * R + 2);
+    // SAP-preconditioned GCR (global solves): full FP32 vectors (even, odd
+    // halves of R systems each) and the block solver's vectors
+    {
+        SapVecs& s = h->sap;
+        const bool on = solve && h->prm.krylov == DD_KRYLOV_SAP_GCR;
+        const int nkv = on ? h->prm.sap_nkv : 0;
+        const size_t half = on ? (size_t)R * 6 * Vh : 0;
+        s.halves = c.take<float4>(half * (size_t)(SapVecs::kFixedHalves + 4 * nkv));
+        s.half = half;
+        s.nkv = nkv;
+        const long long nblk = grid_for(Vh, 128);
+        s.partials = c.take<double>(on ? (size_t)nblk * R * 2 * (DD_SAP_MAX_NKV + 1) : 0);
+        s.nblk = (int)nblk;
+        s.sc = c.take<double>(on ? (size_t)R * 4 * (DD_SAP_MAX_NKV + 4) : 0);
+    }
     // partials of grid reductions with tiles of 64 sites or more (3 values per tile)
     h->partials_cap = (size_t)(grid_for(std::max(Vh, V), 64) + 64) * (R + 1) * 2;
     h->d_partials = c.take<double>(h->partials_cap);
@@ -443,6 +458,9 @@ extern "C" int dd_default_params(dd_params* p) {
     p->tol_block = 1e-12;
     p->tol_inner = 1e-3;
     p->maxit = 20000;
+    p->sap_ncy = 4;
+    p->sap_nmr = 4;
+    p->sap_nkv = 6;
     return DD_OK;
 }
 
@@ -482,7 +500,14 @@ extern "C" int dd_init(dd_t* out, const dd_params* p, void* stream) {
     }
     if (p->inner_prec < DD_PREC_F64 || p->inner_prec > DD_PREC_F16 || p->block_prec < DD_PREC_F64 ||
         p->block_prec > DD_PREC_F32 || p->active_mode < DD_ACTIVE_AUTO || p->active_mode > DD_ACTIVE_ALL ||
-        (p->outer_prec != DD_PREC_F64 && p->outer_prec != DD_PREC_DF64)) {
+        (p->outer_prec != DD_PREC_F64 && p->outer_prec != DD_PREC_DF64) || p->krylov < DD_KRYLOV_CGNR ||
+        p->krylov > DD_KRYLOV_SAP_GCR) {
+        delete h;
+        return DD_ERR_INVALID_ARG;
+    }
+    if (p->krylov == DD_KRYLOV_SAP_GCR &&
+        (p->outer_prec != DD_PREC_F64 || p->sap_ncy < 1 || p->sap_ncy > 16 || p->sap_nmr < 1 || p->sap_nmr > 64 ||
+         p->sap_nkv < 1 || p->sap_nkv > DD_SAP_MAX_NKV)) {
         delete h;
         return DD_ERR_INVALID_ARG;
     }
@@ -619,7 +644,7 @@ extern "C" int dd_set_workspace(dd_t h, void* dev_ptr, size_t bytes) {
     plan(h, h->ws);
     // reduction tickets and solver states start from zero
     DD_CUDA(h, cudaMemsetAsync(h->d_counters, 0, sizeof(unsigned) * (4 * (h->prm.max_rhs + 1) + 64), h->stream));
-    DD_CUDA(h, cudaMemsetAsync(h->d_cg, 0, sizeof(CGState) * (2 * h->prm.max_rhs + 2), h->stream));
+    DD_CUDA(h, cudaMemsetAsync(h->d_cg, 0, sizeof(CGState) * (3 * h->prm.max_rhs + 2), h->stream));
     return DD_OK;
 }
 

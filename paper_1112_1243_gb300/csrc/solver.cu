@@ -1035,6 +1035,8 @@ int defect_correction_df(dd_handle* h, int nrhs, int field0, int step, Inner& cg
     return conv ? DD_OK : DD_ERR_NOT_CONVERGED;
 }
 
+#include "sapgcr.cuh"
+
 }  // namespace
 
 template <class B>
@@ -1078,7 +1080,34 @@ static int solve_packed_mask(dd_handle* h, SiteSet S, int nrhs, int field0, int 
         cg.outer = outer;
         cg.S = S;
         return defect_correction<MASK>(h, nrhs, field0, step, cg, true, tol, maxit, iters, relres);
-    } else if (h->prm.krylov == DD_KRYLOV_BICGSTAB) {
+    } else if (MASK == 0 && h->prm.krylov == DD_KRYLOV_SAP_GCR) {
+        // SAP-preconditioned flexible GCR on D (global solves only)
+        auto fill = [&](auto& sg) {
+            sg.h = h;
+            sg.nrhs = nrhs;
+            sg.x = SpinorF32{v.x32, Vh};
+            sg.r = SpinorF32{v.r32, Vh};
+            sg.st = inner;
+            sg.outer = outer;
+            sg.S = S;
+            sg.bst = h->d_cg + 2 * h->prm.max_rhs;
+            sg.ncy = h->prm.sap_ncy;
+            sg.nmr = h->prm.sap_nmr;
+            sg.nkv = h->sap.nkv;
+        };
+        if (prec == DD_PREC_F32) {
+            SapGcr<SpinorF32, LinkF32> sg;
+            fill(sg);
+            sg.lk = field_links<LinkF32>(h, field0);
+            sg.lk_rs = field_stride<LinkF32>(h, step);
+            return defect_correction<MASK>(h, nrhs, field0, step, sg, false, tol, maxit, iters, relres);
+        }
+        SapGcr<SpinorF16, LinkF16> sg;
+        fill(sg);
+        sg.lk = field_links<LinkF16>(h, field0);
+        sg.lk_rs = field_stride<LinkF16>(h, step);
+        return defect_correction<MASK>(h, nrhs, field0, step, sg, false, tol, maxit, iters, relres);
+    } else if (h->prm.krylov != DD_KRYLOV_CGNR) {
         if (prec == DD_PREC_F32) {
             BiCGStab<float, SpinorF32, SpinorF32, LinkF32, MASK> bi;
             fill_bicg(h, bi, Vh, inner, outer, nrhs);
@@ -1149,7 +1178,8 @@ int solve_packed(dd_handle* h, int nrhs, int field0, int step, int prec, double 
     SiteSet S{nullptr, (long long)h->g.Vh};
     // Dirichlet solves whose right-hand sides live on the blocks of one
     // colour: the other colour's sites stay zero and are not visited
-    if (mask == 1 && colour >= 0 && colour <= 1 && h->d_colour_sites[colour]) S = SiteSet{h->d_colour_sites[colour], (long long)h->g.Vh / 2};
+    if (mask == 1 && colour >= 0 && colour <= 1 && h->d_colour_sites[colour])
+        S = SiteSet{h->d_colour_sites[colour], (long long)h->g.Vh / 2, colour};
     if (mask == 1) return solve_packed_mask<1>(h, S, nrhs, field0, step, prec, tol, maxit, iters, relres);
     return solve_packed_mask<0>(h, S, nrhs, field0, step, prec, tol, maxit, iters, relres);
 }
@@ -1177,5 +1207,68 @@ extern "C" int dd_solve(dd_t h, void* x, const void* b, const void* U, int nrhs,
     launch_unpack_spinor_eo(h, v.xo, (double*)x, 1, nrhs, 24 * V);
     DD_LAUNCH_CHECK(h, "dd_solve unpack");
     if (rc == DD_ERR_NOT_CONVERGED) return dd_fail(h, rc, "dd_solve: iteration cap reached");
+    return DD_OK;
+}
+
+// ncy Schwarz cycles applied to nrhs canonical spinors (see include/dd.h)
+extern "C" int dd_sap_apply(dd_t h, void* out, const void* in, const void* U, int nrhs, int prec) {
+    int rc = dd_require_ws(h);
+    if (rc) return rc;
+    rc = dd_require_feature(h, h->feat_solve, "dd_sap_apply");
+    if (rc) return rc;
+    if (!out || !in || !U || nrhs < 1 || nrhs > h->prm.max_rhs || (prec != DD_PREC_F32 && prec != DD_PREC_F16))
+        return dd_fail(h, DD_ERR_INVALID_ARG, "dd_sap_apply: bad arguments");
+    if (h->prm.krylov != DD_KRYLOV_SAP_GCR || !h->sap.halves)
+        return dd_fail(h, DD_ERR_UNSUPPORTED, "dd_sap_apply: handle not created with krylov DD_KRYLOV_SAP_GCR");
+    if (!h->d_colour_sites[0] || !h->d_colour_sites[1])
+        return dd_fail(h, DD_ERR_UNSUPPORTED, "dd_sap_apply: needs an even block extent along axis 0");
+    const long long V = h->g.V, Vh = h->g.Vh;
+    rc = format_field(h, (const double*)U, h->fields[0], true, prec == DD_PREC_F32, prec == DD_PREC_F16, false, false);
+    if (rc) return rc;
+    SolverVecs& v = h->vecs[0];
+    launch_pack_spinor_eo(h, (const double*)in, v.be, 0, nrhs, 24 * V);
+    launch_pack_spinor_eo(h, (const double*)in, v.bo, 1, nrhs, 24 * V);
+    const SiteSet S{nullptr, Vh};
+    dim3 grid(grid_for(Vh, 128), nrhs);
+    CGState* st = h->d_cg;
+    double* ones = h->d_scalars + 3 * h->prm.max_rhs;
+    DD_KLAUNCH(h, fill_kernel<<<1, 64, 0, h->stream>>>(nrhs, ones, 1.0));
+    DD_KLAUNCH(h, cg_arm_kernel<<<1, 64, 0, h->stream>>>(nrhs, st, nullptr, ones, 0.0, 0.0, 1));
+    auto go = [&](auto& sg) -> int {
+        sg.h = h;
+        sg.nrhs = nrhs;
+        sg.x = SpinorF32{v.x32, Vh};
+        sg.r = SpinorF32{v.r32, Vh};
+        sg.st = st;
+        sg.outer = nullptr;
+        sg.S = S;
+        sg.bst = h->d_cg + 2 * h->prm.max_rhs;
+        sg.ncy = h->prm.sap_ncy;
+        sg.nmr = h->prm.sap_nmr;
+        sg.nkv = h->sap.nkv;
+        const FullF32 rho = sg.R(), z = sg.Zk(0);
+        DD_KLAUNCH(h, copy_kernel<SpinorF64, SpinorF32><<<grid, 128, 0, h->stream>>>(S, SpinorF64{v.be, Vh}, rho.e, nullptr));
+        DD_KLAUNCH(h, copy_kernel<SpinorF64, SpinorF32><<<grid, 128, 0, h->stream>>>(S, SpinorF64{v.bo, Vh}, rho.o, nullptr));
+        int r2 = sg.precondition(rho, z);
+        if (r2) return r2;
+        DD_KLAUNCH(h, copy_kernel<SpinorF32, SpinorF64><<<grid, 128, 0, h->stream>>>(S, z.e, SpinorF64{v.xe, Vh}, nullptr));
+        DD_KLAUNCH(h, copy_kernel<SpinorF32, SpinorF64><<<grid, 128, 0, h->stream>>>(S, z.o, SpinorF64{v.xo, Vh}, nullptr));
+        return DD_OK;
+    };
+    if (prec == DD_PREC_F32) {
+        SapGcr<SpinorF32, LinkF32> sg;
+        sg.lk = field_links<LinkF32>(h, 0);
+        sg.lk_rs = 0;
+        rc = go(sg);
+    } else {
+        SapGcr<SpinorF16, LinkF16> sg;
+        sg.lk = field_links<LinkF16>(h, 0);
+        sg.lk_rs = 0;
+        rc = go(sg);
+    }
+    if (rc) return dd_fail(h, rc, "dd_sap_apply failed");
+    launch_unpack_spinor_eo(h, v.xe, (double*)out, 0, nrhs, 24 * V);
+    launch_unpack_spinor_eo(h, v.xo, (double*)out, 1, nrhs, 24 * V);
+    DD_LAUNCH_CHECK(h, "dd_sap_apply");
     return DD_OK;
 }

@@ -84,7 +84,7 @@ def _dinv_norm(U, lat, kappa):
     return 1.0 / np.linalg.svd(D, compute_uv=False)[-1]
 
 
-@pytest.mark.parametrize("prec,krylov", [(0, 0), (1, 0), (2, 0), (2, 1)])
+@pytest.mark.parametrize("prec,krylov", [(0, 0), (1, 0), (2, 0), (2, 1), (2, 2)])
 @pytest.mark.parametrize("n,mode", [(1, "factors"), (3, "factors"), (2, "replicas")])
 def test_global_estimate_small(api, prec, krylov, n, mode):
     dims, block, kappa = (4, 4, 4, 4), (2, 2, 2, 2), 0.12

@@ -100,3 +100,39 @@ def test_roofline_entries():
     assert abs(r1["frac"] - r1["achieved"] / 6800.0) < 1e-15
     assert bench.roofline_entry(2, m[2], 0.0, 1, 10, 1.0, 6800.0, alu, "probe") is None
     assert bench.roofline_entry(2, m[2], 1.0, 1, 0, 1.0, 6800.0, alu, "probe") is None
+
+
+def colour_site(L, b, c, t, p):
+    """The arithmetic the hop kernels use for the t-th site of the blocks of
+    colour c (even block extent along axis 0): even-odd index h and x."""
+    Lh0 = L[0] // 2
+    q = Lh0 // 2
+    r, u = divmod(t, q)
+    B = b[0] // 2
+    m, k = divmod(u, B)
+    x1 = r % L[1]
+    x2 = (r // L[1]) % L[2]
+    x3 = r // (L[1] * L[2])
+    cr = (x1 // b[1] + x2 // b[2] + x3 // b[3]) & 1
+    hx = (2 * m + ((c + cr) & 1)) * B + k
+    x0 = 2 * hx + ((p + x1 + x2 + x3) & 1)
+    return hx + Lh0 * r, (x0, x1, x2, x3)
+
+
+def test_colour_site_arithmetic_lists_the_colour_sets():
+    """For every parity, the computed sites are the sites of the blocks of
+    colour c (colour of the block-coordinate sum), each once, in increasing
+    even-odd index -- the order of the stored colour maps."""
+    for L, b in (((4, 4, 4, 4), (2, 2, 2, 2)), ((8, 8, 8, 8), (4, 4, 4, 4)), ((16, 8, 8, 16), (8, 4, 4, 8)),
+                 ((8, 4, 4, 4), (4, 2, 2, 2)), ((12, 12, 12, 12), (6, 6, 6, 6)), ((32, 8, 8, 16), (8, 8, 8, 8))):
+        Vh = L[0] * L[1] * L[2] * L[3] // 2
+        for p in (0, 1):
+            for c in (0, 1):
+                hs = []
+                for t in range(Vh // 2):
+                    h, x = colour_site(L, b, c, t, p)
+                    assert (x[0] + x[1] + x[2] + x[3]) % 2 == p
+                    assert (x[0] // b[0] + x[1] // b[1] + x[2] // b[2] + x[3] // b[3]) % 2 == c
+                    assert h == (x[0] + L[0] * (x[1] + L[1] * (x[2] + L[2] * x[3]))) // 2
+                    hs.append(h)
+                assert hs == sorted(set(hs)) and len(hs) == Vh // 2
