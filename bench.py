@@ -543,6 +543,7 @@ def run_gpu(args, cfg):
         line["graph"] = {"value": est / (tg / 1e3), "unit": "estimates/s", "ms_per_step": tg / args.steps,
                          "top_level_nodes": api.dd_graph_nodes(g), "device_status": st_code}
         api.dd_graph_destroy(g)
+        del g  # the graph object holds the handle: release it with the handle
     if args.fp64_steps > 0:
         h64 = api.dd_init(cfg["dims"], cfg["block"], cfg["kappa"], max_rhs=nmax, inner_prec=api.DD_PREC_F64,
                           block_prec=api.DD_PREC_F32, tol_global=1e-10, tol_block=1e-12, maxit=40000,

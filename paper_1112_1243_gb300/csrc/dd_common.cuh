@@ -280,8 +280,8 @@ struct Geo {
     int st[4];    // canonical strides 1, L0, L0 L1, L0 L1 L2
     // multipliers for division by Lh0, L1, L2 with __umulhi (exact for n * d < 2^32; 0: use '/')
     unsigned mLh0, mL1, mL2;
-    // the same for Lh0 / 2, b0 / 2, b1, b2, b3 (colour site sets)
-    unsigned mQ, mB, mb1, mb2, mb3;
+    // the same for Lh0 / 2, b0 / 2 (colour site sets) and the block extents b0..b3
+    unsigned mQ, mB, mb[4];
 };
 
 // derived members of a Geo whose L, b, nbk and bc are set (host side)
@@ -306,9 +306,10 @@ inline void geo_finish(Geo& g) {
     g.mL2 = magic(g.L[2]);
     g.mQ = magic(g.Lh0 / 2);
     g.mB = magic(g.b[0] / 2);
-    g.mb1 = magic(g.b[1]);
-    g.mb2 = magic(g.b[2]);
-    g.mb3 = magic(g.b[3]);
+    for (int a = 0; a < 4; ++a) {
+        // dividends are coordinates (< L_a); the check on Vh above is stricter
+        g.mb[a] = magic(g.b[a]);
+    }
 }
 
 // n / d with a precomputed multiplier (m = 0: plain division)
@@ -342,7 +343,7 @@ DD_DEV int colour_site(const Geo& g, int c, int t, int p, int x[4]) {
     x[1] = r - s1 * g.L[1];
     x[3] = fast_div(s1, g.L[2], g.mL2);
     x[2] = s1 - x[3] * g.L[2];
-    const int cr = (fast_div(x[1], g.b[1], g.mb1) + fast_div(x[2], g.b[2], g.mb2) + fast_div(x[3], g.b[3], g.mb3)) & 1;
+    const int cr = (fast_div(x[1], g.b[1], g.mb[1]) + fast_div(x[2], g.b[2], g.mb[2]) + fast_div(x[3], g.b[3], g.mb[3])) & 1;
     const int hx = (2 * m + ((c + cr) & 1)) * B + k;
     x[0] = 2 * hx + ((p + x[1] + x[2] + x[3]) & 1);
     return hx + g.Lh0 * r;

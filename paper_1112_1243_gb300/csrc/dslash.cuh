@@ -66,7 +66,8 @@ DD_DEV void hop_site(const Geo& g, int p, int h, const int x[4], const SIn& in, 
     const int s = canon_index(g, x);
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        int loc = x[a] % g.b[a];
+        // local coordinate in the block (multiply-high division: b_a is not a compile-time constant)
+        const int loc = x[a] - fast_div(x[a], g.b[a], g.mb[a]) * g.b[a];
         // forward: (1 - gamma_a) U_a(x) psi(x + a)
         bool okf = true, okb = true;
         if (MASK == 1) {
