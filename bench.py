@@ -81,7 +81,7 @@ def parse():
     p.add_argument("--sap-ncy", type=int, default=4, help="Schwarz cycles per SAP-GCR preconditioner application")
     p.add_argument("--sap-nmr", type=int, default=4, help="BiCGStab iterations per approximate SAP block solve")
     p.add_argument("--sap-nkv", type=int, default=6, help="directions of the flexible GCR before a restart")
-    p.add_argument("--mode", default="step", choices=["step", "solve"],
+    p.add_argument("--mode", default="step", choices=["step", "solve", "lu"],
                    help="step: the hierarchical step (the benchmark); solve: one-rhs global solves on a lean "
                         "handle (kernel captures and Dslash GB/s)")
     return p.parse_args()
@@ -893,6 +893,13 @@ def main():
         return run_reference(args, cfg)
     if args.mode == "solve":
         return run_solve(args, cfg)
+    if args.mode == "lu":
+        import torch
+        from paper_1112_1243_gb300 import build
+        build.build()
+        dev = torch.device("cuda", 0)
+        print(json.dumps({"mode": "lu", "exact_lu": measure_lu(dev, torch.cuda.current_stream(dev))}))
+        return 0
     return run_gpu(args, cfg)
 
 
