@@ -370,10 +370,12 @@ const char* dd_last_error(dd_t h);
 int dd_launch_count(dd_t h, long long* launches);
 int dd_kernel_timer(dd_t h, int op, int kind, int every, double* total_ms, long long* timed, long long* sites);
 /* Timer kinds beyond the whole-lattice hops 0-3: 4 FP64, 5 FP16 -> FP16 and
- * 6 FP16 -> FP32 hops restricted to the blocks (Dirichlet solves of the
- * Schur pieces and of the whole-lattice filter form); 7 the persistent block
- * solver (sites = block items of the timed launches). */
-#define DD_TIMER_KIND_COUNT 8
+ * 6 FP16 -> FP32 hops restricted to the blocks on the sites of one block
+ * colour (Dirichlet solves of the Schur pieces; kind 4 also the filter);
+ * 7 the persistent block solver (sites = block items of the timed
+ * launches); 8 FP16 -> FP16 and 9 FP16 -> FP32 hops restricted to the
+ * blocks over every site (the whole-lattice filter form). */
+#define DD_TIMER_KIND_COUNT 10
 
 /* Iteration counts of the solves since the last dd_kernel_timer(op 1) (the
  * paper has no counterpart: work accounting for the measurement).  kind 0:

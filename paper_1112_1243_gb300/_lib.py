@@ -32,7 +32,7 @@ DD_PURPOSE_BLOCK_SCHUR_NOISE = 4
 DD_PURPOSE_BLOCK_SCHUR_ACCEPT = 8
 DD_EST_FACTORS, DD_EST_REPLICAS, DD_EST_INTERP_ALL = 0, 1, 4
 DD_FILTER_STOCHASTIC, DD_FILTER_EXACT = 0, 1
-DD_TIMER_KIND_COUNT = 8
+DD_TIMER_KIND_COUNT = 10
 DD_KRYLOV_CGNR, DD_KRYLOV_BICGSTAB, DD_KRYLOV_SAP_GCR = 0, 1, 2
 
 ERROR_NAMES = {

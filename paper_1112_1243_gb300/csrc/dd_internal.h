@@ -112,8 +112,10 @@ struct SapVecs {
 constexpr int DD_BLOCK_CTAS_MAX = 4;
 // timed kernel kinds: whole-lattice hops 0 FP16 -> FP16, 1 FP16 -> FP32 (xpay),
 // 2 FP64, 3 double-float residual; Dirichlet (block-restricted) hops 4 FP64,
-// 5 FP16 -> FP16, 6 FP16 -> FP32; 7 the persistent block solver
-constexpr int DD_TIMER_KINDS = 8;
+// 5 FP16 -> FP16, 6 FP16 -> FP32 on the sites of one block colour; 7 the
+// persistent block solver; 8 FP16 -> FP16, 9 FP16 -> FP32 Dirichlet hops over
+// every site (both colours)
+constexpr int DD_TIMER_KINDS = 10;
 // device counters after the timer sites: items, inner iterations, outer
 // cycles and site-iterations of the persistent block solver
 constexpr int DD_BLOCK_STATS = 4;

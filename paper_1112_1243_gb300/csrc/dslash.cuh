@@ -212,8 +212,10 @@ inline void launch_hop(const HopArgs<SIn, SX, SOut, LK>& A, int nrhs, dd_handle*
     const int spt = (!f64 && h->tune.hop_spt == 2) ? 2 : 1;
     dim3 grid(grid_for(B.S.n, (long long)tpb * spt), nrhs);
     constexpr int kind0 = hop_kind<SIn, SOut>();
-    // whole-lattice hops keep kinds 0-2; Dirichlet hops are timed as 4 (FP64), 5, 6
-    constexpr int kind = MASK == 0 ? kind0 : (MASK == 1 && kind0 >= 0 ? (kind0 == 2 ? 4 : 5 + kind0) : -1);
+    // whole-lattice hops keep kinds 0-2; Dirichlet hops are timed as 4 (FP64),
+    // 5, 6 (one block colour's sites) or 8, 9 (every site)
+    constexpr int kindm = MASK == 0 ? kind0 : (MASK == 1 && kind0 >= 0 ? (kind0 == 2 ? 4 : 5 + kind0) : -1);
+    const int kind = (MASK == 1 && kind0 >= 0 && kind0 < 2 && B.S.colour < 0) ? 8 + kind0 : kindm;
     bool timed = false;
     if (kind >= 0 && h->timer_on && !h->capturing && !dd_stream_capturing(h)) timed = (h->timer_seen[kind]++ % h->timer_every) == 0;
     B.sites = nullptr;

@@ -308,6 +308,7 @@ static bool block_timer_begin(dd_handle* h) {
     return true;
 }
 static void block_timer_end(dd_handle* h, int nitems) {
+    static_assert(DD_TIMER_KINDS > 7, "timer kind 7 is the persistent block solver");
     cudaEvent_t e = dd_timer_event(h, 7);
     if (e) cudaEventRecord(e, h->stream);
     add_count_kernel<<<1, 1, 0, h->stream>>>(h->d_sites + 7, (unsigned long long)nitems);
