@@ -76,6 +76,8 @@ def parse():
     p.add_argument("--krylov", default="bicgstab", choices=["cgnr", "bicgstab", "sap"],
                    help="inner Krylov method of the mixed-precision solves")
     p.add_argument("--no-lu", action="store_true", help="skip the timing of the dense LU check path (c1)")
+    p.add_argument("--no-tol-block", action="store_true",
+                   help="skip the measurement of the step with Dirichlet solves to 1e-10 instead of 1e-12")
     p.add_argument("--no-sap", action="store_true",
                    help="skip the measurement of the step with SAP-preconditioned GCR global solves")
     p.add_argument("--sap-ncy", type=int, default=4, help="Schwarz cycles per SAP-GCR preconditioner application")
@@ -434,10 +436,12 @@ def run_gpu(args, cfg):
     l0 = api.dd_launch_count(h)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     acc = []
+    ref_ln = []
     with ClockSampler(local) as clocks:
         e0.record(stream)
         for k in range(args.steps):
             ln, a = chain.step(U, args.warmup + k)
+            ref_ln.append(ln.clone())
         e1.record(stream)
         barrier()
     t_ms = e0.elapsed_time(e1)
@@ -572,12 +576,17 @@ def run_gpu(args, cfg):
     del h
     torch.cuda.empty_cache()
     if not args.no_outer_df64 and args.outer == "f64" and args.prec != "f64":
-        line["outer_df64"] = measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune)
+        line["outer_df64"] = measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune, ref_ln=ref_ln)
+    if not args.no_tol_block and args.prec != "f64":
+        # Dirichlet solves of the Schur pieces and the filter to 1e-10 instead of 1e-12
+        line["tol_block_1e-10"] = measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune,
+                                                     outer=api.DD_PREC_F64, tol_block=1e-10, ref_ln=ref_ln)
     if not args.no_sap and args.prec != "f64":
         # the global solves by SAP-preconditioned flexible GCR instead of BiCGStab
         sap = {"sap_ncy": args.sap_ncy, "sap_nmr": args.sap_nmr, "sap_nkv": args.sap_nkv}
         line["sap_gcr"] = dict(measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune,
-                                                  krylov=api.DD_KRYLOV_SAP_GCR, outer=api.DD_PREC_F64, sap=sap),
+                                                  krylov=api.DD_KRYLOV_SAP_GCR, outer=api.DD_PREC_F64, sap=sap,
+                                                  ref_ln=ref_ln),
                                parameters=sap, bicgstab_global_solves=iterations.get("global"))
     if args.compare_config:
         # mixed versus plain FP64 on smaller workloads (the FP64 path at the
@@ -617,7 +626,8 @@ def run_gpu(args, cfg):
     return 0
 
 
-def measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune, krylov=None, outer=None, sap=None):
+def measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune, krylov=None, outer=None, sap=None,
+                       tol_block=1e-12, ref_ln=None):
     """The timed step again with the defect-correction residual in
     double-float arithmetic (outer_prec DD_PREC_DF64), or with another inner
     Krylov method (krylov, sap: DD_KRYLOV_SAP_GCR and its parameters), same
@@ -633,7 +643,7 @@ def measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune, krylov=N
     outer = api.DD_PREC_DF64 if outer is None else outer
     nmax = max(cfg["n_global"], cfg["n_block"])
     h = api.dd_init(cfg["dims"], cfg["block"], cfg["kappa"], max_rhs=nmax, inner_prec=prec,
-                    block_prec=api.DD_PREC_F32, tol_global=1e-10, tol_block=1e-12, tol_inner=args.tol_inner,
+                    block_prec=api.DD_PREC_F32, tol_global=1e-10, tol_block=tol_block, tol_inner=args.tol_inner,
                     maxit=40000, stream=stream, device=dev, krylov=krylov, outer_prec=outer, **(sap or {}))
     if tune:
         api.dd_set_tuning(h, hop_tpb=tune["hop_tpb"], hop_spt=tune["hop_spt"], hop64_tpb=tune["hop64_tpb"],
@@ -648,8 +658,10 @@ def measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune, krylov=N
     api.dd_kernel_timer(h, 1, 0, 1)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    lns = []
     for k in range(args.steps):
-        chain.step(U, args.warmup + k)
+        ln, _ = chain.step(U, args.warmup + k)
+        lns.append(ln.clone())
     e1.record(stream)
     torch.cuda.synchronize(dev)
     t_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
@@ -662,6 +674,11 @@ def measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune, krylov=N
                                  outer_cycles_per_solve=glob["outer_cycles"] / max(1, glob["solves"]))}
     if cnt3:
         out.update(residual_hop_avg_us=1e3 * ms3 / max(1, cnt3), residual_hop_launches_timed=cnt3)
+    if ref_ln is not None:
+        # the same steps (field, seeds, step indices) as the default run: the
+        # largest change of any ln r_i against it
+        out["max_abs_dln_vs_default"] = max(float((a - b).abs().max()) for a, b in zip(lns, ref_ln))
+        out["ln_scale"] = max(float(b.abs().max()) for b in ref_ln)
     del chain
     del h
     torch.cuda.empty_cache()
@@ -769,6 +786,37 @@ def measure_batched_filter(dev, stream, reps=3):
     ms7, cnt7, _ = api.dd_kernel_timer(hs[0], 2, 7)
     st = api.dd_solver_stats(hs[0], 2)
     api.dd_kernel_timer(hs[0], 0, 0)
+    # the same call recorded once as a CUDA graph on the first handle and replayed
+    ln = [torch.zeros(h.nblocks, dtype=torch.float64, device=dev) for h in hs]
+    acc = [torch.zeros(h.nblocks, dtype=torch.uint8, device=dev) for h in hs]
+    for w, u in zip(work, Ups):
+        w.copy_(u)
+    api.dd_block_filter_batch(hs, Us, work, 3, n, 4, 3, ln, acc)
+    for w, u in zip(work, Ups):
+        w.copy_(u)
+    api.dd_graph_begin(hs[0])
+    try:
+        api.dd_block_filter_batch(hs, Us, work, 3, n, 4, 3, ln, acc)
+    finally:
+        g = api.dd_graph_end(hs[0])
+    for _ in range(2):
+        for w, u in zip(work, Ups):
+            w.copy_(u)
+        api.dd_graph_launch(g, 0)
+    torch.cuda.synchronize(dev)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for r in range(reps):
+        for w, u in zip(work, Ups):
+            w.copy_(u)
+        api.dd_graph_launch(g, (r + 1) << 20)
+    g1.record(stream)
+    torch.cuda.synchronize(dev)
+    tg = g0.elapsed_time(g1) / 1e3 / reps
+    graph = {"seconds_per_call": tg, "block_estimates_per_s": items / tg, "top_level_nodes": api.dd_graph_nodes(g),
+             "device_status": api.dd_status(hs[0])[0]}
+    api.dd_graph_destroy(g)
+    del g
     alu = peaks_alu(stream)
     kmodel = kernel_models((8, 8, 8, 8))[7]
     roof = roofline_entry(7, kmodel, ms7, cnt7, st["site_iterations"], 1e3 * t * reps, 6800.0, alu[0], alu[1])
@@ -778,7 +826,7 @@ def measure_batched_filter(dev, stream, reps=3):
            "launch_shape": {"threads": tune["block_tpb"], "blocks_per_sm": tune["block_ctas_per_sm"]},
            "iterations": dict(st, inner_per_item=st["inner_iterations"] / max(1, st["items"]),
                               outer_per_item=st["outer_cycles"] / max(1, st["items"])),
-           "roofline": roof}
+           "roofline": roof, "graph": graph}
     for h in hs:
         del h
     return out

@@ -307,9 +307,12 @@ int dd_relative_gauge_fix(dd_t h, const void* U, void* U_new, int sweeps, double
  * lattices (e.g. 4^4, 6^4 and 8^4).  Per handle k the results are those of
  * dd_block_filter(hs[k], U_old[k], U_new[k], colour_mask, DD_FILTER_STOCHASTIC,
  * n, seed, ctr, ln_b[k], accept[k]) (same random streams, same arithmetic).
- * All handles must share one stream and block precision; hs, U_old, U_new,
- * ln_b and accept are host arrays of nh pointers (the pointers themselves
- * device memory).  ws: device memory of at least
+ * All handles must share one stream and block precision; every launch of
+ * the call goes to the first handle's stream, so a CUDA graph recorded on
+ * hs[0] (dd_graph_begin) holds the whole batch (the descriptor tables must
+ * then equal those of the last eager call with the same ws).  hs, U_old,
+ * U_new, ln_b and accept are host arrays of nh pointers (the pointers
+ * themselves device memory).  ws: device memory of at least
  * dd_block_filter_batch_workspace(nh, hs, n) bytes, 256-byte aligned, owned
  * by the caller (holds the item queue and the thread-block scratch slots). */
 int dd_block_filter_batch_workspace(int nh, const dd_t* hs, int n, size_t* bytes);

@@ -219,7 +219,11 @@ def dd_block_filter_batch(hs, U_olds, U_news, colour_mask, n, seed, ctr, ln_bs=N
     rc = lib.dd_block_filter_batch_workspace(nh, harr, int(n), ctypes.byref(size))
     if rc != _lib.DD_OK:
         raise DDError(rc, "dd_block_filter_batch_workspace failed")
-    ws = torch.empty(size.value + 256, dtype=torch.uint8, device=dev)
+    # the scratch of the last call is reused when large enough (a CUDA-graph
+    # capture of this call needs the scratch of the eager call before it)
+    ws = getattr(hs[0], "batch_ws", None)
+    if ws is None or ws.numel() < size.value + 256 or ws.device != dev:
+        ws = torch.empty(size.value + 256, dtype=torch.uint8, device=dev)
     base = (ws.data_ptr() + 255) & ~255
     if ln_bs is None:
         ln_bs = [torch.zeros(h.nblocks, dtype=torch.float64, device=dev) for h in hs]

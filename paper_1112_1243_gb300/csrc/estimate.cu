@@ -785,6 +785,28 @@ extern "C" int dd_block_filter_batch(int nh, const dd_t* hs_, const void* const*
     for (int k = 0; k < nh; ++k)
         if (!U_old[k] || !U_new[k] || !ln_b[k] || !accept[k])
             return dd_fail(h0, DD_ERR_INVALID_ARG, "dd_block_filter_batch: null field or output");
+    // every launch of the batch runs on the first handle's stream (also while
+    // that handle records a CUDA graph): the other handles follow it for the call
+    struct FollowFirst {
+        dd_handle* const* hs;
+        int nh;
+        std::vector<cudaStream_t> streams;
+        std::vector<bool> capturing;
+        FollowFirst(dd_handle* const* hs_, int nh_) : hs(hs_), nh(nh_), streams(nh_), capturing(nh_) {
+            for (int k = 0; k < nh; ++k) {
+                streams[k] = hs[k]->stream;
+                capturing[k] = hs[k]->capturing;
+                hs[k]->stream = hs[0]->stream;
+                hs[k]->capturing = hs[0]->capturing;
+            }
+        }
+        ~FollowFirst() {
+            for (int k = 1; k < nh; ++k) {
+                hs[k]->stream = streams[k];
+                hs[k]->capturing = capturing[k];
+            }
+        }
+    } follow(hs, nh);
     char* w = (char*)ws;
     LatDesc* d_lats = (LatDesc*)(w + P.lats);
     BlockItem* d_items = (BlockItem*)(w + P.items);

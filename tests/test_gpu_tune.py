@@ -85,3 +85,32 @@ def test_autotune_picks_candidate_and_stays_correct(api):
     rep2 = api.dd_autotune(h, api.DD_TUNE_HOP | api.DD_TUNE_BLOCK, Ud, Up, reps=4)
     rep3 = api.dd_autotune(h, api.DD_TUNE_HOP | api.DD_TUNE_BLOCK, Ud, Up, reps=4)
     assert rep3["from_cache"] and (rep3["hop_tpb"], rep3["hop_spt"]) == (rep2["hop_tpb"], rep2["hop_spt"])
+
+
+def test_instrumentation_counts_and_peaks():
+    """dd_alu_peaks gives plausible pipe rates (FP32 FMA far above FP64 FMA);
+    dd_solver_stats counts one batched whole-lattice solve of nrhs systems with
+    its inner iterations and defect cycles; the kernel timer sees the hop
+    kinds of that solve."""
+    import torch
+    api = lib_api()
+    pk = api.dd_alu_peaks()
+    assert 0.1 < pk["fp64_fma"] < 20 and 10 < pk["fp32_fma"] < 500 and pk["fp32_fma"] > 10 * pk["fp64_fma"]
+    assert 0.05 < pk["fp64_mma"] < 100
+    dims, block = (8, 8, 8, 8), (4, 4, 4, 4)
+    U = dev(synthetic.random_gauge(dims, 0.3, 5))
+    b = dev(synthetic.random_spinor(dims, 6, nrhs=2))
+    h = api.dd_init(dims, block, 0.13, max_rhs=2, inner_prec=api.DD_PREC_F16, krylov=api.DD_KRYLOV_BICGSTAB)
+    x = torch.zeros_like(b)
+    api.dd_kernel_timer(h, 1, 0, 1)
+    it, res, _ = api.dd_solve(h, x, b, U, 2, api.DD_PREC_F16)
+    st = api.dd_solver_stats(h, 0)
+    assert st["solves"] == 1 and st["systems"] == 2 and st["inner_iterations"] == it > 0
+    assert st["outer_cycles"] >= 1 and st["site_iterations"] == it * (h.V // 2)
+    assert api.dd_solver_stats(h, 1)["solves"] == 0
+    ms, cnt, sites = api.dd_kernel_timer(h, 2, 1)
+    assert cnt > 0 and ms > 0 and sites > 0
+    ms2, cnt2, _ = api.dd_kernel_timer(h, 2, 2)
+    assert cnt2 >= 2                                   # FP64 residual hops of the defect correction
+    api.dd_kernel_timer(h, 1, 0, 1)                    # reset
+    assert api.dd_solver_stats(h, 0)["solves"] == 0
