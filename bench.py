@@ -533,9 +533,21 @@ def run_gpu(args, cfg):
         f1.record(stream)
         barrier()
         te = max_over_ranks(f0.elapsed_time(f1), world, dev)
+        # the host<->device copies of one step alone (same buffers, no step)
+        U_back = torch.empty_like(U_host).pin_memory()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for k in range(args.steps):
+            U_dev.copy_(U_host, non_blocking=True)
+            U_back.copy_(U_dev, non_blocking=True)
+        c1.record(stream)
+        c1.synchronize()
         line["e2e"] = {"value": est / (te / 1e3), "unit": "estimates/s",
                        "h2d_bytes_per_step": U.numel() * 16,
-                       "d2h_bytes_per_step": U.numel() * 16 + cfg["n_global"] * 8 + 1}
+                       "d2h_bytes_per_step": U.numel() * 16 + cfg["n_global"] * 8 + 1,
+                       "ms_per_step": te / args.steps,
+                       "copy_ms_per_step": c0.elapsed_time(c1) / args.steps}
+        del U_back
     # the same step recorded once as a CUDA graph (solver loops as device-side
     # conditional nodes) and replayed with advancing random streams
     if not args.no_graph:
@@ -575,30 +587,33 @@ def run_gpu(args, cfg):
     del chain
     del h
     torch.cuda.empty_cache()
+    # supplementary measurements: one that fails is recorded in the line as
+    # {"error": ...} and the run goes on (the numbers above stay valid)
     if not args.no_outer_df64 and args.outer == "f64" and args.prec != "f64":
-        line["outer_df64"] = measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune, ref_ln=ref_ln)
+        supplement(line, "outer_df64", lambda: measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune,
+                                                                  ref_ln=ref_ln))
     if not args.no_tol_block and args.prec != "f64":
         # Dirichlet solves of the Schur pieces and the filter to 1e-10 instead of 1e-12
-        line["tol_block_1e-10"] = measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune,
-                                                     outer=api.DD_PREC_F64, tol_block=1e-10, ref_ln=ref_ln)
+        supplement(line, "tol_block_1e-10", lambda: measure_outer_df64(
+            args, cfg, dev, stream, rank, world, U_np, tune, outer=api.DD_PREC_F64, tol_block=1e-10, ref_ln=ref_ln))
     if not args.no_sap and args.prec != "f64":
         # the global solves by SAP-preconditioned flexible GCR instead of BiCGStab
         sap = {"sap_ncy": args.sap_ncy, "sap_nmr": args.sap_nmr, "sap_nkv": args.sap_nkv}
-        line["sap_gcr"] = dict(measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune,
-                                                  krylov=api.DD_KRYLOV_SAP_GCR, outer=api.DD_PREC_F64, sap=sap,
-                                                  ref_ln=ref_ln),
-                               parameters=sap, bicgstab_global_solves=iterations.get("global"))
+        supplement(line, "sap_gcr", lambda: dict(
+            measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune, krylov=api.DD_KRYLOV_SAP_GCR,
+                               outer=api.DD_PREC_F64, sap=sap, ref_ln=ref_ln),
+            parameters=sap, bicgstab_global_solves=iterations.get("global")))
     if args.compare_config:
         # mixed versus plain FP64 on smaller workloads (the FP64 path at the
         # full volume would hold the GPU for minutes per step)
-        line["mixed_vs_fp64"] = {name: compare_precisions(args, CONFIGS[name], dev, stream, rank)
-                                 for name in args.compare_config.split(",") if name}
+        supplement(line, "mixed_vs_fp64", lambda: {name: compare_precisions(args, CONFIGS[name], dev, stream, rank)
+                                                   for name in args.compare_config.split(",") if name})
     if not args.no_batched_filter:
-        line["batched_filter"] = measure_batched_filter(dev, stream)
+        supplement(line, "batched_filter", lambda: measure_batched_filter(dev, stream))
     if not args.no_recursive:
-        line["recursive"] = measure_recursive(cfg, dev, stream)
+        supplement(line, "recursive", lambda: measure_recursive(cfg, dev, stream))
     if not args.no_lu:
-        line["exact_lu"] = measure_lu(dev, stream)
+        supplement(line, "exact_lu", lambda: measure_lu(dev, stream))
     if rank == 0 and not args.no_cpu_baseline:
         c2 = CONFIGS["c2"]
         r = oracle_estimate_rate(c2)
@@ -612,7 +627,7 @@ def run_gpu(args, cfg):
                       f"every solve to relative residual 1e-10; proposal made before timing): factor 0 alone on "
                       f"one thread {r['seconds_one_factor']:.1f} s; all {r['factors']} factors, one process per "
                       f"core on {r['cores']} cores, {r['seconds_all_factors']:.1f} s",
-            "gpu_same_workload": line.get("mixed_vs_fp64", {}).get("c2"),
+            "gpu_same_workload": (line.get("mixed_vs_fp64") or {}).get("c2"),
             "c5_projection": {
                 "value": 1.0 / (max(D_apps_per_est, 1e-9) * per_app), "unit": "estimates/s", "cores": 1,
                 "projected": True,
@@ -624,6 +639,18 @@ def run_gpu(args, cfg):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def supplement(line, key, fn):
+    """line[key] = fn(); an exception (a CUDA or library error of that one
+    measurement) is printed to stderr and recorded as line[key] = {"error":
+    ...}, so that the headline numbers measured before it are still printed."""
+    import traceback
+    try:
+        line[key] = fn()
+    except Exception as e:  # noqa: BLE001 - recorded, not hidden
+        traceback.print_exc()
+        line[key] = {"error": f"{type(e).__name__}: {e}"}
 
 
 def measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune, krylov=None, outer=None, sap=None,

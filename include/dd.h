@@ -307,10 +307,12 @@ int dd_relative_gauge_fix(dd_t h, const void* U, void* U_new, int sweeps, double
  * lattices (e.g. 4^4, 6^4 and 8^4).  Per handle k the results are those of
  * dd_block_filter(hs[k], U_old[k], U_new[k], colour_mask, DD_FILTER_STOCHASTIC,
  * n, seed, ctr, ln_b[k], accept[k]) (same random streams, same arithmetic).
- * All handles must share one stream and block precision; every launch of
- * the call goes to the first handle's stream, so a CUDA graph recorded on
- * hs[0] (dd_graph_begin) holds the whole batch (the descriptor tables must
- * then equal those of the last eager call with the same ws).  hs, U_old,
+ * All handles must have been created on one stream and share the block
+ * precision; every launch of the call goes to the first handle's stream, so
+ * a CUDA graph recorded on hs[0] (dd_graph_begin; no other handle of the
+ * batch may be recording) holds the whole batch (the descriptor tables must
+ * then equal those of the last eager call with the same ws).
+ * DD_ERR_INVALID_ARG otherwise.  hs, U_old,
  * U_new, ln_b and accept are host arrays of nh pointers (the pointers
  * themselves device memory).  ws: device memory of at least
  * dd_block_filter_batch_workspace(nh, hs, n) bytes, 256-byte aligned, owned
@@ -338,12 +340,17 @@ int dd_gauge_update(dd_t h, void* U, int colour_mask, double beta, int n_hb, int
 int dd_global_accept(dd_t h, void* U, const void* U_old, const double* ln_r, int n, uint64_t seed, uint64_t ctr,
                      uint8_t* accept, double* ln_margin);
 
-/* Exact check path (Sec. 3: block determinants "computed exactly by ...
- * LU-decomposition"): dense FP64 LU with partial pivoting of D (which = 0,
+/* Exact check path (Sec. 3: the block determinants are obtained exactly from
+ * an LU factorisation): dense FP64 LU with partial pivoting of D (which = 0,
  * out[0] = ln|det D|, lattices of at most 512 sites) or of every block
  * operator D_b (which = 1, out[b] = ln|det D_b|, blocks of at most 256 sites),
  * or of the domain Schur complement Dhat (which = 2, out[0] = ln|det Dhat|,
- * at most 512 sites).  out: device doubles. */
+ * at most 512 sites).  out: device doubles.  Blocked LU (panels of 32
+ * columns); panels of matrices above 384 rows are factorised by one
+ * cooperative launch whose thread blocks meet at a bounded grid barrier.
+ * Device status (dd_status): DD_ERR_NUMERIC for a zero pivot,
+ * DD_ERR_TIMEOUT if a grid barrier gave up waiting (the results are then
+ * invalid). */
 int dd_logdet_exact(dd_t h, const void* U, int which, double* out);
 
 /* Mean plaquette <Re tr U_P / 3> (device, 1 double). */

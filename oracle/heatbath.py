@@ -1,8 +1,8 @@
 """Wilson plaquette action, heat-bath and over-relaxation on active links (oracle).
 
-Paper Eq. 4step step 0 ("update active links on all blocks, e.g. heat-bath /
-over-relaxation") with P_0 ~ exp(-S_G) and the Wilson plaquette action
-(Sec. 5):  S_G = beta * sum_P (1 - Re tr U_P / 3).
+Paper Eq. 4step step 0 (the proposal: the active links of every block are
+updated by a pure-gauge algorithm such as heat-bath and over-relaxation),
+with P_0 ~ exp(-S_G) and the Wilson plaquette action (Sec. 5):  S_G = beta * sum_P (1 - Re tr U_P / 3).
 
 The heat-bath is Cabibbo-Marinari: for each link the SU(2) subgroups
 (0,1), (1,2), (0,2) are visited in that order (the order is a reading; the

@@ -751,13 +751,18 @@ BatchPlan batch_plan(int nh, dd_handle* const* hs, int n) {
     p.total = off;
     return p;
 }
+// the stream a handle was created with (while it records a graph, its work
+// goes to the capture stream instead)
+cudaStream_t caller_stream(const dd_handle* h) { return h->capturing ? h->user_stream : h->stream; }
+
 int batch_check(int nh, dd_handle* const* hs, int n) {
     if (nh < 1 || !hs) return DD_ERR_INVALID_ARG;
     for (int k = 0; k < nh; ++k) {
         if (!hs[k] || !hs[k]->ws || !hs[k]->feat_estimate || hs[k]->has_sub) return DD_ERR_INVALID_ARG;
         if (n < 1 || n > hs[k]->prm.max_rhs) return DD_ERR_INVALID_ARG;
-        if (hs[k]->stream != hs[0]->stream || hs[k]->prm.block_prec != hs[0]->prm.block_prec)
+        if (caller_stream(hs[k]) != caller_stream(hs[0]) || hs[k]->prm.block_prec != hs[0]->prm.block_prec)
             return DD_ERR_INVALID_ARG;
+        if (k > 0 && hs[k]->capturing) return DD_ERR_INVALID_ARG;  // only the first handle may record
     }
     return DD_OK;
 }

@@ -5,12 +5,14 @@
 //   D_b    every Dirichlet block operator (batched),
 //   Dhat   the domain Schur complement 1 - A^{-1} B E^{-1} C, assembled
 //          explicitly with block-diagonal solves and a dense product.
-// Right-looking elimination, one pivot launch and one trailing-update launch
-// per column (batched over matrices); matrices are column-major.  FP64
-// arithmetic on the FP64 FMA pipe: on GB300 the FP64 tensor-core instruction
-// (mma.sync m8n8k4) measures 1.10 TFLOP/s against 1.25 for FP64 FMA
-// (dd_alu_peaks), so the trailing update gains nothing from it.
+// Blocked right-looking elimination with panels of 32 columns (batched over
+// matrices; matrices are column-major): per panel one panel launch, one
+// swap-and-triangular-solve launch and one GEMM launch for the trailing
+// matrix.  FP64 arithmetic on the FP64 FMA pipe: on GB300 the FP64
+// tensor-core instruction (mma.sync m8n8k4) measures 1.10 TFLOP/s against
+// 1.25 for FP64 FMA (dd_alu_peaks), so the trailing GEMM stays on FMA.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <vector>
 
@@ -92,78 +94,232 @@ __global__ void zero_kernel(long long n, double2* p) {
 }
 
 // ------------------------------------------------------- LU elimination
-// Step k on a batch of n x ncols matrices (column-major, leading dim n):
-// pivot search in column k (rows k..n-1), row swap over all columns,
-// ln|pivot| accumulated, multipliers stored below the diagonal.
-__global__ void lu_pivot_kernel(double2* M, long long mstride, int n, int ncols, int k, double* logdet,
-                                int* status) {
-    __shared__ double sv[256];
-    __shared__ int si[256];
-    double2* A = M + (long long)blockIdx.x * mstride;
-    double best = -1.0;
-    int bi = k;
-    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-        double2 v = A[i + (long long)k * n];
-        double m = v.x * v.x + v.y * v.y;
-        if (m > best) {
-            best = m;
-            bi = i;
-        }
+// Blocked right-looking LU with partial pivoting, batched over matrices
+// (column-major, leading dimension n, n x ncols with ncols >= n: columns
+// beyond n are right-hand sides that receive the same row operations).  For
+// every panel of LU_NB columns k0..k0+nbe-1:
+//   1. the panel (rows k0..n-1) is factorised column by column: pivot search
+//      (largest |a|, lowest row on ties), row swap inside the panel,
+//      multipliers, rank-1 update of the panel's remaining columns;
+//   2. the columns right of the panel take the panel's row swaps, and their
+//      panel rows become U12 = L11^{-1} A12 (unit lower triangular solve);
+//   3. A22 -= L21 U12, a complex FP64 GEMM (zgemm_tile_kernel).
+// Panels of matrices up to LU_SINGLE_MAX rows live in the shared memory of
+// one thread block.  Larger panels are split into slices of LU_PR rows over
+// the thread blocks of one cooperative launch, which meet once per column at
+// a grid barrier: every block publishes its best pivot candidate (value,
+// row, and the row's panel entries) and the owner of row k publishes that
+// row; after the barrier every block picks the same winner and swaps inside
+// its own slice.  The published buffers alternate between two copies by
+// column parity, so a block never overwrites a copy that a slower block may
+// still read.
+constexpr int LU_NB = 32;
+constexpr int LU_PR = 32;
+constexpr int LU_SINGLE_MAX = 384;
+constexpr int LU_THREADS = 256;
+constexpr int LU_LD = LU_NB + 1;  // padded row of a panel slice in shared memory
+constexpr long long LU_SPIN_LIMIT = 1ll << 22;
+
+struct LuAux {
+    int* ipiv;      // [batch][n]: row swapped with row k at step k
+    double* part;   // [2][chunk][ctas][2]: (|a|^2, row) of each block's candidate
+    double2* prow;  // [2][chunk][ctas][LU_NB]: that candidate's panel row
+    double2* rowk;  // [2][chunk][LU_NB]: panel row k before the swap
+    unsigned* bar;  // arrivals at the grid barrier (zeroed before each launch)
+};
+
+DD_DEV void argmax_merge(double& v, int& i, double ov, int oi) {
+    if (ov > v || (ov == v && oi < i)) {
+        v = ov;
+        i = oi;
     }
-    sv[threadIdx.x] = best;
-    si[threadIdx.x] = bi;
+}
+
+// grid barrier of a cooperative launch; false (and DD_ERR_TIMEOUT in the
+// status word) when the other blocks did not arrive within LU_SPIN_LIMIT polls
+DD_DEV bool lu_grid_barrier(unsigned* bar, unsigned target, int* status, int* s_ok) {
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            double o = sv[threadIdx.x + s];
-            int oi = si[threadIdx.x + s];
-            if (o > sv[threadIdx.x] || (o == sv[threadIdx.x] && oi < si[threadIdx.x])) {
-                sv[threadIdx.x] = o;
-                si[threadIdx.x] = oi;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        int ok = 1;
+        for (long long spin = 0;; ++spin) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+            if (v >= target) break;
+            if (spin >= LU_SPIN_LIMIT) {
+                ok = 0;
+                raise_status(status, DD_ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// panel factorisation, step 1; grid (ctas, matrices), thread block b holds
+// rows k0 + b*rows_per .. of the panel
+template <bool MULTI>
+__global__ void __launch_bounds__(LU_THREADS) lu_panel_kernel(double2* M, long long mstride, int n, int k0, int nbe,
+                                                              int rows_per, LuAux aux, double* logdet, int* status) {
+    extern __shared__ double2 pan[];  // [rows_per][LU_LD]
+    __shared__ double2 urow[LU_NB];
+    __shared__ double sv[LU_THREADS / 32];
+    __shared__ int si[LU_THREADS / 32];
+    __shared__ int s_p, s_bc, s_ok;
+    const int m = blockIdx.y, c = blockIdx.x, ctas = gridDim.x, tid = threadIdx.x;
+    double2* A = M + (long long)m * mstride;
+    const int r0 = k0 + c * rows_per;
+    const int nr = min(rows_per, n - r0);
+    for (int e = tid; e < nr * nbe; e += blockDim.x) {
+        const int r = e % nr, j = e / nr;
+        pan[r * LU_LD + j] = A[(r0 + r) + (long long)(k0 + j) * n];
+    }
+    __syncthreads();
+    for (int j = 0; j < nbe; ++j) {
+        const int k = k0 + j;
+        double best = -1.0;
+        int bi = INT_MAX;
+        for (int r = max(0, k - r0) + tid; r < nr; r += blockDim.x) {
+            const double2 v = pan[r * LU_LD + j];
+            argmax_merge(best, bi, v.x * v.x + v.y * v.y, r0 + r);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            argmax_merge(best, bi, ov, oi);
+        }
+        if ((tid & 31) == 0) {
+            sv[tid >> 5] = best;
+            si[tid >> 5] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) argmax_merge(best, bi, sv[w], si[w]);
+            sv[0] = best;
+            si[0] = bi;
+        }
+        __syncthreads();
+        const bool own_k = k >= r0 && k < r0 + nr;
+        if (MULTI) {
+            const int buf = j & 1;
+            const long long mc = (long long)buf * gridDim.y + m;
+            if (tid == 0) {
+                aux.part[(mc * ctas + c) * 2] = sv[0];
+                aux.part[(mc * ctas + c) * 2 + 1] = (double)si[0];
+            }
+            if (tid < nbe && sv[0] >= 0.0) aux.prow[(mc * ctas + c) * LU_NB + tid] = pan[(si[0] - r0) * LU_LD + tid];
+            if (tid < nbe && own_k) aux.rowk[mc * LU_NB + tid] = pan[(k - r0) * LU_LD + tid];
+            if (!lu_grid_barrier(aux.bar, (unsigned)(j + 1) * ctas * gridDim.y, status, &s_ok)) return;
+            if (tid == 0) {
+                double bv = -1.0;
+                int bidx = INT_MAX, bc = 0;
+                for (int q = 0; q < ctas; ++q) {
+                    const double v = __ldcg(aux.part + (mc * ctas + q) * 2);
+                    const int ix = (int)__ldcg(aux.part + (mc * ctas + q) * 2 + 1);
+                    if (v > bv || (v == bv && ix < bidx)) {
+                        bv = v;
+                        bidx = ix;
+                        bc = q;
+                    }
+                }
+                s_p = bidx;
+                s_bc = bc;
+            }
+            __syncthreads();
+            const int p = s_p;
+            if (tid < nbe) {
+                const double2 u = __ldcg(aux.prow + (mc * ctas + s_bc) * LU_NB + tid);
+                const double2 old = __ldcg(aux.rowk + mc * LU_NB + tid);
+                urow[tid] = u;
+                if (own_k) pan[(k - r0) * LU_LD + tid] = u;
+                if (p != k && p >= r0 && p < r0 + nr) pan[(p - r0) * LU_LD + tid] = old;
+            }
+        } else {
+            if (tid == 0) s_p = si[0];
+            __syncthreads();
+            const int p = s_p;
+            if (tid < nbe) {
+                const double2 u = pan[(p - r0) * LU_LD + tid], old = pan[(k - r0) * LU_LD + tid];
+                urow[tid] = u;
+                pan[(k - r0) * LU_LD + tid] = u;
+                pan[(p - r0) * LU_LD + tid] = old;
+            }
+        }
+        __syncthreads();
+        const double2 piv = urow[j];
+        const double pm = piv.x * piv.x + piv.y * piv.y;
+        if (tid == 0 && own_k) {
+            aux.ipiv[(long long)m * n + k] = s_p;
+            if (!(pm > 0.0)) raise_status(status, DD_ERR_NUMERIC);
+            logdet[m] += 0.5 * log(pm);
+        }
+        if (pm > 0.0) {
+            const cpx<double> inv = mk<double>(piv.x / pm, -piv.y / pm);
+            for (int r = max(0, k + 1 - r0) + tid; r < nr; r += blockDim.x) {
+                const double2 a = pan[r * LU_LD + j];
+                const cpx<double> l = cmul(mk<double>(a.x, a.y), inv);
+                pan[r * LU_LD + j] = make_double2(l.x, l.y);
+                for (int jj = j + 1; jj < nbe; ++jj) {
+                    const double2 u = urow[jj];
+                    double2& t = pan[r * LU_LD + jj];
+                    t.x -= l.x * u.x - l.y * u.y;
+                    t.y -= l.x * u.y + l.y * u.x;
+                }
             }
         }
         __syncthreads();
     }
-    const int p = si[0];
-    if (p != k)
-        for (int j = threadIdx.x; j < ncols; j += blockDim.x) {
-            double2 t = A[k + (long long)j * n];
-            A[k + (long long)j * n] = A[p + (long long)j * n];
-            A[p + (long long)j * n] = t;
-        }
-    __syncthreads();
-    const double2 piv = A[k + (long long)k * n];
-    const double pm = piv.x * piv.x + piv.y * piv.y;
-    if (threadIdx.x == 0) {
-        if (!(pm > 0.0)) raise_status(status, DD_ERR_NUMERIC);
-        logdet[blockIdx.x] += 0.5 * log(pm);
-    }
-    if (pm > 0.0) {
-        const cpx<double> inv = mk<double>(piv.x / pm, -piv.y / pm);
-        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
-            double2 v = A[i + (long long)k * n];
-            cpx<double> w = cmul(mk<double>(v.x, v.y), inv);
-            A[i + (long long)k * n] = make_double2(w.x, w.y);
-        }
+    for (int e = tid; e < nr * nbe; e += blockDim.x) {
+        const int r = e % nr, j = e / nr;
+        A[(r0 + r) + (long long)(k0 + j) * n] = pan[r * LU_LD + j];
     }
 }
 
-// trailing update a_ij -= l_ik u_kj for i > k, k < j < ncols
-__global__ void lu_update_kernel(double2* M, long long mstride, int n, int ncols, int k) {
-    __shared__ double2 lcol[16];
-    __shared__ double2 urow[16];
-    double2* A = M + (long long)blockIdx.z * mstride;
-    const int i = k + 1 + blockIdx.y * 16 + threadIdx.y;
-    const int j = k + 1 + blockIdx.x * 16 + threadIdx.x;
-    if (threadIdx.x == 0) lcol[threadIdx.y] = (i < n) ? A[i + (long long)k * n] : make_double2(0, 0);
-    if (threadIdx.y == 0) urow[threadIdx.x] = (j < ncols) ? A[k + (long long)j * n] : make_double2(0, 0);
-    __syncthreads();
-    if (i < n && j < ncols) {
-        double2 l = lcol[threadIdx.y], u = urow[threadIdx.x];
-        double2& a = A[i + (long long)j * n];
-        a.x -= l.x * u.x - l.y * u.y;
-        a.y -= l.x * u.y + l.y * u.x;
+// step 2: one thread per column right of the panel: the panel's row swaps in
+// order, then forward substitution with the unit lower triangle L11
+__global__ void __launch_bounds__(64) lu_swap_trsm_kernel(double2* M, long long mstride, int n, int ncols, int k0,
+                                                          int nbe, const int* ipiv) {
+    __shared__ double2 L[LU_NB][LU_LD];
+    const int m = blockIdx.y;
+    double2* A = M + (long long)m * mstride;
+    for (int e = threadIdx.x; e < nbe * nbe; e += blockDim.x) {
+        const int r = e % nbe, cc = e / nbe;
+        L[r][cc] = A[(k0 + r) + (long long)(k0 + cc) * n];
     }
+    __syncthreads();
+    const int j = k0 + nbe + blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ncols) return;
+    double2* col = A + (long long)j * n;
+    const int* piv = ipiv + (long long)m * n;
+    for (int t = 0; t < nbe; ++t) {
+        const int k = k0 + t, p = piv[k];
+        if (p != k) {
+            const double2 a = col[k];
+            col[k] = col[p];
+            col[p] = a;
+        }
+    }
+    double2 x[LU_NB];
+#pragma unroll
+    for (int r = 0; r < LU_NB; ++r) x[r] = r < nbe ? col[k0 + r] : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int r = 1; r < LU_NB; ++r) {
+#pragma unroll
+        for (int cc = 0; cc < r; ++cc) {
+            const double2 l = L[r][cc];
+            x[r].x -= l.x * x[cc].x - l.y * x[cc].y;
+            x[r].y -= l.x * x[cc].y + l.y * x[cc].x;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < LU_NB; ++r)
+        if (r < nbe) col[k0 + r] = x[r];
 }
 
 // back substitution on the right-hand-side columns nelim..ncols-1 of an
@@ -191,30 +347,74 @@ __global__ void back_update_kernel(double2* M, long long mstride, int n, int nco
     a.y -= u.x * x.y + u.y * x.x;
 }
 
-// C (m x n, ld ldc) = alpha * A (m x kk, lda) * B (kk x n, ldb) + beta * C, complex FP64
-__global__ void zgemm_kernel(int m, int nn, int kk, const double2* A, int lda, const double2* B, int ldb, double2* C,
-                             int ldc, double alpha, double beta) {
-    __shared__ double2 As[16][17];
-    __shared__ double2 Bs[16][17];
-    int r = blockIdx.y * 16 + threadIdx.y, c = blockIdx.x * 16 + threadIdx.x;
-    double sr = 0, si = 0;
-    for (int t = 0; t < kk; t += 16) {
-        As[threadIdx.y][threadIdx.x] = (r < m && t + threadIdx.x < kk) ? A[r + (long long)(t + threadIdx.x) * lda]
-                                                                        : make_double2(0, 0);
-        Bs[threadIdx.y][threadIdx.x] = (c < nn && t + threadIdx.y < kk) ? B[(t + threadIdx.y) + (long long)c * ldb]
-                                                                         : make_double2(0, 0);
+// C = beta C + alpha A B for complex FP64 column-major matrices (m x kk times
+// kk x nn), batched over blockIdx.z with the strides sA, sB, sC: a 64 x 64
+// tile of C per thread block of 256 threads, 4 x 4 elements per thread (rows
+// tr + 16 i, columns tc + 16 j), A and B staged through shared memory in
+// slices of 16 along k.  Every complex product is four FP64 FMAs; with beta
+// == 0 C is not read.
+constexpr int ZG_T = 64, ZG_K = 16;
+__global__ void __launch_bounds__(256) zgemm_tile_kernel(int m, int nn, int kk, const double2* A, int lda, long long sA,
+                                                         const double2* B, int ldb, long long sB, double2* C, int ldc,
+                                                         long long sC, double alpha, double beta) {
+    __shared__ double2 As[ZG_K][ZG_T + 1];
+    __shared__ double2 Bs[ZG_K][ZG_T + 1];
+    const long long z = blockIdx.z;
+    A += z * sA;
+    B += z * sB;
+    C += z * sC;
+    const int r0 = blockIdx.y * ZG_T, c0 = blockIdx.x * ZG_T;
+    const int t = threadIdx.x, tr = t & 15, tc = t >> 4;
+    double2 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+    for (int k0 = 0; k0 < kk; k0 += ZG_K) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = t + 256 * q, row = e & 63, kx = e >> 6;
+            const int gr = r0 + row, gk = k0 + kx;
+            As[kx][row] = (gr < m && gk < kk) ? A[gr + (long long)gk * lda] : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = t + 256 * q, kx = e & 15, col = e >> 4;
+            const int gc = c0 + col, gk = k0 + kx;
+            Bs[kx][col] = (gc < nn && gk < kk) ? B[gk + (long long)gc * ldb] : make_double2(0.0, 0.0);
+        }
         __syncthreads();
-        for (int q = 0; q < 16; ++q) {
-            double2 a = As[threadIdx.y][q], b = Bs[q][threadIdx.x];
-            sr += a.x * b.x - a.y * b.y;
-            si += a.x * b.y + a.y * b.x;
+#pragma unroll
+        for (int kx = 0; kx < ZG_K; ++kx) {
+            double2 a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                a[i] = As[kx][tr + 16 * i];
+                b[i] = Bs[kx][tc + 16 * i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc[i][j].x = fma(a[i].x, b[j].x, acc[i][j].x);
+                    acc[i][j].x = fma(-a[i].y, b[j].y, acc[i][j].x);
+                    acc[i][j].y = fma(a[i].x, b[j].y, acc[i][j].y);
+                    acc[i][j].y = fma(a[i].y, b[j].x, acc[i][j].y);
+                }
         }
         __syncthreads();
     }
-    if (r < m && c < nn) {
-        double2& o = C[r + (long long)c * ldc];
-        o = make_double2(alpha * sr + beta * o.x, alpha * si + beta * o.y);
-    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = r0 + tr + 16 * i, cc = c0 + tc + 16 * j;
+            if (r < m && cc < nn) {
+                double2& o = C[r + (long long)cc * ldc];
+                const double2 old = beta != 0.0 ? o : make_double2(0.0, 0.0);
+                o = make_double2(alpha * acc[i][j].x + beta * old.x, alpha * acc[i][j].y + beta * old.y);
+            }
+        }
 }
 
 // copy a sub-matrix (rows r0.., cols c0.., size rm x cm) of S (ld lds) into D (ld ldd) at (0, dc)
@@ -236,18 +436,94 @@ __global__ void zero_doubles_kernel(int n, double* p) {
 
 }  // namespace
 
+// scratch of the blocked LU, behind the matrices of the exact path
+static char* lu_scratch(dd_handle* h, size_t* cap) {
+    const size_t n = (size_t)12 * h->g.V, nb12 = (size_t)12 * h->g.bsites;
+    const size_t off = h->g.V <= 512 ? 2 * n * n * sizeof(double2) : (size_t)h->g.nblocks * nb12 * nb12 * sizeof(double2);
+    *cap = h->lu_bytes > off ? h->lu_bytes - off : 0;
+    return (char*)h->d_lu + off;
+}
+
 // LU of `batch` n x ncols matrices, eliminating the first n columns; logdet
 // receives sum_k ln|u_kk| per matrix; with back = true the right-hand-side
 // columns are overwritten by the solutions.
 static int lu_batched(dd_handle* h, double2* M, long long mstride, int batch, int n, int ncols, double* logdet,
                       bool back) {
+    size_t cap = 0;
+    char* scr = lu_scratch(h, &cap);
+    const bool single = n <= LU_SINGLE_MAX;
+    const int ctas0 = single ? 1 : grid_for(n, LU_PR);
+    const size_t multi_smem = (size_t)LU_PR * LU_LD * sizeof(double2);
+    int chunk = batch;
+    if (single) {
+        const size_t smem = (size_t)n * LU_LD * sizeof(double2);
+        cudaError_t e = cudaFuncSetAttribute(lu_panel_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return dd_cuda_check(h, e, "lu_panel_kernel shared memory");
+    } else {
+        // one cooperative launch holds every thread block of its matrices
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_panel_kernel<true>, LU_THREADS, multi_smem);
+        if (e != cudaSuccess) return dd_cuda_check(h, e, "lu_panel_kernel occupancy");
+        const long long resident = (long long)per_sm * std::max(1, h->num_sms);
+        if (resident < ctas0) return dd_fail(h, DD_ERR_UNSUPPORTED, "dense LU: a panel needs more thread blocks than fit on the GPU");
+        chunk = (int)std::min<long long>(batch, resident / ctas0);
+    }
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t o = 0;
+    LuAux aux{};
+    aux.ipiv = (int*)(scr + o);
+    o += up((size_t)batch * n * sizeof(int));
+    if (!single) {
+        aux.part = (double*)(scr + o);
+        o += up((size_t)2 * chunk * ctas0 * 2 * sizeof(double));
+        aux.prow = (double2*)(scr + o);
+        o += up((size_t)2 * chunk * ctas0 * LU_NB * sizeof(double2));
+        aux.rowk = (double2*)(scr + o);
+        o += up((size_t)2 * chunk * LU_NB * sizeof(double2));
+        aux.bar = (unsigned*)(scr + o);
+        o += 256;
+    }
+    if (o > cap) return dd_fail(h, DD_ERR_UNSUPPORTED, "dense LU: no room for the pivot scratch");
     DD_KLAUNCH(h, zero_doubles_kernel<<<grid_for(batch, 64), 64, 0, h->stream>>>(batch, logdet));
-    for (int k = 0; k < n; ++k) {
-        DD_KLAUNCH(h, lu_pivot_kernel<<<batch, 256, 0, h->stream>>>(M, mstride, n, ncols, k, logdet, h->d_status));
-        int rows = n - k - 1, cols = ncols - k - 1;
-        if (rows > 0 && cols > 0) {
-            dim3 grid((cols + 15) / 16, (rows + 15) / 16, batch);
-            DD_KLAUNCH(h, lu_update_kernel<<<grid, dim3(16, 16), 0, h->stream>>>(M, mstride, n, ncols, k));
+    for (int k0 = 0; k0 < n; k0 += LU_NB) {
+        const int nbe = std::min(LU_NB, n - k0);
+        if (single) {
+            const int rows = n - k0;
+            const size_t smem = (size_t)rows * LU_LD * sizeof(double2);
+            DD_KLAUNCH(h, lu_panel_kernel<false><<<dim3(1, batch), LU_THREADS, smem, h->stream>>>(
+                              M, mstride, n, k0, nbe, rows, aux, logdet, h->d_status));
+        } else {
+            const int ctas = grid_for(n - k0, LU_PR);
+            for (int m0 = 0; m0 < batch; m0 += chunk) {
+                const int mb = std::min(chunk, batch - m0);
+                cudaError_t e = cudaMemsetAsync(aux.bar, 0, sizeof(unsigned), h->stream);
+                if (e != cudaSuccess) return dd_cuda_check(h, e, "lu barrier reset");
+                double2* Mc = M + (long long)m0 * mstride;
+                double* ldc = logdet + m0;
+                LuAux ac = aux;
+                ac.ipiv = aux.ipiv + (long long)m0 * n;
+                int nn = n, kk0 = k0, nb_ = nbe, rp = LU_PR;
+                long long ms = mstride;
+                int* st = h->d_status;
+                void* args[] = {&Mc, &ms, &nn, &kk0, &nb_, &rp, &ac, &ldc, &st};
+                e = cudaLaunchCooperativeKernel((const void*)lu_panel_kernel<true>, dim3(ctas, mb), dim3(LU_THREADS), args,
+                                                multi_smem, h->stream);
+                ++h->launches;
+                if (e != cudaSuccess) return dd_cuda_check(h, e, "lu_panel_kernel (cooperative launch)");
+            }
+        }
+        const int right = ncols - k0 - nbe;
+        if (right > 0) {
+            DD_KLAUNCH(h, lu_swap_trsm_kernel<<<dim3(grid_for(right, 64), batch), 64, 0, h->stream>>>(
+                              M, mstride, n, ncols, k0, nbe, aux.ipiv));
+            const int below = n - k0 - nbe;
+            if (below > 0) {
+                dim3 g(grid_for(right, ZG_T), grid_for(below, ZG_T), batch);
+                DD_KLAUNCH(h, zgemm_tile_kernel<<<g, 256, 0, h->stream>>>(
+                                  below, right, nbe, M + (k0 + nbe) + (long long)k0 * n, n, mstride,
+                                  M + k0 + (long long)(k0 + nbe) * n, n, mstride,
+                                  M + (k0 + nbe) + (long long)(k0 + nbe) * n, n, mstride, -1.0, 1.0));
+            }
         }
     }
     if (back && ncols > n) {
@@ -316,10 +592,10 @@ static int logdet_schur(dd_handle* h, const double* U, double* out) {
     if (rc) return rc;
     // Y = B X: B = D[0:nh, nh:n]; X rows of white block b live in aug b, columns nb12..
     for (int b = 0; b < nbk; ++b) {
-        dim3 g(grid_for(nh, 16), grid_for(nh, 16));
-        DD_KLAUNCH(h, zgemm_kernel<<<g, b16, 0, h->stream>>>(nh, nh, nb12, D + (long long)(nh + b * nb12) * n, n,
-                                                           aug + b * as + (long long)nb12 * nb12, nb12, Y, nh, 1.0,
-                                                           b == 0 ? 0.0 : 1.0));
+        dim3 g(grid_for(nh, ZG_T), grid_for(nh, ZG_T), 1);
+        DD_KLAUNCH(h, zgemm_tile_kernel<<<g, 256, 0, h->stream>>>(nh, nh, nb12, D + (long long)(nh + b * nb12) * n, n, 0,
+                                                                aug + b * as + (long long)nb12 * nb12, nb12, 0, Y, nh,
+                                                                0, 1.0, b == 0 ? 0.0 : 1.0));
     }
     // Z = A^{-1} Y: per black block [A_b | Y_b]
     for (int b = 0; b < nbk; ++b) {

@@ -78,3 +78,29 @@ def test_block_filter_exact(api, case, cm):
     gacc = host(acc).astype(bool)
     assert np.array_equal(gacc[clear], racc[clear])
     assert np.array_equal(host(Upd), accept.restore_rejected_blocks(Up, U, lat, gacc))
+
+
+def test_logdet_largest_panels(api):
+    """The largest matrices of the exact path: on an 8 x 4^3 lattice (512
+    sites) with 2 x 2^3 blocks, D is 6144 x 6144 and Dhat 3072 x 3072 (panels
+    split over the thread blocks of one cooperative launch), the 16 block
+    operators are 384 x 384 (one thread block per panel at the largest
+    shared-memory panel), and the Schur assembly solves augmented 384 x 3456
+    systems.  Against LAPACK on the oracle's matrices, and Eq. ddfactor."""
+    dims, block = (8, 4, 4, 4), (4, 2, 2, 2)
+    lat = geometry.Lattice(dims, block)
+    U = synthetic.random_gauge(dims, 0.4, 3)
+    h = api.dd_init(dims, block, KAPPA)
+    D = dirac.dense_D(U, lat, KAPPA)
+    gd = float(host(api.dd_logdet_exact(h, dev(U), 0))[0])
+    ref = dirac.logabsdet(D)
+    assert abs(gd - ref) < 1e-9 * abs(ref)
+    gb = host(api.dd_logdet_exact(h, dev(U), 1))
+    for b in range(lat.nblocks):
+        rb = dirac.logabsdet(dirac.dense_dirichlet_block(U, lat, KAPPA, b))
+        assert abs(gb[b] - rb) < 1e-10 * max(1.0, abs(rb))
+    gs = float(host(api.dd_logdet_exact(h, dev(U), 2))[0])
+    rs = dirac.logabsdet(dirac.dense_schur(D, lat))
+    assert abs(gs - rs) < 1e-9 * max(1.0, abs(rs))
+    assert abs(gd - (gb.sum() + gs)) < 1e-9 * abs(gd)
+    assert api.dd_status(h)[0] == 0
