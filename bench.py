@@ -940,8 +940,8 @@ def run_solve(args, cfg):
     krylov = {"cgnr": api.DD_KRYLOV_CGNR, "bicgstab": api.DD_KRYLOV_BICGSTAB, "sap": api.DD_KRYLOV_SAP_GCR}[args.krylov]
     outer = {"f64": api.DD_PREC_F64, "df64": api.DD_PREC_DF64}[args.outer]
     h = api.dd_init(cfg["dims"], cfg["block"], cfg["kappa"], max_rhs=1, inner_prec=prec, tol_global=1e-10,
-                    maxit=40000, features=api.DD_FEAT_SOLVE, device=dev, krylov=krylov, outer_prec=outer,
-                    sap_ncy=args.sap_ncy, sap_nmr=args.sap_nmr, sap_nkv=args.sap_nkv)
+                    tol_inner=args.tol_inner, maxit=40000, features=api.DD_FEAT_SOLVE, device=dev, krylov=krylov,
+                    outer_prec=outer, sap_ncy=args.sap_ncy, sap_nmr=args.sap_nmr, sap_nkv=args.sap_nkv)
     U = torch.from_numpy(synthetic.random_gauge(cfg["dims"], cfg["eps"], cfg["seed"])).to(dev)
     b = torch.from_numpy(synthetic.random_spinor(cfg["dims"], 1)).to(dev)
     x = torch.zeros_like(b)
@@ -956,9 +956,11 @@ def run_solve(args, cfg):
         its += it
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
+    st = api.dd_solver_stats(h, 0)
     out = {"mode": "solve", "config": args.config, "prec": args.prec, "outer": args.outer,
-           "seconds_per_solve": t / args.steps,
-           "inner_iterations_per_solve": its / args.steps, "relres": res[0]}
+           "tol_inner": args.tol_inner, "seconds_per_solve": t / args.steps,
+           "inner_iterations_per_solve": its / args.steps, "relres": res[0],
+           "outer_cycles_per_solve": st["outer_cycles"] / max(1, st["solves"])}
     for kind in (0, 1, 2, 3):
         ms, cnt, sites = api.dd_kernel_timer(h, 2, kind)
         if cnt:

@@ -120,19 +120,44 @@ constexpr int LU_THREADS = 256;
 constexpr int LU_LD = LU_NB + 1;  // padded row of a panel slice in shared memory
 constexpr long long LU_SPIN_LIMIT = 1ll << 22;
 
+DD_DEV void argmax_merge(double& v, int& i, double ov, int oi) {
+    if (ov > v || (ov == v && oi < i)) {
+        v = ov;
+        i = oi;
+    }
+}
+
 struct LuAux {
     int* ipiv;      // [batch][n]: row swapped with row k at step k
     double* part;   // [2][chunk][ctas][2]: (|a|^2, row) of each block's candidate
     double2* prow;  // [2][chunk][ctas][LU_NB]: that candidate's panel row
     double2* rowk;  // [2][chunk][LU_NB]: panel row k before the swap
     unsigned* bar;  // arrivals at the grid barrier (zeroed before each launch)
+    int* perm;      // [batch][4 LU_NB + 1]: the panel's row swaps as one permutation
+                    // (destination rows, source rows, count)
 };
+static_assert(LU_PR >= LU_NB, "the first thread block of a panel must own all its pivot rows");
 
-DD_DEV void argmax_merge(double& v, int& i, double ov, int oi) {
-    if (ov > v || (ov == v && oi < i)) {
-        v = ov;
-        i = oi;
+// (value, row) pair of the largest value, lowest row on ties, over the
+// thread block; the result is in sv[0], si[0] for every thread
+DD_DEV void block_argmax(double best, int bi, double* sv, int* si) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        argmax_merge(best, bi, ov, oi);
     }
+    if ((threadIdx.x & 31) == 0) {
+        sv[threadIdx.x >> 5] = best;
+        si[threadIdx.x >> 5] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) argmax_merge(best, bi, sv[w], si[w]);
+        sv[0] = best;
+        si[0] = bi;
+    }
+    __syncthreads();
 }
 
 // grid barrier of a cooperative launch; false (and DD_ERR_TIMEOUT in the
@@ -188,23 +213,7 @@ __global__ void __launch_bounds__(LU_THREADS) lu_panel_kernel(double2* M, long l
             const double2 v = pan[r * LU_LD + j];
             argmax_merge(best, bi, v.x * v.x + v.y * v.y, r0 + r);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            argmax_merge(best, bi, ov, oi);
-        }
-        if ((tid & 31) == 0) {
-            sv[tid >> 5] = best;
-            si[tid >> 5] = bi;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) argmax_merge(best, bi, sv[w], si[w]);
-            sv[0] = best;
-            si[0] = bi;
-        }
-        __syncthreads();
+        block_argmax(best, bi, sv, si);
         const bool own_k = k >= r0 && k < r0 + nr;
         if (MULTI) {
             const int buf = j & 1;
@@ -216,20 +225,16 @@ __global__ void __launch_bounds__(LU_THREADS) lu_panel_kernel(double2* M, long l
             if (tid < nbe && sv[0] >= 0.0) aux.prow[(mc * ctas + c) * LU_NB + tid] = pan[(si[0] - r0) * LU_LD + tid];
             if (tid < nbe && own_k) aux.rowk[mc * LU_NB + tid] = pan[(k - r0) * LU_LD + tid];
             if (!lu_grid_barrier(aux.bar, (unsigned)(j + 1) * ctas * gridDim.y, status, &s_ok)) return;
+            // the winner over all thread blocks of this matrix, read in parallel
+            double bv = -1.0;
+            int bidx = INT_MAX;
+            for (int q = tid; q < ctas; q += blockDim.x)
+                argmax_merge(bv, bidx, __ldcg(aux.part + (mc * ctas + q) * 2),
+                             (int)__ldcg(aux.part + (mc * ctas + q) * 2 + 1));
+            block_argmax(bv, bidx, sv, si);
             if (tid == 0) {
-                double bv = -1.0;
-                int bidx = INT_MAX, bc = 0;
-                for (int q = 0; q < ctas; ++q) {
-                    const double v = __ldcg(aux.part + (mc * ctas + q) * 2);
-                    const int ix = (int)__ldcg(aux.part + (mc * ctas + q) * 2 + 1);
-                    if (v > bv || (v == bv && ix < bidx)) {
-                        bv = v;
-                        bidx = ix;
-                        bc = q;
-                    }
-                }
-                s_p = bidx;
-                s_bc = bc;
+                s_p = si[0];
+                s_bc = (si[0] - k0) / rows_per;
             }
             __syncthreads();
             const int p = s_p;
@@ -279,47 +284,80 @@ __global__ void __launch_bounds__(LU_THREADS) lu_panel_kernel(double2* M, long l
         const int r = e % nr, j = e / nr;
         A[(r0 + r) + (long long)(k0 + j) * n] = pan[r * LU_LD + j];
     }
+    // the panel's swaps as one permutation of the rows they touch (the first
+    // thread block owns rows k0.. and wrote their pivots): position i of the
+    // list receives the value that row src[i] held before the panel
+    if (c == 0 && tid == 0) {
+        int rows[2 * LU_NB], src[2 * LU_NB];
+        int nrow = nbe;
+        for (int t = 0; t < nbe; ++t) rows[t] = src[t] = k0 + t;
+        for (int t = 0; t < nbe; ++t) {
+            const int p = aux.ipiv[(long long)m * n + k0 + t];
+            int q = -1;
+            for (int i = 0; i < nrow; ++i)
+                if (rows[i] == p) {
+                    q = i;
+                    break;
+                }
+            if (q < 0) {
+                q = nrow++;
+                rows[q] = src[q] = p;
+            }
+            const int tmp = src[t];
+            src[t] = src[q];
+            src[q] = tmp;
+        }
+        int* pm = aux.perm + (long long)m * (4 * LU_NB + 1);
+        for (int i = 0; i < nrow; ++i) {
+            pm[i] = rows[i];
+            pm[2 * LU_NB + i] = src[i];
+        }
+        pm[4 * LU_NB] = nrow;
+    }
 }
 
-// step 2: one thread per column right of the panel: the panel's row swaps in
-// order, then forward substitution with the unit lower triangle L11
-__global__ void __launch_bounds__(64) lu_swap_trsm_kernel(double2* M, long long mstride, int n, int ncols, int k0,
-                                                          int nbe, const int* ipiv) {
+// step 2: one warp per column right of the panel: the panel's row
+// permutation (all touched rows gathered, then scattered), then forward
+// substitution with the unit lower triangle L11, lane r holding row k0 + r
+constexpr int LU_TRSM_WARPS = 4;
+__global__ void __launch_bounds__(32 * LU_TRSM_WARPS) lu_swap_trsm_kernel(double2* M, long long mstride, int n,
+                                                                         int ncols, int k0, int nbe, const int* perm) {
     __shared__ double2 L[LU_NB][LU_LD];
-    const int m = blockIdx.y;
+    __shared__ int s_dst[2 * LU_NB], s_src[2 * LU_NB];
+    __shared__ int s_np;
+    const int m = blockIdx.y, tid = threadIdx.x, lane = tid & 31;
     double2* A = M + (long long)m * mstride;
-    for (int e = threadIdx.x; e < nbe * nbe; e += blockDim.x) {
+    for (int e = tid; e < nbe * nbe; e += blockDim.x) {
         const int r = e % nbe, cc = e / nbe;
         L[r][cc] = A[(k0 + r) + (long long)(k0 + cc) * n];
     }
+    const int* pm = perm + (long long)m * (4 * LU_NB + 1);
+    if (tid < 2 * LU_NB) {
+        s_dst[tid] = pm[tid];
+        s_src[tid] = pm[2 * LU_NB + tid];
+    }
+    if (tid == 0) s_np = pm[4 * LU_NB];
     __syncthreads();
-    const int j = k0 + nbe + blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= ncols) return;
+    const int j = k0 + nbe + blockIdx.x * LU_TRSM_WARPS + (tid >> 5);
+    if (j >= ncols) return;  // uniform per warp
     double2* col = A + (long long)j * n;
-    const int* piv = ipiv + (long long)m * n;
-    for (int t = 0; t < nbe; ++t) {
-        const int k = k0 + t, p = piv[k];
-        if (p != k) {
-            const double2 a = col[k];
-            col[k] = col[p];
-            col[p] = a;
+    const int np = s_np;
+    const double2 zero = make_double2(0.0, 0.0);
+    const double2 v0 = lane < np ? col[s_src[lane]] : zero;
+    const double2 v1 = lane + 32 < np ? col[s_src[lane + 32]] : zero;
+    __syncwarp();
+    if (lane >= nbe && lane < np) col[s_dst[lane]] = v0;
+    if (lane + 32 < np) col[s_dst[lane + 32]] = v1;
+    double2 x = v0;
+    for (int cc = 0; cc + 1 < nbe; ++cc) {
+        const double xr = __shfl_sync(0xffffffffu, x.x, cc), xi = __shfl_sync(0xffffffffu, x.y, cc);
+        if (lane > cc && lane < nbe) {
+            const double2 l = L[lane][cc];
+            x.x -= l.x * xr - l.y * xi;
+            x.y -= l.x * xi + l.y * xr;
         }
     }
-    double2 x[LU_NB];
-#pragma unroll
-    for (int r = 0; r < LU_NB; ++r) x[r] = r < nbe ? col[k0 + r] : make_double2(0.0, 0.0);
-#pragma unroll
-    for (int r = 1; r < LU_NB; ++r) {
-#pragma unroll
-        for (int cc = 0; cc < r; ++cc) {
-            const double2 l = L[r][cc];
-            x[r].x -= l.x * x[cc].x - l.y * x[cc].y;
-            x[r].y -= l.x * x[cc].y + l.y * x[cc].x;
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < LU_NB; ++r)
-        if (r < nbe) col[k0 + r] = x[r];
+    if (lane < nbe) col[k0 + lane] = x;
 }
 
 // back substitution on the right-hand-side columns nelim..ncols-1 of an
@@ -473,6 +511,8 @@ static int lu_batched(dd_handle* h, double2* M, long long mstride, int batch, in
     LuAux aux{};
     aux.ipiv = (int*)(scr + o);
     o += up((size_t)batch * n * sizeof(int));
+    aux.perm = (int*)(scr + o);
+    o += up((size_t)batch * (4 * LU_NB + 1) * sizeof(int));
     if (!single) {
         aux.part = (double*)(scr + o);
         o += up((size_t)2 * chunk * ctas0 * 2 * sizeof(double));
@@ -502,6 +542,7 @@ static int lu_batched(dd_handle* h, double2* M, long long mstride, int batch, in
                 double* ldc = logdet + m0;
                 LuAux ac = aux;
                 ac.ipiv = aux.ipiv + (long long)m0 * n;
+                ac.perm = aux.perm + (long long)m0 * (4 * LU_NB + 1);
                 int nn = n, kk0 = k0, nb_ = nbe, rp = LU_PR;
                 long long ms = mstride;
                 int* st = h->d_status;
@@ -514,8 +555,8 @@ static int lu_batched(dd_handle* h, double2* M, long long mstride, int batch, in
         }
         const int right = ncols - k0 - nbe;
         if (right > 0) {
-            DD_KLAUNCH(h, lu_swap_trsm_kernel<<<dim3(grid_for(right, 64), batch), 64, 0, h->stream>>>(
-                              M, mstride, n, ncols, k0, nbe, aux.ipiv));
+            DD_KLAUNCH(h, lu_swap_trsm_kernel<<<dim3(grid_for(right, LU_TRSM_WARPS), batch), 32 * LU_TRSM_WARPS, 0,
+                                                h->stream>>>(M, mstride, n, ncols, k0, nbe, aux.perm));
             const int below = n - k0 - nbe;
             if (below > 0) {
                 dim3 g(grid_for(right, ZG_T), grid_for(below, ZG_T), batch);
