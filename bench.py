@@ -78,6 +78,8 @@ def parse():
     p.add_argument("--no-lu", action="store_true", help="skip the timing of the dense LU check path (c1)")
     p.add_argument("--no-tol-block", action="store_true",
                    help="skip the measurement of the step with Dirichlet solves to 1e-10 instead of 1e-12")
+    p.add_argument("--no-f32-storage", action="store_true",
+                   help="skip the measurement of the step with FP32-storage inner solvers (tol_inner 1e-6)")
     p.add_argument("--no-sap", action="store_true",
                    help="skip the measurement of the step with SAP-preconditioned GCR global solves")
     p.add_argument("--sap-ncy", type=int, default=4, help="Schwarz cycles per SAP-GCR preconditioner application")
@@ -596,6 +598,12 @@ def run_gpu(args, cfg):
         # Dirichlet solves of the Schur pieces and the filter to 1e-10 instead of 1e-12
         supplement(line, "tol_block_1e-10", lambda: measure_outer_df64(
             args, cfg, dev, stream, rank, world, U_np, tune, outer=api.DD_PREC_F64, tol_block=1e-10, ref_ln=ref_ln))
+    if not args.no_f32_storage and args.prec == "f16":
+        # FP32 instead of FP16 storage of the inner solvers' vectors and links,
+        # each inner solve reducing the residual by 1e-6 (two FP64 cycles)
+        supplement(line, "inner_f32_storage", lambda: dict(measure_outer_df64(
+            args, cfg, dev, stream, rank, world, U_np, tune, outer=api.DD_PREC_F64, ref_ln=ref_ln,
+            prec=api.DD_PREC_F32, tol_inner=1e-6), tol_inner=1e-6))
     if not args.no_sap and args.prec != "f64":
         # the global solves by SAP-preconditioned flexible GCR instead of BiCGStab
         sap = {"sap_ncy": args.sap_ncy, "sap_nmr": args.sap_nmr, "sap_nkv": args.sap_nkv}
@@ -654,7 +662,7 @@ def supplement(line, key, fn):
 
 
 def measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune, krylov=None, outer=None, sap=None,
-                       tol_block=1e-12, ref_ln=None):
+                       tol_block=1e-12, ref_ln=None, prec=None, tol_inner=None):
     """The timed step again with the defect-correction residual in
     double-float arithmetic (outer_prec DD_PREC_DF64), or with another inner
     Krylov method (krylov, sap: DD_KRYLOV_SAP_GCR and its parameters), same
@@ -663,14 +671,15 @@ def measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune, krylov=N
     import torch
     from paper_1112_1243_gb300 import api
     from paper_1112_1243_gb300.chain import HierarchicalStep
-    prec = {"f16": api.DD_PREC_F16, "f32": api.DD_PREC_F32}[args.prec]
+    prec = {"f16": api.DD_PREC_F16, "f32": api.DD_PREC_F32}[args.prec] if prec is None else prec
+    tol_inner = args.tol_inner if tol_inner is None else tol_inner
     if krylov is None:
         krylov = {"cgnr": api.DD_KRYLOV_CGNR, "bicgstab": api.DD_KRYLOV_BICGSTAB,
                   "sap": api.DD_KRYLOV_SAP_GCR}[args.krylov]
     outer = api.DD_PREC_DF64 if outer is None else outer
     nmax = max(cfg["n_global"], cfg["n_block"])
     h = api.dd_init(cfg["dims"], cfg["block"], cfg["kappa"], max_rhs=nmax, inner_prec=prec,
-                    block_prec=api.DD_PREC_F32, tol_global=1e-10, tol_block=tol_block, tol_inner=args.tol_inner,
+                    block_prec=api.DD_PREC_F32, tol_global=1e-10, tol_block=tol_block, tol_inner=tol_inner,
                     maxit=40000, stream=stream, device=dev, krylov=krylov, outer_prec=outer, **(sap or {}))
     if tune:
         api.dd_set_tuning(h, hop_tpb=tune["hop_tpb"], hop_spt=tune["hop_spt"], hop64_tpb=tune["hop64_tpb"],
@@ -694,11 +703,14 @@ def measure_outer_df64(args, cfg, dev, stream, rank, world, U_np, tune, krylov=N
     t_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     ms3, cnt3, _ = api.dd_kernel_timer(h, 2, 3)
     glob = api.dd_solver_stats(h, 0)
+    diri = api.dd_solver_stats(h, 1)
     api.dd_kernel_timer(h, 0, 0)
     out = {"value": job_rate(cfg["n_global"] * args.steps, world, t_ms), "unit": "estimates/s",
            "ms_per_step": t_ms / args.steps, "device_status": api.dd_status(h)[0],
            "global_solves": dict(glob, inner_per_system=glob["inner_iterations"] / max(1, glob["systems"]),
-                                 outer_cycles_per_solve=glob["outer_cycles"] / max(1, glob["solves"]))}
+                                 outer_cycles_per_solve=glob["outer_cycles"] / max(1, glob["solves"])),
+           "dirichlet_solves": dict(diri, inner_per_system=diri["inner_iterations"] / max(1, diri["systems"]),
+                                    outer_cycles_per_solve=diri["outer_cycles"] / max(1, diri["solves"]))}
     if cnt3:
         out.update(residual_hop_avg_us=1e3 * ms3 / max(1, cnt3), residual_hop_launches_timed=cnt3)
     if ref_ln is not None:
