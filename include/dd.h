@@ -353,6 +353,18 @@ int dd_global_accept(dd_t h, void* U, const void* U_old, const double* ln_r, int
  * invalid). */
 int dd_logdet_exact(dd_t h, const void* U, int which, double* out);
 
+/* Check of the bounded wait in the grid barrier of the LU panel launch (the
+ * paper has no counterpart: failure detection of the only kernel of the
+ * library that waits on other thread blocks).  Runs a cooperative launch of
+ * up to 8 thread blocks through three grid barriers; with missing > 0 the
+ * last barrier waits for that many arrivals that never come, gives up after
+ * its poll limit (a few seconds), raises DD_ERR_TIMEOUT in the device status
+ * word (dd_status) and returns.  *passed = 1 when every block passed all
+ * barriers, else 0.  Synchronises the handle's stream; needs the exact-path
+ * workspace (DD_FEAT_EXACT).  Errors: DD_ERR_INVALID_ARG (passed NULL,
+ * missing outside 0..64), DD_ERR_UNSUPPORTED, DD_ERR_CUDA. */
+int dd_barrier_check(dd_t h, int missing, int* passed);
+
 /* Mean plaquette <Re tr U_P / 3> (device, 1 double). */
 int dd_plaquette(dd_t h, const void* U, double* out);
 

@@ -330,6 +330,15 @@ def dd_solver_stats(h, kind):
     return dict(zip(names, list(out)))
 
 
+def dd_barrier_check(h, missing=0):
+    """Grid barrier of the LU panel launch with `missing` arrivals that never
+    come: True when every thread block passed (the bounded wait raises
+    DD_ERR_TIMEOUT in the device status word otherwise)."""
+    out = ctypes.c_int()
+    _check(h, _lib.load().dd_barrier_check(h.ptr, int(missing), ctypes.byref(out)))
+    return bool(out.value)
+
+
 def dd_alu_peaks(stream=None):
     """Measured FP64 FMA, FP32 FMA and FP64 mma.sync throughput (TFLOP/s) of the current GPU."""
     out = (ctypes.c_double * 3)()

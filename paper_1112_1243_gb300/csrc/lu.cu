@@ -682,6 +682,43 @@ int block_filter_exact(dd_handle* h, const double* U_old, const double* U_new, i
     return DD_OK;
 }
 
+// check of the bounded wait of the grid barrier: `rounds` barriers of all
+// thread blocks; the last one waits for `missing` arrivals that never come
+__global__ void barrier_check_kernel(unsigned* bar, int rounds, int missing, int* status, int* passed) {
+    __shared__ int s_ok;
+    for (int r = 1; r <= rounds; ++r) {
+        const unsigned target = (unsigned)r * gridDim.x + (r == rounds ? (unsigned)missing : 0u);
+        if (!lu_grid_barrier(bar, target, status, &s_ok)) return;
+    }
+    if (threadIdx.x == 0) atomicAdd(passed, 1);
+}
+
+extern "C" int dd_barrier_check(dd_t h, int missing, int* passed) {
+    int rc = dd_require_ws(h);
+    if (rc) return rc;
+    rc = dd_require_feature(h, h->feat_exact, "dd_barrier_check");
+    if (rc) return rc;
+    if (!passed || missing < 0 || missing > 64) return dd_fail(h, DD_ERR_INVALID_ARG, "dd_barrier_check: bad arguments");
+    size_t cap = 0;
+    char* scr = lu_scratch(h, &cap);
+    if (cap < 256) return dd_fail(h, DD_ERR_UNSUPPORTED, "dd_barrier_check: no scratch");
+    unsigned* bar = (unsigned*)scr;
+    int* dpassed = (int*)(scr + 128);
+    DD_CUDA(h, cudaMemsetAsync(scr, 0, 256, h->stream));
+    const int ctas = std::max(1, std::min(8, h->num_sms));
+    int rounds = 3;
+    void* args[] = {&bar, &rounds, &missing, &h->d_status, &dpassed};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)barrier_check_kernel, dim3(ctas), dim3(LU_THREADS), args,
+                                                0, h->stream);
+    ++h->launches;
+    if (e != cudaSuccess) return dd_cuda_check(h, e, "barrier_check_kernel (cooperative launch)");
+    int np = 0;
+    DD_CUDA(h, cudaMemcpyAsync(&np, dpassed, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    DD_CUDA(h, cudaStreamSynchronize(h->stream));
+    *passed = np == ctas ? 1 : 0;
+    return DD_OK;
+}
+
 extern "C" int dd_logdet_exact(dd_t h, const void* U, int which, double* out) {
     int rc = dd_require_ws(h);
     if (rc) return rc;

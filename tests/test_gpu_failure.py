@@ -1,9 +1,13 @@
 """Failure paths of the library, driven by host-made inputs (nothing here
-faults a GPU): an iteration cap the solver cannot meet, and a gauge field
-with a non-finite entry.  Every call returns its documented error code, and
-the device status word (read and cleared by dd_status) carries the same code
-where the work ran without host polling (a replayed CUDA graph).  No kernel
-of the library waits on a flag, so there is no wait to time out."""
+faults a GPU): an iteration cap the solver cannot meet, a gauge field with a
+non-finite entry, and a grid barrier that waits for an arrival that never
+comes.  Every call returns its documented error code, and the device status
+word (read and cleared by dd_status) carries the same code where the work
+ran without host polling (a replayed CUDA graph).  The only kernel of the
+library that waits on other thread blocks is the cooperative LU panel
+launch; its barrier gives up after a bounded number of polls."""
+import time
+
 import numpy as np
 import pytest
 
@@ -85,4 +89,25 @@ def test_non_finite_gauge_field_reports_numeric(api):
     api.dd_gauge_update(h, Up, 3, 5.3, 1, 0, 11, 3)
     ln = api.dd_det_ratio_estimate(h, U, Up, 2, 5, 3)
     assert np.all(np.isfinite(host(ln)))
+    assert api.dd_status(h)[0] == 0
+
+
+def test_grid_barrier_wait_is_bounded(api):
+    """The grid barrier of the LU panel launch: all arrivals -> passed, no
+    status; one arrival missing -> the wait gives up within seconds, the
+    status word reads DD_ERR_TIMEOUT, and the context still works (an exact
+    determinant right after matches the one before)."""
+    dims, block = (4, 4, 4, 4), (2, 2, 2, 2)
+    h = api.dd_init(dims, block, 0.12)
+    U = dev(synthetic.random_gauge(dims, 0.4, 1))
+    ref = float(host(api.dd_logdet_exact(h, U, 0))[0])
+    assert api.dd_barrier_check(h, 0) is True
+    assert api.dd_status(h)[0] == 0
+    t0 = time.time()
+    assert api.dd_barrier_check(h, 1) is False
+    waited = time.time() - t0
+    assert api.dd_status(h)[0] == api.DD_ERR_TIMEOUT
+    assert waited < 60.0
+    assert api.dd_status(h)[0] == 0              # read and cleared
+    assert float(host(api.dd_logdet_exact(h, U, 0))[0]) == ref
     assert api.dd_status(h)[0] == 0
