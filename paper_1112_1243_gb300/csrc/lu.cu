@@ -186,16 +186,46 @@ DD_DEV bool lu_grid_barrier(unsigned* bar, unsigned target, int* status, int* s_
     return *s_ok != 0;
 }
 
-// panel factorisation, step 1; grid (ctas, matrices), thread block b holds
-// rows k0 + b*rows_per .. of the panel
-template <bool MULTI>
+// the panel's swaps as one permutation of the rows they touch (the first
+// thread block owns rows k0.. and wrote their pivots): position i of the
+// list receives the value that row src[i] held before the panel
+DD_DEV void lu_panel_permutation(const LuAux& aux, int m, int n, int k0, int nbe) {
+    int rows[2 * LU_NB], src[2 * LU_NB];
+    int nrow = nbe;
+    for (int t = 0; t < nbe; ++t) rows[t] = src[t] = k0 + t;
+    for (int t = 0; t < nbe; ++t) {
+        const int p = aux.ipiv[(long long)m * n + k0 + t];
+        int q = -1;
+        for (int i = 0; i < nrow; ++i)
+            if (rows[i] == p) {
+                q = i;
+                break;
+            }
+        if (q < 0) {
+            q = nrow++;
+            rows[q] = src[q] = p;
+        }
+        const int tmp = src[t];
+        src[t] = src[q];
+        src[q] = tmp;
+    }
+    int* pm = aux.perm + (long long)m * (4 * LU_NB + 1);
+    for (int i = 0; i < nrow; ++i) {
+        pm[i] = rows[i];
+        pm[2 * LU_NB + i] = src[i];
+    }
+    pm[4 * LU_NB] = nrow;
+}
+
+// panel factorisation, step 1, of matrices up to LU_SINGLE_MAX rows: one
+// thread block per matrix holds all rows k0..n-1 of the panel
 __global__ void __launch_bounds__(LU_THREADS) lu_panel_kernel(double2* M, long long mstride, int n, int k0, int nbe,
                                                               int rows_per, LuAux aux, double* logdet, int* status) {
     extern __shared__ double2 pan[];  // [rows_per][LU_LD]
     __shared__ double2 urow[LU_NB];
     __shared__ double sv[LU_THREADS / 32];
     __shared__ int si[LU_THREADS / 32];
-    __shared__ int s_p, s_bc, s_ok;
+    __shared__ int s_p;
     const int m = blockIdx.y, c = blockIdx.x, ctas = gridDim.x, tid = threadIdx.x;
     double2* A = M + (long long)m * mstride;
     const int r0 = k0 + c * rows_per;
@@ -215,46 +245,14 @@ __global__ void __launch_bounds__(LU_THREADS) lu_panel_kernel(double2* M, long l
         }
         block_argmax(best, bi, sv, si);
         const bool own_k = k >= r0 && k < r0 + nr;
-        if (MULTI) {
-            const int buf = j & 1;
-            const long long mc = (long long)buf * gridDim.y + m;
-            if (tid == 0) {
-                aux.part[(mc * ctas + c) * 2] = sv[0];
-                aux.part[(mc * ctas + c) * 2 + 1] = (double)si[0];
-            }
-            if (tid < nbe && sv[0] >= 0.0) aux.prow[(mc * ctas + c) * LU_NB + tid] = pan[(si[0] - r0) * LU_LD + tid];
-            if (tid < nbe && own_k) aux.rowk[mc * LU_NB + tid] = pan[(k - r0) * LU_LD + tid];
-            if (!lu_grid_barrier(aux.bar, (unsigned)(j + 1) * ctas * gridDim.y, status, &s_ok)) return;
-            // the winner over all thread blocks of this matrix, read in parallel
-            double bv = -1.0;
-            int bidx = INT_MAX;
-            for (int q = tid; q < ctas; q += blockDim.x)
-                argmax_merge(bv, bidx, __ldcg(aux.part + (mc * ctas + q) * 2),
-                             (int)__ldcg(aux.part + (mc * ctas + q) * 2 + 1));
-            block_argmax(bv, bidx, sv, si);
-            if (tid == 0) {
-                s_p = si[0];
-                s_bc = (si[0] - k0) / rows_per;
-            }
-            __syncthreads();
-            const int p = s_p;
-            if (tid < nbe) {
-                const double2 u = __ldcg(aux.prow + (mc * ctas + s_bc) * LU_NB + tid);
-                const double2 old = __ldcg(aux.rowk + mc * LU_NB + tid);
-                urow[tid] = u;
-                if (own_k) pan[(k - r0) * LU_LD + tid] = u;
-                if (p != k && p >= r0 && p < r0 + nr) pan[(p - r0) * LU_LD + tid] = old;
-            }
-        } else {
-            if (tid == 0) s_p = si[0];
-            __syncthreads();
-            const int p = s_p;
-            if (tid < nbe) {
-                const double2 u = pan[(p - r0) * LU_LD + tid], old = pan[(k - r0) * LU_LD + tid];
-                urow[tid] = u;
-                pan[(k - r0) * LU_LD + tid] = u;
-                pan[(p - r0) * LU_LD + tid] = old;
-            }
+        if (tid == 0) s_p = si[0];
+        __syncthreads();
+        const int p = s_p;
+        if (tid < nbe) {
+            const double2 u = pan[(p - r0) * LU_LD + tid], old = pan[(k - r0) * LU_LD + tid];
+            urow[tid] = u;
+            pan[(k - r0) * LU_LD + tid] = u;
+            pan[(p - r0) * LU_LD + tid] = old;
         }
         __syncthreads();
         const double2 piv = urow[j];
@@ -284,36 +282,111 @@ __global__ void __launch_bounds__(LU_THREADS) lu_panel_kernel(double2* M, long l
         const int r = e % nr, j = e / nr;
         A[(r0 + r) + (long long)(k0 + j) * n] = pan[r * LU_LD + j];
     }
-    // the panel's swaps as one permutation of the rows they touch (the first
-    // thread block owns rows k0.. and wrote their pivots): position i of the
-    // list receives the value that row src[i] held before the panel
-    if (c == 0 && tid == 0) {
-        int rows[2 * LU_NB], src[2 * LU_NB];
-        int nrow = nbe;
-        for (int t = 0; t < nbe; ++t) rows[t] = src[t] = k0 + t;
-        for (int t = 0; t < nbe; ++t) {
-            const int p = aux.ipiv[(long long)m * n + k0 + t];
-            int q = -1;
-            for (int i = 0; i < nrow; ++i)
-                if (rows[i] == p) {
-                    q = i;
-                    break;
-                }
-            if (q < 0) {
-                q = nrow++;
-                rows[q] = src[q] = p;
-            }
-            const int tmp = src[t];
-            src[t] = src[q];
-            src[q] = tmp;
-        }
-        int* pm = aux.perm + (long long)m * (4 * LU_NB + 1);
-        for (int i = 0; i < nrow; ++i) {
-            pm[i] = rows[i];
-            pm[2 * LU_NB + i] = src[i];
-        }
-        pm[4 * LU_NB] = nrow;
+    if (c == 0 && tid == 0) lu_panel_permutation(aux, m, n, k0, nbe);
+}
+
+// Panel factorisation of matrices above LU_SINGLE_MAX rows: thread block b of
+// the cooperative launch holds rows k0 + 32 b .. (one row per lane).  Warp 0
+// does the pivot search and the exchange of candidates with warp shuffles;
+// all warps do the rank-1 update (lane = row, warp = group of columns).  The
+// multipliers go to Lm, not into the column being read, so the update needs
+// no extra barrier; a row that moves carries its multipliers (Lm, columns
+// left of j) and its remaining entries (pan, columns from j on).
+static_assert(LU_PR == 32, "one panel row per lane");
+__global__ void __launch_bounds__(LU_THREADS) lu_panel_multi_kernel(double2* M, long long mstride, int n, int k0,
+                                                                    int nbe, LuAux aux, double* logdet, int* status) {
+    __shared__ double2 pan[LU_PR][LU_LD];
+    __shared__ double2 Lm[LU_PR][LU_LD];
+    __shared__ double2 urow[LU_NB];
+    __shared__ int s_p, s_ok;
+    const int m = blockIdx.y, c = blockIdx.x, ctas = gridDim.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    double2* A = M + (long long)m * mstride;
+    const int r0 = k0 + c * LU_PR;
+    const int nr = min(LU_PR, n - r0);
+    for (int e = tid; e < nr * nbe; e += blockDim.x) {
+        const int r = e % nr, j = e / nr;
+        pan[r][j] = A[(r0 + r) + (long long)(k0 + j) * n];
     }
+    __syncthreads();
+    for (int j = 0; j < nbe; ++j) {
+        const int k = k0 + j;
+        const bool own_k = k >= r0 && k < r0 + nr;
+        const long long mc = (long long)(j & 1) * gridDim.y + m;
+        if (warp == 0) {
+            double best = -1.0;
+            int bi = INT_MAX;
+            if (lane < nr && r0 + lane >= k) {
+                const double2 v = pan[lane][j];
+                best = v.x * v.x + v.y * v.y;
+                bi = r0 + lane;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                argmax_merge(best, bi, __shfl_xor_sync(0xffffffffu, best, o), __shfl_xor_sync(0xffffffffu, bi, o));
+            if (lane == 0) {
+                aux.part[(mc * ctas + c) * 2] = best;
+                aux.part[(mc * ctas + c) * 2 + 1] = (double)bi;
+            }
+            if (lane < nbe) {
+                if (best >= 0.0) {
+                    const int rb = bi - r0;
+                    aux.prow[(mc * ctas + c) * LU_NB + lane] = lane < j ? Lm[rb][lane] : pan[rb][lane];
+                }
+                if (own_k) aux.rowk[mc * LU_NB + lane] = lane < j ? Lm[k - r0][lane] : pan[k - r0][lane];
+            }
+        }
+        if (!lu_grid_barrier(aux.bar, (unsigned)(j + 1) * ctas * gridDim.y, status, &s_ok)) return;
+        if (warp == 0) {
+            double bv = -1.0;
+            int bidx = INT_MAX;
+            for (int q = lane; q < ctas; q += 32)
+                argmax_merge(bv, bidx, __ldcg(aux.part + (mc * ctas + q) * 2),
+                             (int)__ldcg(aux.part + (mc * ctas + q) * 2 + 1));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                argmax_merge(bv, bidx, __shfl_xor_sync(0xffffffffu, bv, o), __shfl_xor_sync(0xffffffffu, bidx, o));
+            const int bc = (bidx - k0) / LU_PR;
+            if (lane < nbe) {
+                const double2 u = __ldcg(aux.prow + (mc * ctas + bc) * LU_NB + lane);
+                const double2 old = __ldcg(aux.rowk + mc * LU_NB + lane);
+                urow[lane] = u;
+                if (own_k) (lane < j ? Lm[k - r0][lane] : pan[k - r0][lane]) = u;
+                if (bidx != k && bidx >= r0 && bidx < r0 + nr) (lane < j ? Lm[bidx - r0][lane] : pan[bidx - r0][lane]) = old;
+            }
+            if (lane == 0) s_p = bidx;
+        }
+        __syncthreads();
+        const double2 piv = urow[j];
+        const double pm = piv.x * piv.x + piv.y * piv.y;
+        if (tid == 0 && own_k) {
+            aux.ipiv[(long long)m * n + k] = s_p;
+            if (!(pm > 0.0)) raise_status(status, DD_ERR_NUMERIC);
+            logdet[m] += 0.5 * log(pm);
+        }
+        const int r = lane;
+        if (r < nr && r0 + r > k) {
+            const double2 a = pan[r][j];
+            if (pm > 0.0) {
+                const cpx<double> l = cmul(mk<double>(a.x, a.y), mk<double>(piv.x / pm, -piv.y / pm));
+                if (warp == 0) Lm[r][j] = make_double2(l.x, l.y);
+                for (int jj = j + 1 + warp; jj < nbe; jj += nwarps) {
+                    const double2 u = urow[jj];
+                    double2& t = pan[r][jj];
+                    t.x -= l.x * u.x - l.y * u.y;
+                    t.y -= l.x * u.y + l.y * u.x;
+                }
+            } else if (warp == 0) {
+                Lm[r][j] = a;  // zero pivot: column left as it is (DD_ERR_NUMERIC raised)
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < nr * nbe; e += blockDim.x) {
+        const int rr = e % nr, j = e / nr;
+        A[(r0 + rr) + (long long)(k0 + j) * n] = (r0 + rr > k0 + j) ? Lm[rr][j] : pan[rr][j];
+    }
+    if (c == 0 && tid == 0) lu_panel_permutation(aux, m, n, k0, nbe);
 }
 
 // step 2: one warp per column right of the panel: the panel's row
@@ -491,16 +564,15 @@ static int lu_batched(dd_handle* h, double2* M, long long mstride, int batch, in
     char* scr = lu_scratch(h, &cap);
     const bool single = n <= LU_SINGLE_MAX;
     const int ctas0 = single ? 1 : grid_for(n, LU_PR);
-    const size_t multi_smem = (size_t)LU_PR * LU_LD * sizeof(double2);
     int chunk = batch;
     if (single) {
         const size_t smem = (size_t)n * LU_LD * sizeof(double2);
-        cudaError_t e = cudaFuncSetAttribute(lu_panel_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(lu_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return dd_cuda_check(h, e, "lu_panel_kernel shared memory");
     } else {
         // one cooperative launch holds every thread block of its matrices
         int per_sm = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_panel_kernel<true>, LU_THREADS, multi_smem);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_panel_multi_kernel, LU_THREADS, 0);
         if (e != cudaSuccess) return dd_cuda_check(h, e, "lu_panel_kernel occupancy");
         const long long resident = (long long)per_sm * std::max(1, h->num_sms);
         if (resident < ctas0) return dd_fail(h, DD_ERR_UNSUPPORTED, "dense LU: a panel needs more thread blocks than fit on the GPU");
@@ -530,7 +602,7 @@ static int lu_batched(dd_handle* h, double2* M, long long mstride, int batch, in
         if (single) {
             const int rows = n - k0;
             const size_t smem = (size_t)rows * LU_LD * sizeof(double2);
-            DD_KLAUNCH(h, lu_panel_kernel<false><<<dim3(1, batch), LU_THREADS, smem, h->stream>>>(
+            DD_KLAUNCH(h, lu_panel_kernel<<<dim3(1, batch), LU_THREADS, smem, h->stream>>>(
                               M, mstride, n, k0, nbe, rows, aux, logdet, h->d_status));
         } else {
             const int ctas = grid_for(n - k0, LU_PR);
@@ -543,12 +615,12 @@ static int lu_batched(dd_handle* h, double2* M, long long mstride, int batch, in
                 LuAux ac = aux;
                 ac.ipiv = aux.ipiv + (long long)m0 * n;
                 ac.perm = aux.perm + (long long)m0 * (4 * LU_NB + 1);
-                int nn = n, kk0 = k0, nb_ = nbe, rp = LU_PR;
+                int nn = n, kk0 = k0, nb_ = nbe;
                 long long ms = mstride;
                 int* st = h->d_status;
-                void* args[] = {&Mc, &ms, &nn, &kk0, &nb_, &rp, &ac, &ldc, &st};
-                e = cudaLaunchCooperativeKernel((const void*)lu_panel_kernel<true>, dim3(ctas, mb), dim3(LU_THREADS), args,
-                                                multi_smem, h->stream);
+                void* args[] = {&Mc, &ms, &nn, &kk0, &nb_, &ac, &ldc, &st};
+                e = cudaLaunchCooperativeKernel((const void*)lu_panel_multi_kernel, dim3(ctas, mb), dim3(LU_THREADS), args,
+                                                0, h->stream);
                 ++h->launches;
                 if (e != cudaSuccess) return dd_cuda_check(h, e, "lu_panel_kernel (cooperative launch)");
             }
