@@ -887,7 +887,9 @@ def measure_lu(dev, stream, reps=3):
     U = torch.from_numpy(synthetic.random_gauge(dims, 0.4, 1)).to(dev)
     out = {"workload": "c1: 4^4 lattice, 2^4 blocks, kappa 0.12, eps 0.4"}
     alu, src = peaks_alu(stream)
-    for which, name, n, nmat in ((0, "D", 3072, 1), (1, "D_b", 192, 16), (2, "Dhat", 1536, 1)):
+    for which, name, n, nmat, tc in ((0, "D", 3072, 1, True), (1, "D_b", 192, 16, True), (2, "Dhat", 1536, 1, True),
+                                     (0, "D_fp64_update", 3072, 1, False), (2, "Dhat_fp64_update", 1536, 1, False)):
+        api.dd_lu_tensor_cores(h, tc)
         api.dd_logdet_exact(h, U, which)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -898,6 +900,8 @@ def measure_lu(dev, stream, reps=3):
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1) / reps
         out[name] = {"ms": ms, "n": n, "matrices": nmat}
+        out[name]["trailing_update"] = ("FP16 tensor cores (FP64-exact Ozaki slices)" if tc and n > 384
+                                        else "FP64 FMA")
         if which == 0:
             tf = 8.0 * n ** 3 / 3.0 / (ms / 1e3) / 1e12
             out[name].update(achieved_tflops=tf, peak_fp64_tflops=alu["fp64_fma"], frac=tf / alu["fp64_fma"],

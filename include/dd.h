@@ -353,6 +353,18 @@ int dd_global_accept(dd_t h, void* U, const void* U_old, const double* ln_r, int
  * invalid). */
 int dd_logdet_exact(dd_t h, const void* U, int which, double* out);
 
+/* Trailing update of the dense LU of dd_logdet_exact (matrices above 384
+ * rows): on = 1 (default) on the FP16 tensor cores with FP64 accuracy by the
+ * Ozaki scheme (every FP64 row and column scaled by a power of two and cut
+ * into 8 integer slices of 7 bits; the 36 slice pairs of the 8 heaviest
+ * weights multiplied with mma.sync, whose FP32 accumulation is exact for
+ * these integers, and summed in FP64; what is left out stays below the
+ * rounding bound of an FP64 dot product); on = 0 on the FP64 FMA pipe (no
+ * counterpart in the paper: the tensor-core form of its exact check path).
+ * Falls back to FP64 FMA when the exact-path workspace has no room for the
+ * slices.  Errors: DD_ERR_INVALID_ARG (on not 0 or 1). */
+int dd_lu_tensor_cores(dd_t h, int on);
+
 /* Check of the bounded wait in the grid barrier of the LU panel launch (the
  * paper has no counterpart: failure detection of the only kernel of the
  * library that waits on other thread blocks).  Runs a cooperative launch of

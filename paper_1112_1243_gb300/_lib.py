@@ -143,6 +143,7 @@ SIGNATURES = {
     "dd_block_accept": [_P, _P, _P, _I, _P, _U64, _U64, _P],
     "dd_alu_peaks": [ctypes.POINTER(_D), _P],
     "dd_barrier_check": [_P, _I, ctypes.POINTER(_I)],
+    "dd_lu_tensor_cores": [_P, _I],
     "dd_block_ratios_noalloc": [ctypes.POINTER(_I), ctypes.POINTER(_I), _D, _I, _I, _P, _P, _U64, _U64, _D, _P,
                                 _P],
     "dd_chain_step": [_P, _P, ctypes.POINTER(dd_chain_params), ctypes.POINTER(dd_chain_buffers), ctypes.c_ulonglong],

@@ -330,6 +330,12 @@ def dd_solver_stats(h, kind):
     return dict(zip(names, list(out)))
 
 
+def dd_lu_tensor_cores(h, on=True):
+    """Trailing update of the dense LU on the tensor cores (FP64-exact Ozaki
+    slices; default) or on the FP64 FMA pipe."""
+    _check(h, _lib.load().dd_lu_tensor_cores(h.ptr, 1 if on else 0))
+
+
 def dd_barrier_check(h, missing=0):
     """Grid barrier of the LU panel launch with `missing` arrivals that never
     come: True when every thread block passed (the bounded wait raises

@@ -163,6 +163,7 @@ struct dd_handle {
     int* d_imap = nullptr;           // small index maps: [nblocks] item bases, [2*max_rhs] field slots
     int items_cap = 0;
     double* d_lu = nullptr;          // dense matrices for the exact path
+    bool lu_tensor = true;           // dense LU: trailing update on the tensor cores (Ozaki slices)
     double* d_gauge_g = nullptr;     // relative gauge fixing: one SU(3) matrix per site [V][18]
     size_t lu_bytes = 0;
     std::string last_error;

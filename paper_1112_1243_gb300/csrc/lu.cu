@@ -433,6 +433,157 @@ __global__ void __launch_bounds__(32 * LU_TRSM_WARPS) lu_swap_trsm_kernel(double
     if (lane < nbe) col[k0 + lane] = x;
 }
 
+// ------------------------------------------------ trailing update on tensor cores
+// The trailing update A22 -= L21 U12 as an FP64-exact product on the FP16
+// tensor cores (Ozaki scheme).  Each row i of [Re L21, Im L21] (64 reals) is
+// scaled by 2^-e_i so that its entries are below 1 in magnitude and cut into
+// OZ_S slices of OZ_BETA bits: x 2^-e_i = sum_s q_s 2^(-OZ_BETA (s + 1)),
+// q_s integers (|q_0| <= 2^OZ_BETA, |q_s| <= 2^(OZ_BETA - 1)), exact in FP16.
+// The columns of [Re U12; Im U12] likewise (exponents f_j).  A product of two
+// slices is an integer below 2^(2 OZ_BETA); the slice pairs (s, t) of one
+// diagonal d = s + t share the weight 2^(-OZ_BETA (d + 2)), and their sum
+// over the 64 terms stays below 2^22, so the tensor cores' FP32 accumulation
+// of a diagonal is exact.  The diagonals d < OZ_S are summed in FP64 and
+// scaled by 2^(e_i + f_j).  What is left out (the pairs with s + t >= OZ_S
+// and the remainders after OZ_S slices) adds up to less than 2^-48 of the
+// product of the row and column maxima, below the rounding bound of an FP64
+// dot product of the same 64 terms (64 x 2^-53).  Complex products:
+// C_re = [Re L, Im L] [Re U; -Im U], C_im = [Re L, Im L] [Im U; Re U].
+constexpr int OZ_BETA = 7;
+constexpr int OZ_S = 8;
+constexpr int OZ_K = 2 * LU_NB;  // real k of the complex panel width
+constexpr int OZ_T = 64;         // rows and columns of C per thread block
+constexpr int OZ_LD = OZ_K + 8;  // padded smem row of 64 halves (conflict-free fragment loads)
+
+// slices of L21 rows (transposed = false) or U12 columns (transposed = true):
+// one warp per row / column; out[s][r][0..63] (FP16), ex[r] the exponent
+__global__ void __launch_bounds__(256) ozaki_split_kernel(const double2* X, int ld, int nrows, int nbe, bool transposed,
+                                                          __half* out, long long slice_stride, int* ex) {
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (r >= nrows) return;
+    double a0 = 0.0, a1 = 0.0;
+    if (lane < nbe) {
+        const double2 v = transposed ? X[lane + (long long)r * ld] : X[r + (long long)lane * ld];
+        a0 = v.x;
+        a1 = v.y;
+    }
+    double mx = fmax(fabs(a0), fabs(a1));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);  // mx < 2^e
+    double t0 = ldexp(a0, -e), t1 = ldexp(a1, -e);
+    __half* o = out + (long long)r * OZ_K;
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+        t0 *= (double)(1 << OZ_BETA);
+        t1 *= (double)(1 << OZ_BETA);
+        const double q0 = rint(t0), q1 = rint(t1);
+        t0 -= q0;
+        t1 -= q1;
+        o[s * slice_stride + lane] = __double2half(q0);
+        o[s * slice_stride + lane + 32] = __double2half(q1);
+    }
+    if (lane == 0) ex[r] = e;
+}
+
+DD_DEV void mma_f16_f32(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// C (m x nn complex, column-major, ld ldc) -= L21 U12 from the slices: a
+// 64 x 64 tile of C per thread block of 8 warps, 16 x 32 per warp (one m16
+// row of four n8 tiles), every slice of the tile's rows and columns staged
+// in shared memory once
+__global__ void __launch_bounds__(256, 1) ozaki_update_kernel(int m, int nn, const __half* As, const int* ea,
+                                                              long long sa, const __half* Bs, const int* eb,
+                                                              long long sb, double2* C, int ldc) {
+    extern __shared__ __align__(16) unsigned char oz_smem[];
+    __half* sA = reinterpret_cast<__half*>(oz_smem);
+    __half* sB = sA + OZ_S * OZ_T * OZ_LD;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int r0 = blockIdx.y * OZ_T, c0 = blockIdx.x * OZ_T;
+    for (int e = tid; e < OZ_S * OZ_T * (OZ_K / 8); e += blockDim.x) {
+        const int s = e / (OZ_T * (OZ_K / 8)), rem = e % (OZ_T * (OZ_K / 8)), row = rem / (OZ_K / 8), q = rem % (OZ_K / 8);
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        const uint4 va = r0 + row < m ? reinterpret_cast<const uint4*>(As + s * sa + (long long)(r0 + row) * OZ_K)[q] : z;
+        const uint4 vb = c0 + row < nn ? reinterpret_cast<const uint4*>(Bs + s * sb + (long long)(c0 + row) * OZ_K)[q] : z;
+        *reinterpret_cast<uint4*>(sA + (s * OZ_T + row) * OZ_LD + q * 8) = va;
+        *reinterpret_cast<uint4*>(sB + (s * OZ_T + row) * OZ_LD + q * 8) = vb;
+    }
+    __syncthreads();
+    const int wm = warp & 3, wn = warp >> 2, g = lane >> 2, tig = lane & 3;
+    double accR[4][4], accI[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) accR[nt][c] = accI[nt][c] = 0.0;
+#pragma unroll 1
+    for (int d = 0; d < OZ_S; ++d) {
+        float fR[4][4], fI[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) fR[nt][c] = fI[nt][c] = 0.0f;
+#pragma unroll 1
+        for (int s = 0; s <= d; ++s) {
+            const __half* ab = sA + (s * OZ_T + 16 * wm) * OZ_LD;
+            const __half* bb = sB + ((d - s) * OZ_T + 32 * wn) * OZ_LD;
+#pragma unroll
+            for (int ks = 0; ks < OZ_K / 16; ++ks) {
+                const int k0 = 16 * ks + 2 * tig, k1 = k0 + 8;
+                uint32_t a[4];
+                a[0] = *reinterpret_cast<const uint32_t*>(ab + g * OZ_LD + k0);
+                a[1] = *reinterpret_cast<const uint32_t*>(ab + (g + 8) * OZ_LD + k0);
+                a[2] = *reinterpret_cast<const uint32_t*>(ab + g * OZ_LD + k1);
+                a[3] = *reinterpret_cast<const uint32_t*>(ab + (g + 8) * OZ_LD + k1);
+                // first half of k: Re U (real part), Im U (imaginary part);
+                // second half: -Im U (real part), Re U (imaginary part)
+                const bool hi = 16 * ks >= LU_NB;
+                const int ko = hi ? -LU_NB : LU_NB;
+                const uint32_t sg = hi ? 0x80008000u : 0u;
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) {
+                    const __half* bc = bb + (8 * nt + g) * OZ_LD;
+                    const uint32_t br0 = *reinterpret_cast<const uint32_t*>(bc + k0) ^ sg;
+                    const uint32_t br1 = *reinterpret_cast<const uint32_t*>(bc + k1) ^ sg;
+                    const uint32_t bi0 = *reinterpret_cast<const uint32_t*>(bc + k0 + ko);
+                    const uint32_t bi1 = *reinterpret_cast<const uint32_t*>(bc + k1 + ko);
+                    mma_f16_f32(fR[nt], a, br0, br1);
+                    mma_f16_f32(fI[nt], a, bi0, bi1);
+                }
+            }
+        }
+        const double w = ldexp(1.0, -OZ_BETA * (d + 2));
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                accR[nt][c] = fma(w, (double)fR[nt][c], accR[nt][c]);
+                accI[nt][c] = fma(w, (double)fI[nt][c], accI[nt][c]);
+            }
+    }
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int row = r0 + 16 * wm + g + (c >= 2 ? 8 : 0);
+            const int col = c0 + 32 * wn + 8 * nt + 2 * tig + (c & 1);
+            if (row < m && col < nn) {
+                const double sc = ldexp(1.0, ea[row] + eb[col]);
+                double2& o = C[row + (long long)col * ldc];
+                o.x -= sc * accR[nt][c];
+                o.y -= sc * accI[nt][c];
+            }
+        }
+}
+constexpr size_t OZ_SMEM = (size_t)2 * OZ_S * OZ_T * OZ_LD * sizeof(__half);
+
 // back substitution on the right-hand-side columns nelim..ncols-1 of an
 // eliminated augmented matrix [U | Y]: step k (descending) scales row k and
 // eliminates it from the rows above
@@ -596,6 +747,30 @@ static int lu_batched(dd_handle* h, double2* M, long long mstride, int batch, in
         o += 256;
     }
     if (o > cap) return dd_fail(h, DD_ERR_UNSUPPORTED, "dense LU: no room for the pivot scratch");
+    // slices of the tensor-core trailing update (matrices above LU_SINGLE_MAX rows)
+    __half *oa = nullptr, *ob = nullptr;
+    int *oea = nullptr, *oeb = nullptr;
+    const long long osa = (long long)n * OZ_K, osb = (long long)ncols * OZ_K;
+    bool tensor = !single && h->lu_tensor;
+    if (tensor) {
+        size_t need = o + up((size_t)OZ_S * osa * sizeof(__half)) + up((size_t)OZ_S * osb * sizeof(__half)) +
+                      up((size_t)n * sizeof(int)) + up((size_t)ncols * sizeof(int));
+        if (need > cap) {
+            tensor = false;  // no room: the FP64 FMA update
+        } else {
+            oa = (__half*)(scr + o);
+            o += up((size_t)OZ_S * osa * sizeof(__half));
+            ob = (__half*)(scr + o);
+            o += up((size_t)OZ_S * osb * sizeof(__half));
+            oea = (int*)(scr + o);
+            o += up((size_t)n * sizeof(int));
+            oeb = (int*)(scr + o);
+            o += up((size_t)ncols * sizeof(int));
+            cudaError_t e = cudaFuncSetAttribute(ozaki_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)OZ_SMEM);
+            if (e != cudaSuccess) return dd_cuda_check(h, e, "ozaki_update_kernel shared memory");
+        }
+    }
     DD_KLAUNCH(h, zero_doubles_kernel<<<grid_for(batch, 64), 64, 0, h->stream>>>(batch, logdet));
     for (int k0 = 0; k0 < n; k0 += LU_NB) {
         const int nbe = std::min(LU_NB, n - k0);
@@ -630,7 +805,19 @@ static int lu_batched(dd_handle* h, double2* M, long long mstride, int batch, in
             DD_KLAUNCH(h, lu_swap_trsm_kernel<<<dim3(grid_for(right, LU_TRSM_WARPS), batch), 32 * LU_TRSM_WARPS, 0,
                                                 h->stream>>>(M, mstride, n, ncols, k0, nbe, aux.perm));
             const int below = n - k0 - nbe;
-            if (below > 0) {
+            if (below > 0 && tensor) {
+                for (int mi = 0; mi < batch; ++mi) {
+                    double2* Mm = M + (long long)mi * mstride;
+                    DD_KLAUNCH(h, ozaki_split_kernel<<<grid_for(below, 8), 256, 0, h->stream>>>(
+                                      Mm + (k0 + nbe) + (long long)k0 * n, n, below, nbe, false, oa, osa, oea));
+                    DD_KLAUNCH(h, ozaki_split_kernel<<<grid_for(right, 8), 256, 0, h->stream>>>(
+                                      Mm + k0 + (long long)(k0 + nbe) * n, n, right, nbe, true, ob, osb, oeb));
+                    dim3 g(grid_for(right, OZ_T), grid_for(below, OZ_T));
+                    DD_KLAUNCH(h, ozaki_update_kernel<<<g, 256, OZ_SMEM, h->stream>>>(
+                                      below, right, oa, oea, osa, ob, oeb, osb, Mm + (k0 + nbe) + (long long)(k0 + nbe) * n,
+                                      n));
+                }
+            } else if (below > 0) {
                 dim3 g(grid_for(right, ZG_T), grid_for(below, ZG_T), batch);
                 DD_KLAUNCH(h, zgemm_tile_kernel<<<g, 256, 0, h->stream>>>(
                                   below, right, nbe, M + (k0 + nbe) + (long long)k0 * n, n, mstride,
@@ -788,6 +975,12 @@ extern "C" int dd_barrier_check(dd_t h, int missing, int* passed) {
     DD_CUDA(h, cudaMemcpyAsync(&np, dpassed, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     DD_CUDA(h, cudaStreamSynchronize(h->stream));
     *passed = np == ctas ? 1 : 0;
+    return DD_OK;
+}
+
+extern "C" int dd_lu_tensor_cores(dd_t h, int on) {
+    if (!h || on < 0 || on > 1) return DD_ERR_INVALID_ARG;
+    h->lu_tensor = on != 0;
     return DD_OK;
 }
 
