@@ -452,7 +452,8 @@ __global__ void __launch_bounds__(32 * LU_TRSM_WARPS) lu_swap_trsm_kernel(double
 constexpr int OZ_BETA = 7;
 constexpr int OZ_S = 8;
 constexpr int OZ_K = 2 * LU_NB;  // real k of the complex panel width
-constexpr int OZ_T = 64;         // rows and columns of C per thread block
+constexpr int OZ_TM = 64;        // rows of C per thread block (4 warps of 16 rows)
+constexpr int OZ_TN = 32;        // columns of C per thread block (two thread blocks per SM)
 constexpr int OZ_LD = OZ_K + 8;  // padded smem row of 64 halves (conflict-free fragment loads)
 
 // slices of L21 rows (transposed = false) or U12 columns (transposed = true):
@@ -497,27 +498,31 @@ DD_DEV void mma_f16_f32(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
 }
 
 // C (m x nn complex, column-major, ld ldc) -= L21 U12 from the slices: a
-// 64 x 64 tile of C per thread block of 8 warps, 16 x 32 per warp (one m16
+// 64 x 32 tile of C per thread block of 4 warps, 16 x 32 per warp (one m16
 // row of four n8 tiles), every slice of the tile's rows and columns staged
-// in shared memory once
-__global__ void __launch_bounds__(256, 1) ozaki_update_kernel(int m, int nn, const __half* As, const int* ea,
+// in shared memory once (110 KB: two thread blocks per SM, so that one
+// stages while the other computes)
+__global__ void __launch_bounds__(128, 2) ozaki_update_kernel(int m, int nn, const __half* As, const int* ea,
                                                               long long sa, const __half* Bs, const int* eb,
                                                               long long sb, double2* C, int ldc) {
     extern __shared__ __align__(16) unsigned char oz_smem[];
     __half* sA = reinterpret_cast<__half*>(oz_smem);
-    __half* sB = sA + OZ_S * OZ_T * OZ_LD;
+    __half* sB = sA + OZ_S * OZ_TM * OZ_LD;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int r0 = blockIdx.y * OZ_T, c0 = blockIdx.x * OZ_T;
-    for (int e = tid; e < OZ_S * OZ_T * (OZ_K / 8); e += blockDim.x) {
-        const int s = e / (OZ_T * (OZ_K / 8)), rem = e % (OZ_T * (OZ_K / 8)), row = rem / (OZ_K / 8), q = rem % (OZ_K / 8);
-        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    const int r0 = blockIdx.y * OZ_TM, c0 = blockIdx.x * OZ_TN;
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    for (int e = tid; e < OZ_S * OZ_TM * (OZ_K / 8); e += blockDim.x) {
+        const int s = e / (OZ_TM * (OZ_K / 8)), rem = e % (OZ_TM * (OZ_K / 8)), row = rem / (OZ_K / 8), q = rem % (OZ_K / 8);
         const uint4 va = r0 + row < m ? reinterpret_cast<const uint4*>(As + s * sa + (long long)(r0 + row) * OZ_K)[q] : z;
-        const uint4 vb = c0 + row < nn ? reinterpret_cast<const uint4*>(Bs + s * sb + (long long)(c0 + row) * OZ_K)[q] : z;
-        *reinterpret_cast<uint4*>(sA + (s * OZ_T + row) * OZ_LD + q * 8) = va;
-        *reinterpret_cast<uint4*>(sB + (s * OZ_T + row) * OZ_LD + q * 8) = vb;
+        *reinterpret_cast<uint4*>(sA + (s * OZ_TM + row) * OZ_LD + q * 8) = va;
+    }
+    for (int e = tid; e < OZ_S * OZ_TN * (OZ_K / 8); e += blockDim.x) {
+        const int s = e / (OZ_TN * (OZ_K / 8)), rem = e % (OZ_TN * (OZ_K / 8)), col = rem / (OZ_K / 8), q = rem % (OZ_K / 8);
+        const uint4 vb = c0 + col < nn ? reinterpret_cast<const uint4*>(Bs + s * sb + (long long)(c0 + col) * OZ_K)[q] : z;
+        *reinterpret_cast<uint4*>(sB + (s * OZ_TN + col) * OZ_LD + q * 8) = vb;
     }
     __syncthreads();
-    const int wm = warp & 3, wn = warp >> 2, g = lane >> 2, tig = lane & 3;
+    const int wm = warp, wn = 0, g = lane >> 2, tig = lane & 3;
     double accR[4][4], accI[4][4];
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt)
@@ -532,8 +537,8 @@ __global__ void __launch_bounds__(256, 1) ozaki_update_kernel(int m, int nn, con
             for (int c = 0; c < 4; ++c) fR[nt][c] = fI[nt][c] = 0.0f;
 #pragma unroll 1
         for (int s = 0; s <= d; ++s) {
-            const __half* ab = sA + (s * OZ_T + 16 * wm) * OZ_LD;
-            const __half* bb = sB + ((d - s) * OZ_T + 32 * wn) * OZ_LD;
+            const __half* ab = sA + (s * OZ_TM + 16 * wm) * OZ_LD;
+            const __half* bb = sB + ((d - s) * OZ_TN + 32 * wn) * OZ_LD;
 #pragma unroll
             for (int ks = 0; ks < OZ_K / 16; ++ks) {
                 const int k0 = 16 * ks + 2 * tig, k1 = k0 + 8;
@@ -582,7 +587,7 @@ __global__ void __launch_bounds__(256, 1) ozaki_update_kernel(int m, int nn, con
             }
         }
 }
-constexpr size_t OZ_SMEM = (size_t)2 * OZ_S * OZ_T * OZ_LD * sizeof(__half);
+constexpr size_t OZ_SMEM = (size_t)OZ_S * (OZ_TM + OZ_TN) * OZ_LD * sizeof(__half);
 
 // back substitution on the right-hand-side columns nelim..ncols-1 of an
 // eliminated augmented matrix [U | Y]: step k (descending) scales row k and
@@ -812,8 +817,8 @@ static int lu_batched(dd_handle* h, double2* M, long long mstride, int batch, in
                                       Mm + (k0 + nbe) + (long long)k0 * n, n, below, nbe, false, oa, osa, oea));
                     DD_KLAUNCH(h, ozaki_split_kernel<<<grid_for(right, 8), 256, 0, h->stream>>>(
                                       Mm + k0 + (long long)(k0 + nbe) * n, n, right, nbe, true, ob, osb, oeb));
-                    dim3 g(grid_for(right, OZ_T), grid_for(below, OZ_T));
-                    DD_KLAUNCH(h, ozaki_update_kernel<<<g, 256, OZ_SMEM, h->stream>>>(
+                    dim3 g(grid_for(right, OZ_TN), grid_for(below, OZ_TM));
+                    DD_KLAUNCH(h, ozaki_update_kernel<<<g, 128, OZ_SMEM, h->stream>>>(
                                       below, right, oa, oea, osa, ob, oeb, osb, Mm + (k0 + nbe) + (long long)(k0 + nbe) * n,
                                       n));
                 }
