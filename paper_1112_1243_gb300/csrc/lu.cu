@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(LU_THREADS) lu_panel_kernel(double2* M, long l
     __shared__ double sv[LU_THREADS / 32];
     __shared__ int si[LU_THREADS / 32];
     __shared__ int s_p;
-    const int m = blockIdx.y, c = blockIdx.x, ctas = gridDim.x, tid = threadIdx.x;
+    const int m = blockIdx.y, c = blockIdx.x, tid = threadIdx.x;
     double2* A = M + (long long)m * mstride;
     const int r0 = k0 + c * rows_per;
     const int nr = min(rows_per, n - r0);
@@ -489,6 +489,15 @@ __global__ void __launch_bounds__(256) ozaki_split_kernel(const double2* X, int 
     if (lane == 0) ex[r] = e;
 }
 
+// four 8 x 8 FP16 matrices from shared memory (row addresses from lanes 0-7,
+// 8-15, 16-23, 24-31), each thread receiving its fragment pair of each
+DD_DEV void ldsm_x4(uint32_t* r, const __half* row_addr) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(row_addr);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
 DD_DEV void mma_f16_f32(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -541,26 +550,23 @@ __global__ void __launch_bounds__(128, 2) ozaki_update_kernel(int m, int nn, con
             const __half* bb = sB + ((d - s) * OZ_TN + 32 * wn) * OZ_LD;
 #pragma unroll
             for (int ks = 0; ks < OZ_K / 16; ++ks) {
-                const int k0 = 16 * ks + 2 * tig, k1 = k0 + 8;
+                // A fragment: rows lane % 16, k half lane / 16 of the 16 x 16 tile
                 uint32_t a[4];
-                a[0] = *reinterpret_cast<const uint32_t*>(ab + g * OZ_LD + k0);
-                a[1] = *reinterpret_cast<const uint32_t*>(ab + (g + 8) * OZ_LD + k0);
-                a[2] = *reinterpret_cast<const uint32_t*>(ab + g * OZ_LD + k1);
-                a[3] = *reinterpret_cast<const uint32_t*>(ab + (g + 8) * OZ_LD + k1);
+                ldsm_x4(a, ab + (lane & 15) * OZ_LD + 16 * ks + (lane >> 4) * 8);
                 // first half of k: Re U (real part), Im U (imaginary part);
                 // second half: -Im U (real part), Re U (imaginary part)
                 const bool hi = 16 * ks >= LU_NB;
                 const int ko = hi ? -LU_NB : LU_NB;
                 const uint32_t sg = hi ? 0x80008000u : 0u;
+                // B fragments of one n8 tile: k and k + 8 for the real part,
+                // the same at offset ko for the imaginary part
+                const int kl = 16 * ks + ((lane >> 3) & 1) * 8 + ((lane >> 4) ? ko : 0);
 #pragma unroll
                 for (int nt = 0; nt < 4; ++nt) {
-                    const __half* bc = bb + (8 * nt + g) * OZ_LD;
-                    const uint32_t br0 = *reinterpret_cast<const uint32_t*>(bc + k0) ^ sg;
-                    const uint32_t br1 = *reinterpret_cast<const uint32_t*>(bc + k1) ^ sg;
-                    const uint32_t bi0 = *reinterpret_cast<const uint32_t*>(bc + k0 + ko);
-                    const uint32_t bi1 = *reinterpret_cast<const uint32_t*>(bc + k1 + ko);
-                    mma_f16_f32(fR[nt], a, br0, br1);
-                    mma_f16_f32(fI[nt], a, bi0, bi1);
+                    uint32_t b[4];
+                    ldsm_x4(b, bb + (8 * nt + (lane & 7)) * OZ_LD + kl);
+                    mma_f16_f32(fR[nt], a, b[0] ^ sg, b[1] ^ sg);
+                    mma_f16_f32(fI[nt], a, b[2], b[3]);
                 }
             }
         }
