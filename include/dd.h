@@ -358,7 +358,8 @@ int dd_logdet_exact(dd_t h, const void* U, int which, double* out);
  * Ozaki scheme (every FP64 row and column scaled by a power of two and cut
  * into 8 integer slices of 7 bits; the 36 slice pairs of the 8 heaviest
  * weights multiplied with mma.sync, whose FP32 accumulation is exact for
- * these integers, and summed in FP64; what is left out stays below the
+ * these integers, paired exactly in int32 and summed in FP64; what is left
+ * out stays below the
  * rounding bound of an FP64 dot product); on = 0 on the FP64 FMA pipe (no
  * counterpart in the paper: the tensor-core form of its exact check path).
  * Falls back to FP64 FMA when the exact-path workspace has no room for the
