@@ -165,8 +165,10 @@ DD_DEV void block_argmax(double best, int bi, double* sv, int* si) {
 DD_DEV bool lu_grid_barrier(unsigned* bar, unsigned target, int* status, int* s_ok) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(bar, 1u);
+        // the arrival releases the block's writes before the barrier (ordered
+        // after them by __syncthreads); the acquiring load of the count
+        // orders the block's later reads after the other blocks' writes
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
         int ok = 1;
         for (long long spin = 0;; ++spin) {
             unsigned v;
@@ -177,9 +179,8 @@ DD_DEV bool lu_grid_barrier(unsigned* bar, unsigned target, int* status, int* s_
                 raise_status(status, DD_ERR_TIMEOUT);
                 break;
             }
-            __nanosleep(64);
+            __nanosleep(16);
         }
-        __threadfence();
         *s_ok = ok;
     }
     __syncthreads();
