@@ -358,7 +358,7 @@ int dd_logdet_exact(dd_t h, const void* U, int which, double* out);
  * Ozaki scheme (every FP64 row and column scaled by a power of two and cut
  * into 8 integer slices of 7 bits; the 36 slice pairs of the 8 heaviest
  * weights multiplied with mma.sync, whose FP32 accumulation is exact for
- * these integers, paired exactly in int32 and summed in FP64; what is left
+ * these integers, grouped exactly in int64 and summed in FP64; what is left
  * out stays below the
  * rounding bound of an FP64 dot product); on = 0 on the FP64 FMA pipe (no
  * counterpart in the paper: the tensor-core form of its exact check path).

@@ -444,8 +444,9 @@ __global__ void __launch_bounds__(32 * LU_TRSM_WARPS) lu_swap_trsm_kernel(double
 // slices is an integer below 2^(2 OZ_BETA); the slice pairs (s, t) of one
 // diagonal d = s + t share the weight 2^(-OZ_BETA (d + 2)), and their sum
 // over the 64 terms stays below 2^22, so the tensor cores' FP32 accumulation
-// of a diagonal is exact.  The diagonals d < OZ_S are combined in pairs in
-// int32 (exact), the pairs summed in FP64 and scaled by 2^(e_i + f_j).  What is left out (the pairs with s + t >= OZ_S
+// of a diagonal is exact.  The diagonals d < OZ_S are combined in groups of
+// four in int64 (exact), the groups summed in FP64 and scaled by
+// 2^(e_i + f_j).  What is left out (the pairs with s + t >= OZ_S
 // and the remainders after OZ_S slices) adds up to less than 2^-48 of the
 // product of the row and column maxima, below the rounding bound of an FP64
 // dot product of the same 64 terms (64 x 2^-53).  Complex products:
@@ -534,7 +535,7 @@ __global__ void __launch_bounds__(128, 2) ozaki_update_kernel(int m, int nn, con
     __syncthreads();
     const int wm = warp, wn = 0, g = lane >> 2, tig = lane & 3;
     double accR[4][4], accI[4][4];
-    int gR[4][4], gI[4][4];
+    long long gR[4][4], gI[4][4];
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
@@ -542,7 +543,7 @@ __global__ void __launch_bounds__(128, 2) ozaki_update_kernel(int m, int nn, con
             accR[nt][c] = accI[nt][c] = 0.0;
             gR[nt][c] = gI[nt][c] = 0;
         }
-    static_assert(OZ_S % 2 == 0, "diagonals are summed in pairs");
+    static_assert(OZ_S % 4 == 0, "diagonals are summed in groups of four");
 #pragma unroll 1
     for (int d = 0; d < OZ_S; ++d) {
         float fR[4][4], fI[4][4];
@@ -576,25 +577,25 @@ __global__ void __launch_bounds__(128, 2) ozaki_update_kernel(int m, int nn, con
                 }
             }
         }
-        // two neighbouring diagonals combine exactly in int32 (2^7 |v_d| +
-        // |v_d+1| < 2^31), so the FP64 pipe sees one conversion and one FMA
-        // per element for every pair of diagonals
-        if ((d & 1) == 0) {
+        // four neighbouring diagonals combine exactly in int64 (Horner in
+        // 2^7: below 2^43), so the FP64 pipe sees one conversion and one FMA
+        // per element for every four diagonals
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
+        for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    gR[nt][c] = __float2int_rn(fR[nt][c]) * (1 << OZ_BETA);
-                    gI[nt][c] = __float2int_rn(fI[nt][c]) * (1 << OZ_BETA);
-                }
-        } else {
+            for (int c = 0; c < 4; ++c) {
+                gR[nt][c] = gR[nt][c] * (1 << OZ_BETA) + __float2int_rn(fR[nt][c]);
+                gI[nt][c] = gI[nt][c] * (1 << OZ_BETA) + __float2int_rn(fI[nt][c]);
+            }
+        if ((d & 3) == 3) {
             const double w = ldexp(1.0, -OZ_BETA * (d + 2));
 #pragma unroll
             for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    accR[nt][c] = fma(w, (double)(gR[nt][c] + __float2int_rn(fR[nt][c])), accR[nt][c]);
-                    accI[nt][c] = fma(w, (double)(gI[nt][c] + __float2int_rn(fI[nt][c])), accI[nt][c]);
+                    accR[nt][c] = fma(w, (double)gR[nt][c], accR[nt][c]);
+                    accI[nt][c] = fma(w, (double)gI[nt][c], accI[nt][c]);
+                    gR[nt][c] = gI[nt][c] = 0;
                 }
         }
     }
