@@ -299,6 +299,8 @@ __global__ void __launch_bounds__(LU_THREADS) lu_panel_multi_kernel(double2* M, 
     __shared__ double2 pan[LU_PR][LU_LD];
     __shared__ double2 Lm[LU_PR][LU_LD];
     __shared__ double2 urow[LU_NB];
+    __shared__ double2 s_inv;     // 1 / pivot of the current column
+    __shared__ double s_pm[LU_NB];  // |pivot|^2 per column (their logs are summed at the end)
     __shared__ int s_p, s_ok;
     const int m = blockIdx.y, c = blockIdx.x, ctas = gridDim.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -352,24 +354,27 @@ __global__ void __launch_bounds__(LU_THREADS) lu_panel_multi_kernel(double2* M, 
                 const double2 u = __ldcg(aux.prow + (mc * ctas + bc) * LU_NB + lane);
                 const double2 old = __ldcg(aux.rowk + mc * LU_NB + lane);
                 urow[lane] = u;
+                if (lane == j) {  // the pivot: its reciprocal once for the block
+                    const double pm = u.x * u.x + u.y * u.y;
+                    s_pm[j] = pm;
+                    s_inv = pm > 0.0 ? make_double2(u.x / pm, -u.y / pm) : make_double2(0.0, 0.0);
+                }
                 if (own_k) (lane < j ? Lm[k - r0][lane] : pan[k - r0][lane]) = u;
                 if (bidx != k && bidx >= r0 && bidx < r0 + nr) (lane < j ? Lm[bidx - r0][lane] : pan[bidx - r0][lane]) = old;
             }
             if (lane == 0) s_p = bidx;
         }
         __syncthreads();
-        const double2 piv = urow[j];
-        const double pm = piv.x * piv.x + piv.y * piv.y;
+        const double pm = s_pm[j];
         if (tid == 0 && own_k) {
             aux.ipiv[(long long)m * n + k] = s_p;
             if (!(pm > 0.0)) raise_status(status, DD_ERR_NUMERIC);
-            logdet[m] += 0.5 * log(pm);
         }
         const int r = lane;
         if (r < nr && r0 + r > k) {
             const double2 a = pan[r][j];
             if (pm > 0.0) {
-                const cpx<double> l = cmul(mk<double>(a.x, a.y), mk<double>(piv.x / pm, -piv.y / pm));
+                const cpx<double> l = cmul(mk<double>(a.x, a.y), mk<double>(s_inv.x, s_inv.y));
                 if (warp == 0) Lm[r][j] = make_double2(l.x, l.y);
                 for (int jj = j + 1 + warp; jj < nbe; jj += nwarps) {
                     const double2 u = urow[jj];
@@ -386,6 +391,13 @@ __global__ void __launch_bounds__(LU_THREADS) lu_panel_multi_kernel(double2* M, 
     for (int e = tid; e < nr * nbe; e += blockDim.x) {
         const int rr = e % nr, j = e / nr;
         A[(r0 + rr) + (long long)(k0 + j) * n] = (r0 + rr > k0 + j) ? Lm[rr][j] : pan[rr][j];
+    }
+    // ln|det| of the panel's pivots (the first thread block owns them)
+    if (c == 0 && warp == 0) {
+        double l = lane < nbe ? 0.5 * log(s_pm[lane]) : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+        if (lane == 0) logdet[m] += l;
     }
     if (c == 0 && tid == 0) lu_panel_permutation(aux, m, n, k0, nbe);
 }
