@@ -521,11 +521,12 @@ DD_DEV void mma_f16_f32(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
 }
 
 // C (m x nn complex, column-major, ld ldc) -= L21 U12 from the slices: a
-// 64 x 32 tile of C per thread block of 4 warps, 16 x 32 per warp (one m16
-// row of four n8 tiles), every slice of the tile's rows and columns staged
+// 64 x 32 tile of C per thread block of 8 warps, 16 x 16 per warp (one m16
+// row of two n8 tiles), every slice of the tile's rows and columns staged
 // in shared memory once (110 KB: two thread blocks per SM, so that one
 // stages while the other computes)
-__global__ void __launch_bounds__(128, 2) ozaki_update_kernel(int m, int nn, const __half* As, const int* ea,
+constexpr int OZ_NT = 2;  // n8 tiles per warp
+__global__ void __launch_bounds__(256, 2) ozaki_update_kernel(int m, int nn, const __half* As, const int* ea,
                                                               long long sa, const __half* Bs, const int* eb,
                                                               long long sb, double2* C, int ldc) {
     extern __shared__ __align__(16) unsigned char oz_smem[];
@@ -545,11 +546,11 @@ __global__ void __launch_bounds__(128, 2) ozaki_update_kernel(int m, int nn, con
         *reinterpret_cast<uint4*>(sB + (s * OZ_TN + col) * OZ_LD + q * 8) = vb;
     }
     __syncthreads();
-    const int wm = warp, wn = 0, g = lane >> 2, tig = lane & 3;
-    double accR[4][4], accI[4][4];
-    long long gR[4][4], gI[4][4];
+    const int wm = warp & 3, wn = warp >> 2, g = lane >> 2, tig = lane & 3;
+    double accR[OZ_NT][4], accI[OZ_NT][4];
+    long long gR[OZ_NT][4], gI[OZ_NT][4];
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
+    for (int nt = 0; nt < OZ_NT; ++nt)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             accR[nt][c] = accI[nt][c] = 0.0;
@@ -558,15 +559,15 @@ __global__ void __launch_bounds__(128, 2) ozaki_update_kernel(int m, int nn, con
     static_assert(OZ_S % 4 == 0, "diagonals are summed in groups of four");
 #pragma unroll 1
     for (int d = 0; d < OZ_S; ++d) {
-        float fR[4][4], fI[4][4];
+        float fR[OZ_NT][4], fI[OZ_NT][4];
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
+        for (int nt = 0; nt < OZ_NT; ++nt)
 #pragma unroll
             for (int c = 0; c < 4; ++c) fR[nt][c] = fI[nt][c] = 0.0f;
 #pragma unroll 1
         for (int s = 0; s <= d; ++s) {
             const __half* ab = sA + (s * OZ_TM + 16 * wm) * OZ_LD;
-            const __half* bb = sB + ((d - s) * OZ_TN + 32 * wn) * OZ_LD;
+            const __half* bb = sB + ((d - s) * OZ_TN + 8 * OZ_NT * wn) * OZ_LD;
 #pragma unroll
             for (int ks = 0; ks < OZ_K / 16; ++ks) {
                 // A fragment: rows lane % 16, k half lane / 16 of the 16 x 16 tile
@@ -581,7 +582,7 @@ __global__ void __launch_bounds__(128, 2) ozaki_update_kernel(int m, int nn, con
                 // the same at offset ko for the imaginary part
                 const int kl = 16 * ks + ((lane >> 3) & 1) * 8 + ((lane >> 4) ? ko : 0);
 #pragma unroll
-                for (int nt = 0; nt < 4; ++nt) {
+                for (int nt = 0; nt < OZ_NT; ++nt) {
                     uint32_t b[4];
                     ldsm_x4(b, bb + (8 * nt + (lane & 7)) * OZ_LD + kl);
                     mma_f16_f32(fR[nt], a, b[0] ^ sg, b[1] ^ sg);
@@ -593,7 +594,7 @@ __global__ void __launch_bounds__(128, 2) ozaki_update_kernel(int m, int nn, con
         // 2^7: below 2^43), so the FP64 pipe sees one conversion and one FMA
         // per element for every four diagonals
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
+        for (int nt = 0; nt < OZ_NT; ++nt)
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 gR[nt][c] = gR[nt][c] * (1 << OZ_BETA) + __float2int_rn(fR[nt][c]);
@@ -602,7 +603,7 @@ __global__ void __launch_bounds__(128, 2) ozaki_update_kernel(int m, int nn, con
         if ((d & 3) == 3) {
             const double w = ldexp(1.0, -OZ_BETA * (d + 2));
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
+            for (int nt = 0; nt < OZ_NT; ++nt)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     accR[nt][c] = fma(w, (double)gR[nt][c], accR[nt][c]);
@@ -612,11 +613,11 @@ __global__ void __launch_bounds__(128, 2) ozaki_update_kernel(int m, int nn, con
         }
     }
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
+    for (int nt = 0; nt < OZ_NT; ++nt)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int row = r0 + 16 * wm + g + (c >= 2 ? 8 : 0);
-            const int col = c0 + 32 * wn + 8 * nt + 2 * tig + (c & 1);
+            const int col = c0 + 8 * OZ_NT * wn + 8 * nt + 2 * tig + (c & 1);
             if (row < m && col < nn) {
                 const double sc = ldexp(1.0, ea[row] + eb[col]);
                 double2& o = C[row + (long long)col * ldc];
@@ -856,7 +857,7 @@ static int lu_batched(dd_handle* h, double2* M, long long mstride, int batch, in
                     DD_KLAUNCH(h, ozaki_split_kernel<<<grid_for(right, 8), 256, 0, h->stream>>>(
                                       Mm + k0 + (long long)(k0 + nbe) * n, n, right, nbe, true, ob, osb, oeb));
                     dim3 g(grid_for(right, OZ_TN), grid_for(below, OZ_TM));
-                    DD_KLAUNCH(h, ozaki_update_kernel<<<g, 128, OZ_SMEM, h->stream>>>(
+                    DD_KLAUNCH(h, ozaki_update_kernel<<<g, 256, OZ_SMEM, h->stream>>>(
                                       below, right, oa, oea, osa, ob, oeb, osb, Mm + (k0 + nbe) + (long long)(k0 + nbe) * n,
                                       n));
                 }
