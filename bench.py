@@ -900,7 +900,7 @@ def measure_lu(dev, stream, reps=3):
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1) / reps
         out[name] = {"ms": ms, "n": n, "matrices": nmat}
-        out[name]["trailing_update"] = ("FP16 tensor cores (FP64-exact Ozaki slices)" if tc and n > 384
+        out[name]["trailing_update"] = ("FP16 tensor cores (Ozaki slices, FP64 accuracy)" if tc and n > 384
                                         else "FP64 FMA")
         if which == 0:
             tf = 8.0 * n ** 3 / 3.0 / (ms / 1e3) / 1e12

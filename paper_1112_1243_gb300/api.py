@@ -331,8 +331,8 @@ def dd_solver_stats(h, kind):
 
 
 def dd_lu_tensor_cores(h, on=True):
-    """Trailing update of the dense LU on the tensor cores (FP64-exact Ozaki
-    slices; default) or on the FP64 FMA pipe."""
+    """Trailing update of the dense LU on the tensor cores (Ozaki slices with
+    FP64 accuracy; default) or on the FP64 FMA pipe."""
     _check(h, _lib.load().dd_lu_tensor_cores(h.ptr, 1 if on else 0))
 
 

@@ -447,8 +447,8 @@ __global__ void __launch_bounds__(32 * LU_TRSM_WARPS) lu_swap_trsm_kernel(double
 }
 
 // ------------------------------------------------ trailing update on tensor cores
-// The trailing update A22 -= L21 U12 as an FP64-exact product on the FP16
-// tensor cores (Ozaki scheme).  Each row i of [Re L21, Im L21] (64 reals) is
+// The trailing update A22 -= L21 U12 on the FP16 tensor cores with FP64
+// accuracy (Ozaki scheme).  Each row i of [Re L21, Im L21] (64 reals) is
 // scaled by 2^-e_i so that its entries are below 1 in magnitude and cut into
 // OZ_S slices of OZ_BETA bits: x 2^-e_i = sum_s q_s 2^(-OZ_BETA (s + 1)),
 // q_s integers (|q_0| <= 2^OZ_BETA, |q_s| <= 2^(OZ_BETA - 1)), exact in FP16.
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(32 * LU_TRSM_WARPS) lu_swap_trsm_kernel(double
 constexpr int OZ_BETA = 7;
 constexpr int OZ_S = 8;
 constexpr int OZ_K = 2 * LU_NB;  // real k of the complex panel width
-constexpr int OZ_TM = 64;        // rows of C per thread block (4 warps of 16 rows)
+constexpr int OZ_TM = 64;        // rows of C per thread block (4 groups of 16 rows)
 constexpr int OZ_TN = 32;        // columns of C per thread block (two thread blocks per SM)
 constexpr int OZ_LD = OZ_K + 8;  // padded smem row of 64 halves (conflict-free fragment loads)
 
