@@ -935,18 +935,47 @@ static int logdet_schur(dd_handle* h, const double* U, double* out) {
     rc = lu_batched(h, aug, as, nbk, nb12, nb12 + nh, ld, true);
     if (rc) return rc;
     // Y = B X: B = D[0:nh, nh:n]; X rows of white block b live in aug b, columns nb12..
-    for (int b = 0; b < nbk; ++b) {
-        dim3 g(grid_for(nh, ZG_T), grid_for(nh, ZG_T), 1);
-        DD_KLAUNCH(h, zgemm_tile_kernel<<<g, 256, 0, h->stream>>>(nh, nh, nb12, D + (long long)(nh + b * nb12) * n, n, 0,
-                                                                aug + b * as + (long long)nb12 * nb12, nb12, 0, Y, nh,
-                                                                0, 1.0, b == 0 ? 0.0 : 1.0));
+    // On the tensor cores (the slices of the LU's trailing update, 32 columns
+    // of B and rows of X at a time) Y accumulates -B X.
+    size_t cap = 0;
+    char* scr = lu_scratch(h, &cap);
+    const long long osz = (long long)nh * OZ_K;
+    const bool tensor = h->lu_tensor && nb12 % LU_NB == 0 &&
+                        2 * (size_t)OZ_S * osz * sizeof(__half) + 2 * (size_t)nh * sizeof(int) <= cap;
+    if (tensor) {
+        __half* oa = (__half*)scr;
+        __half* ob = oa + OZ_S * osz;
+        int* oea = (int*)(ob + OZ_S * osz);
+        int* oeb = oea + nh;
+        cudaError_t e = cudaFuncSetAttribute(ozaki_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)OZ_SMEM);
+        if (e != cudaSuccess) return dd_cuda_check(h, e, "ozaki_update_kernel shared memory");
+        const long long yn = (long long)nh * nh;
+        DD_KLAUNCH(h, zero_kernel<<<grid_for(yn, 256), 256, 0, h->stream>>>(yn, Y));
+        for (int b = 0; b < nbk; ++b)
+            for (int kc = 0; kc < nb12 / LU_NB; ++kc) {
+                DD_KLAUNCH(h, ozaki_split_kernel<<<grid_for(nh, 8), 256, 0, h->stream>>>(
+                                  D + (long long)(nh + b * nb12 + kc * LU_NB) * n, n, nh, LU_NB, false, oa, osz, oea));
+                DD_KLAUNCH(h, ozaki_split_kernel<<<grid_for(nh, 8), 256, 0, h->stream>>>(
+                                  aug + b * as + (long long)nb12 * nb12 + kc * LU_NB, nb12, nh, LU_NB, true, ob, osz, oeb));
+                DD_KLAUNCH(h, ozaki_update_kernel<<<dim3(grid_for(nh, OZ_TN), grid_for(nh, OZ_TM)), 256, OZ_SMEM,
+                                                    h->stream>>>(nh, nh, oa, oea, osz, ob, oeb, osz, Y, nh));
+            }
+    } else {
+        for (int b = 0; b < nbk; ++b) {
+            dim3 g(grid_for(nh, ZG_T), grid_for(nh, ZG_T), 1);
+            DD_KLAUNCH(h, zgemm_tile_kernel<<<g, 256, 0, h->stream>>>(nh, nh, nb12, D + (long long)(nh + b * nb12) * n, n,
+                                                                    0, aug + b * as + (long long)nb12 * nb12, nb12, 0,
+                                                                    Y, nh, 0, 1.0, b == 0 ? 0.0 : 1.0));
+        }
     }
+    const double ysign = tensor ? -1.0 : 1.0;
     // Z = A^{-1} Y: per black block [A_b | Y_b]
     for (int b = 0; b < nbk; ++b) {
         int r0 = b * nb12;
         dim3 gA(grid_for(nb12, 16), grid_for(nb12, 16)), gY(grid_for(nh, 16), grid_for(nb12, 16));
         DD_KLAUNCH(h, copy_sub_kernel<<<gA, b16, 0, h->stream>>>(D, n, r0, r0, nb12, nb12, aug + b * as, nb12, 0, 1.0, 0));
-        DD_KLAUNCH(h, copy_sub_kernel<<<gY, b16, 0, h->stream>>>(Y, nh, r0, 0, nb12, nh, aug + b * as, nb12, nb12, 1.0, 0));
+        DD_KLAUNCH(h, copy_sub_kernel<<<gY, b16, 0, h->stream>>>(Y, nh, r0, 0, nb12, nh, aug + b * as, nb12, nb12, ysign, 0));
     }
     rc = lu_batched(h, aug, as, nbk, nb12, nb12 + nh, ld, true);
     if (rc) return rc;
