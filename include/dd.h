@@ -354,7 +354,8 @@ int dd_global_accept(dd_t h, void* U, const void* U_old, const double* ln_r, int
 int dd_logdet_exact(dd_t h, const void* U, int which, double* out);
 
 /* Trailing update of the dense LU of dd_logdet_exact (matrices above 384
- * rows): on = 1 (default) on the FP16 tensor cores with FP64 accuracy by the
+ * rows) and the product B E^-1 C of its Schur-complement assembly (which =
+ * 2): on = 1 (default) on the FP16 tensor cores with FP64 accuracy by the
  * Ozaki scheme (every FP64 row and column scaled by a power of two and cut
  * into 8 integer slices of 7 bits; the 36 slice pairs of the 8 heaviest
  * weights multiplied with mma.sync, whose FP32 accumulation is exact for
